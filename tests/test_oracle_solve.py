@@ -1,0 +1,101 @@
+"""Pins for the oracle's solvers (paper Sec. 5) against dense factorisation and beam theory."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fem as F
+from oracle import mesh as M
+from oracle import solve as S
+
+NU = 0.3
+
+
+def _system(w):
+    d = w.dom
+    m = M.build_mesh(d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, dirichlet_faces=w.dirichlet_faces)
+    rho = w.rho[m.perm]
+    A, f, C = F.reduced_system(m, rho, w.load_nodes, w.load_comp, w.load_val)
+    return m, rho, A, f, C
+
+
+def test_sparse_direct_matches_textbook_dense_cholesky():
+    dom = W.Domain(4, 2, 2, 1, 0.5)
+    w = W.random_field_mesh("tiny", dom, 7, [(0.2, 0.8)])
+    w.rho = 0.2 + 0.8 * w.rho          # moderate contrast: both factorisations stay accurate
+    m, rho, A, f, C = _system(w)
+    assert A.shape[0] < 600
+    Lm = S.dense_cholesky(A.toarray())
+    ud = S.cholesky_solve(Lm, f)
+    us = S.direct(A, f)
+    assert np.abs(ud - us).max() <= 1e-10 * np.abs(us).max()
+    assert S.relative_residual(A, us, f) < 1e-12
+
+
+def test_jacobi_pcg_reaches_direct_solution():
+    w = W.config1()
+    m, rho, A, f, C = _system(w)
+    u = S.direct(A, f)
+    up, it, rr, _ = S.jacobi_pcg(A, f, rtol=1e-12)
+    assert rr <= 1e-12
+    assert S.relative_residual(A, up, f) < 1e-11
+    # energy-norm error of CG is what the residual controls; compliance converges fast
+    assert abs(f @ up - f @ u) <= 1e-9 * abs(f @ u)
+    # warm start from the solution needs no iterations
+    _, it0, _, _ = S.jacobi_pcg(A, f, u0=u, rtol=1e-8)
+    assert it0 == 0
+
+
+def _tip_deflection(k):
+    dom = W.Domain(8 * k, k, k, 0, 1.0 / k)
+    m = M.build_mesh(dom.nx, dom.ny, dom.nz, 0, dom.h0, W.uniform_leaves(dom))
+    tip = np.nonzero(m.nodes[:, 0] == 8 * k)[0]
+    yz = m.nodes[tip][:, 1:]
+    wgt = np.where((yz == 0) | (yz == k), 0.5, 1.0).prod(axis=1)
+    wgt = wgt / wgt.sum()          # consistent nodal loads of a uniform traction, total -1
+    A, f, C = F.reduced_system(m, np.ones(m.Ne), m.nodes[tip], np.full(tip.size, 2), -wgt, Emin=0.0)
+    uf = (C @ S.direct(A, f)).reshape(-1, 3)
+    return -(uf[tip, 2] * wgt).sum()
+
+
+def test_cantilever_tip_deflection_converges_to_timoshenko():
+    """Slender 8 x 1 x 1 box, E = 1, nu = 0.3, clamped at x = 0, unit shear load on the tip:
+    delta = F L^3 / (3 E I) + F L / (kappa G A) with kappa = 5/6."""
+    G = 1.0 / (2 * (1 + NU))
+    exact = 8.0 ** 3 / (3.0 / 12.0) + 8.0 / (5.0 / 6.0 * G)
+    d = [_tip_deflection(k) for k in (2, 4, 8)]
+    assert d[0] < d[1] < d[2] < exact
+    assert abs(d[2] / exact - 1) < 0.025
+    aitken = d[2] - (d[2] - d[1]) ** 2 / ((d[2] - d[1]) - (d[1] - d[0]))
+    assert abs(aitken / exact - 1) < 0.01
+
+
+def test_refined_mesh_agrees_with_uniform_mesh_on_a_linear_solution():
+    """A pure tension field is represented exactly on any mesh: uniform and AMR meshes give
+    the same displacements at shared nodes (AMR's premise, Sec. 1)."""
+    dom = W.Domain(4, 2, 2, 1, 0.5)
+    lv_uni = W.refine(dom, W.uniform_leaves(dom), np.ones(16, bool))
+    lv_amr = W.refine(dom, W.uniform_leaves(dom), np.arange(16) % 3 == 0)
+    out = []
+    for leaves in (lv_uni, lv_amr):
+        m = M.build_mesh(4, 2, 2, 1, 0.5, leaves, dirichlet_faces=0b1)
+        tip = np.nonzero(m.nodes[:, 0] == 8)[0]
+        yz = m.nodes[tip][:, 1:]
+        # consistent nodal loads of a uniform traction on the tip face (finest unit 0.25)
+        wgt = np.zeros(tip.size)
+        lk = {tuple(p): i for i, p in enumerate(map(tuple, m.nodes[tip]))}
+        for e in range(m.Ne):
+            s = 1 << (1 - m.leaves[e, 3])
+            if m.leaves[e, 0] + s != 8:
+                continue
+            for k in (1, 3, 5, 7):
+                p = tuple(m.leaves[e, :3] + s * M.CORNER_OFFSETS[k])
+                wgt[lk[p]] += (s * 0.25) ** 2 / 4.0     # physical face area / 4
+        A, f, C = F.reduced_system(m, np.ones(m.Ne), m.nodes[tip], np.zeros(tip.size, int), wgt, Emin=0.0, nu=0.0)
+        uf = (C @ S.direct(A, f)).reshape(-1, 3)
+        out.append({tuple(p): uf[i] for i, p in enumerate(map(tuple, m.nodes))})
+    common = set(out[0]) & set(out[1])
+    assert len(common) > 20
+    # nu = 0 and a clamped face that only has to resist x: uniaxial tension, u_x = sigma x / E
+    for p in common:
+        assert np.allclose(out[0][p], out[1][p], atol=1e-11)
+        assert abs(out[0][p][0] - p[0] * 0.25) < 1e-11
