@@ -1,0 +1,197 @@
+/*
+ * tm.h -- C ABI of the GB300 hot path for SIMP topology optimisation on a
+ * dynamically refined, 2:1-balanced octree hex mesh (Wang, de Sturler,
+ * Paulino, "Dynamic adaptive mesh refinement for topology optimization").
+ *
+ * The library solves the paper's state equation K(rho) u = f (Sec. 3, Eq. 1)
+ * on B8 (trilinear hex) elements with element-constant density and SIMP
+ * stiffness E_e = Emin + rho_e^p (E0 - Emin) (Eq. 2, Emin = 0 is the paper's
+ * form), eliminates hanging-node DOFs by the interpolation of Sec. 6 (Eq. 6-9),
+ * and provides the remaining steps of one optimisation iteration: compliance
+ * sensitivities, the volume-weighted filter of Eq. 5 and the optimality-
+ * criteria update.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Status: every function returns TM_OK (0) or a TM_E* code; the message of
+ *   the last failure is available from tm_last_error().  Nothing falls back to
+ *   the host: a missing or failing GPU is an error.
+ * - Memory: pointers named *_dev are caller-owned device memory on the
+ *   context's device; all other pointers are caller-owned host memory that is
+ *   only read (or written, for outputs) during the call.  The library copies
+ *   what it keeps.
+ * - Streams: work is enqueued on the stream given to tm_create / tm_set_stream
+ *   (a cudaStream_t, NULL = legacy default).  Device outputs are valid once that
+ *   stream reaches them.  Calls that return a host scalar synchronise the
+ *   stream before returning.
+ * - Node vectors ("A-space"): length 3*Nn doubles, node-major, component
+ *   fastest (x, y, z), nodes in canonical order.  Entries at hanging and
+ *   Dirichlet DOFs are ignored on input and written as 0 on output; the
+ *   remaining n_free entries are the unknowns of the reduced system
+ *   A = C^T K C (Eq. 7 with the constrained DOFs eliminated; the paper's Eq. 8
+ *   keeps them with a unit diagonal and yields the same u).
+ * - Full vectors: length 3*Nn with hanging DOFs interpolated (Eq. 9) and
+ *   Dirichlet DOFs at their prescribed value 0.
+ * - Element vectors: length Ne doubles in canonical element order.
+ * - Canonical orders: elements by the Morton key of their anchor, nodes by
+ *   the Morton key of their coordinates (bit i of x, y, z at bits 3i, 3i+1,
+ *   3i+2); local corner k = i + 2j + 4m of an element sits at anchor + s(i,j,m).
+ */
+#ifndef TM_H
+#define TM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TM_OK 0
+#define TM_EINVAL 1          /* bad argument or invalid mesh                      */
+#define TM_ECUDA 2           /* CUDA runtime error (message has the CUDA string)  */
+#define TM_ENOTCONVERGED 3   /* solver hit max_iter before rtol                   */
+#define TM_ENONFINITE 4      /* NaN/Inf met in a reduction                        */
+#define TM_ETIMEOUT 5        /* a bounded device-side wait gave up                */
+#define TM_ENOMEM 6          /* device allocation failed                          */
+#define TM_ESTATE 7          /* call out of order (e.g. no mesh uploaded)         */
+
+#define TM_PREC_FP64 0       /* every step in FP64                                */
+#define TM_PREC_MIXED 1      /* FP32 operator inside FP64 iterative refinement    */
+#define TM_PREC_FP32 1
+
+typedef struct tm_ctx tm_ctx;
+
+/* A mesh: the box [0, nx h0] x [0, ny h0] x [0, nz h0] split into base cells of
+ * side h0, refined up to max_level.  Leaves are given on the finest integer grid
+ * (unit h0 / 2^max_level): leaf (ix, iy, iz, l) is the cube of side
+ * 2^(max_level - l) units anchored at (ix, iy, iz). */
+typedef struct {
+  int32_t nx, ny, nz;
+  int32_t max_level;
+  double h0;
+  int64_t n_leaves;
+  const int32_t *leaves;      /* host, 4 * n_leaves: ix, iy, iz, level          */
+  uint32_t dirichlet_faces;   /* bit 2*axis + side: that face is clamped (u = 0) */
+  double E0, Emin, nu, penal; /* SIMP material, Eq. 2                            */
+} tm_mesh_desc;
+
+typedef struct {
+  int64_t Ne, Nn;             /* elements, nodes                                  */
+  int64_t n_hanging;          /* hanging nodes                                    */
+  int64_t n_dirichlet;        /* Dirichlet nodes (hanging ones included)          */
+  int64_t n_free;             /* unknowns: 3 * (nodes neither hanging nor clamped) */
+  int32_t n_blocks;           /* element blocks of the operator kernel            */
+  int32_t max_local;          /* largest local-node count of a block              */
+  int64_t n_shared;           /* nodes touched by more than one block             */
+  int64_t device_bytes;       /* device memory held for this mesh                 */
+} tm_mesh_info;
+
+typedef struct {
+  double rtol;                /* stop when ||f - A u||_2 <= rtol ||f||_2          */
+  int32_t max_iter;           /* CG iterations (all sweeps together)              */
+  int32_t precision;          /* TM_PREC_FP64 or TM_PREC_MIXED                    */
+  double inner_rtol;          /* mixed: residual reduction of one FP32 sweep      */
+  int32_t check_every;        /* iterations between host convergence checks       */
+} tm_solve_opts;
+
+typedef struct {
+  int32_t iterations;         /* CG iterations performed (sum over sweeps)        */
+  int32_t sweeps;             /* refinement sweeps (1 for FP64)                   */
+  double rel_residual;        /* final ||f - A u|| / ||f|| evaluated in FP64      */
+  double seconds;             /* device time of the solve (CUDA events)           */
+  int32_t fp64_applies;       /* FP64 operator applications                       */
+  int32_t fp32_applies;       /* FP32 operator applications                       */
+} tm_solve_stats;
+
+/* Create a context on CUDA device `device`, enqueueing on `cuda_stream`
+ * (cudaStream_t or NULL).  *out receives the context; TM_ECUDA if the device is
+ * unusable. */
+int tm_create(tm_ctx **out, int device, void *cuda_stream);
+int tm_destroy(tm_ctx *ctx);
+int tm_set_stream(tm_ctx *ctx, void *cuda_stream);
+const char *tm_last_error(tm_ctx *ctx);
+
+/* Build the mesh tables of Sec. 6 from a leaf set and upload them (paper
+ * Sec. 4 marks/refines, Sec. 6 Fig. 3 limits incompatibility to one level).
+ * Rejects with TM_EINVAL: leaves out of range or misaligned, overlapping or
+ * non-covering leaf sets, and sets that are not 2:1 balanced (any two leaves
+ * whose closures meet differ by at most one level).  Replaces any previous
+ * mesh.  `info` (may be NULL) receives the sizes. */
+int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info);
+
+/* Copy the integer tables to host arrays (any may be NULL):
+ * perm[Ne]        canonical element i is input leaf perm[i];
+ * node_xyz[3*Nn]  node coordinates on the finest grid;
+ * conn[8*Ne]      node id of corner k of element e at conn[8e + k];
+ * hang_node[nh]   hanging node ids, ascending;
+ * hang_master[4*nh] their masters ascending (-1 padded; 2 = edge, 4 = face);
+ * node_flags[Nn]  bit 0 Dirichlet, bit 1 hanging. */
+int tm_mesh_tables(tm_ctx *ctx, int64_t *perm, int32_t *node_xyz, int32_t *conn,
+                   int32_t *hang_node, int32_t *hang_master, uint8_t *node_flags);
+
+/* Host-only construction of the same integer tables (no device, no context):
+ * the tables tm_mesh_upload builds, for inspection and testing on machines
+ * without a GPU.  On failure returns TM_EINVAL and writes a message into err
+ * (err_len bytes, may be 0).  info->device_bytes is 0. */
+typedef struct tm_tables tm_tables;
+int tm_tables_build(const tm_mesh_desc *d, tm_tables **out, tm_mesh_info *info, char *err, int err_len);
+/* Same layout as tm_mesh_tables. */
+int tm_tables_copy(const tm_tables *t, int64_t *perm, int32_t *node_xyz, int32_t *conn, int32_t *hang_node,
+                   int32_t *hang_master, uint8_t *node_flags);
+void tm_tables_free(tm_tables *t);
+
+/* f_dev (A-space) = C^T f_full where f_full holds the given nodal point loads
+ * (Eq. 7 right-hand side).  node_xyz: host, 3 per load, must be mesh nodes
+ * (TM_EINVAL otherwise); comp in {0,1,2}; loads on hanging nodes are folded
+ * into their masters. */
+int tm_build_rhs(tm_ctx *ctx, int64_t n_loads, const int32_t *node_xyz, const int32_t *comp,
+                 const double *val, double *f_dev);
+
+/* y = C^T K(rho) C x on the A-space (Eq. 6-7), FP64 arithmetic. */
+int tm_apply_K(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double *y_dev);
+
+/* Same operator in FP32 arithmetic on FP32 A-space vectors (the inner operator
+ * of TM_PREC_MIXED). */
+int tm_apply_K_f32(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float *y_dev);
+
+/* d_dev = diag(C^T K(rho) C) on the A-space (1 at constrained DOFs): the
+ * diagonal D of the rescaling D^-1/2 K D^-1/2 of Sec. 5. */
+int tm_jacobi_diag(tm_ctx *ctx, const double *rho_dev, double *d_dev);
+
+/* Solve C^T K(rho) C u = f by Jacobi-preconditioned CG (equivalent to CG on the
+ * diagonally rescaled system of Sec. 5), warm-started from u_dev (Sec. 5).
+ * TM_PREC_FP64: every step in FP64.  TM_PREC_MIXED: FP64 residual and update
+ * around FP32-operator CG sweeps whose dot products accumulate in FP64.
+ * Returns TM_ENOTCONVERGED (u holds the last iterate) when max_iter is reached,
+ * TM_ENONFINITE on NaN/Inf. `stats` may be NULL. */
+int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double *u_dev,
+                 const tm_solve_opts *opts, tm_solve_stats *stats);
+
+/* u_full = C u (Eq. 9): hanging DOFs interpolated, Dirichlet DOFs 0. */
+int tm_expand(tm_ctx *ctx, const double *u_dev, double *u_full_dev);
+
+/* dc_e = -p rho_e^(p-1) (E0 - Emin) h_e u_e^T K0 u_e (compliance sensitivity of
+ * Sec. 3) from a full vector; *compliance_out (host, may be NULL) receives
+ * sum_e E_e h_e u_e^T K0 u_e, which equals f^T u (Eq. 1) at convergence. */
+int tm_sensitivity(tm_ctx *ctx, const double *rho_dev, const double *u_full_dev, double *dc_dev,
+                   double *compliance_out);
+
+/* Element filters over centre distances below rmin with H_de = rmin - dist
+ * (Eq. 4), self included:
+ * mode 0: Eq. 5, out_e = sum_d rho_d H_de V_d x_d / (rho_e sum_d H_de V_d);
+ * mode 1: density filter, out_e = sum_d H_de V_d x_d / sum_d H_de V_d.
+ * rmin is limited to 4 finest cells (TM_EINVAL beyond). */
+int tm_filter(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double rmin, int mode,
+              double *out_dev);
+
+/* Optimality-criteria update (Sec. 3): rho_new = clamp(rho (max(-dc,0)/(lambda V_e))^eta,
+ * max(rho_min, rho - move), min(1, rho + move)) with lambda bisected until
+ * sum rho_new V_e = volfrac * |Omega| (relative lambda bracket 1e-12).
+ * *change_out (host, may be NULL) receives max |rho_new - rho|. */
+int tm_oc_update(tm_ctx *ctx, const double *rho_dev, const double *dc_dev, double volfrac, double move,
+                 double eta, double rho_min, double *rho_new_dev, double *change_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TM_H */

@@ -1,0 +1,524 @@
+// C ABI of libtm (declared in include/tm.h): argument checks, device memory of
+// the mesh tables and work buffers, and the host-side drivers of the solvers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pcg.cuh"
+#include "tm_internal.h"
+#include "topopt.cuh"
+
+using namespace amr;
+
+namespace {
+
+int fail(tm_ctx *ctx, int code, const std::string &msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+#define TM_CUDA(ctx, ...)                                                                   \
+  do {                                                                                      \
+    cudaError_t _e = (__VA_ARGS__);                                                         \
+    if (_e != cudaSuccess)                                                                  \
+      return fail(ctx, TM_ECUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+#define TM_CHECK_CTX(ctx)                                                                   \
+  do {                                                                                      \
+    if (!(ctx)) return TM_EINVAL;                                                           \
+    cudaError_t _e = cudaSetDevice((ctx)->device);                                          \
+    if (_e != cudaSuccess) return fail(ctx, TM_ECUDA, cudaGetErrorString(_e));              \
+  } while (0)
+
+#define TM_CHECK_MESH(ctx)                                                                  \
+  do {                                                                                      \
+    if (!(ctx)->has_mesh) return fail(ctx, TM_ESTATE, "no mesh uploaded");                  \
+  } while (0)
+
+template <typename T>
+cudaError_t upload(std::vector<void *> &owned, int64_t &bytes, T **dst, const std::vector<T> &src) {
+  const size_t n = std::max<size_t>(src.size(), 1);
+  cudaError_t e = cudaMalloc((void **)dst, n * sizeof(T));
+  if (e != cudaSuccess) return e;
+  owned.push_back(*dst);
+  bytes += (int64_t)(n * sizeof(T));
+  if (!src.empty()) return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t alloc(std::vector<void *> &owned, int64_t &bytes, T **dst, size_t n) {
+  n = std::max<size_t>(n, 1);
+  cudaError_t e = cudaMalloc((void **)dst, n * sizeof(T));
+  if (e != cudaSuccess) return e;
+  owned.push_back(*dst);
+  bytes += (int64_t)(n * sizeof(T));
+  return cudaMemset(*dst, 0, n * sizeof(T));
+}
+
+void release(std::vector<void *> &owned) {
+  for (void *p : owned) cudaFree(p);
+  owned.clear();
+}
+
+// Scalars region layout (doubles): [0, 64) SolveScalars, [64, 80) OcState, [80] compliance,
+// [81] outer rr, [82] ff.
+constexpr int kScalDoubles = 128;
+SolveScalars *solve_scalars(tm_ctx *c) { return reinterpret_cast<SolveScalars *>(c->w.scal); }
+OcState *oc_state(tm_ctx *c) { return reinterpret_cast<OcState *>(c->w.scal + 64); }
+double *scal_at(tm_ctx *c, int i) { return c->w.scal + i; }
+
+int read_scalar(tm_ctx *ctx, const double *dev, double *out) {
+  TM_CUDA(ctx, cudaMemcpyAsync(out, dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return TM_OK;
+}
+
+__global__ void scatter_loads_kernel(const int64_t *idx, const double *val, int64_t n, double *f) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int64_t i = 0; i < n; ++i) f[idx[i]] += val[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+int tm_create(tm_ctx **out, int device, void *cuda_stream) {
+  if (!out) return TM_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0) return TM_ECUDA;
+  if (device < 0 || device >= n) return TM_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return TM_ECUDA;
+  tm_ctx *c = new tm_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+    delete c;
+    return TM_ECUDA;
+  }
+  *out = c;
+  return TM_OK;
+}
+
+int tm_destroy(tm_ctx *ctx) {
+  if (!ctx) return TM_OK;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  release(ctx->dm.owned);
+  release(ctx->w.owned);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  delete ctx;
+  return TM_OK;
+}
+
+int tm_set_stream(tm_ctx *ctx, void *cuda_stream) {
+  if (!ctx) return TM_EINVAL;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return TM_OK;
+}
+
+const char *tm_last_error(tm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
+  TM_CHECK_CTX(ctx);
+  if (!d) return fail(ctx, TM_EINVAL, "null mesh descriptor");
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->has_mesh = false;
+  release(ctx->dm.owned);
+  release(ctx->w.owned);
+  ctx->dm = DeviceMesh();
+  ctx->w = Work();
+  HostMesh &h = ctx->host;
+  std::string msg = build_host_mesh(*d, h);
+  if (!msg.empty()) return fail(ctx, TM_EINVAL, msg);
+
+  DeviceMesh &m = ctx->dm;
+  m.Ne = h.Ne; m.Nn = h.Nn; m.nh = (int64_t)h.hang_node.size(); m.nsh = (int64_t)h.sh_node.size();
+  m.nblk = h.nblk; m.L = h.L; m.max_local = h.max_local;
+  m.fx = h.nx << h.L; m.fy = h.ny << h.L; m.fz = h.nz << h.L;
+  m.h0 = h.h0; m.hmin = std::ldexp(h.h0, -h.L);
+  m.E0 = h.E0; m.Emin = h.Emin; m.penal = h.penal; m.nu = h.nu;
+  m.lam = h.nu / ((1 + h.nu) * (1 - 2 * h.nu));
+  m.mu = 0.5 / (1 + h.nu);
+  m.k0diag = h.K0[0];
+  m.volume = (double)h.nx * h.ny * h.nz * h.h0 * h.h0 * h.h0;
+  m.n_free = 3 * h.n_free_nodes;
+  m.nslot = h.blk_slot.empty() ? 0 : h.blk_slot.back();
+  std::vector<void *> &o = m.owned;
+  int64_t &B = m.bytes;
+  TM_CUDA(ctx, upload(o, B, &m.leaf, h.leaf));
+  TM_CUDA(ctx, upload(o, B, &m.cellmap, h.cellmap));
+  TM_CUDA(ctx, upload(o, B, &m.conn, h.conn));
+  TM_CUDA(ctx, upload(o, B, &m.nflag, h.nflag));
+  TM_CUDA(ctx, upload(o, B, &m.hang_node, h.hang_node));
+  TM_CUDA(ctx, upload(o, B, &m.hang_master, h.hang_master));
+  TM_CUDA(ctx, upload(o, B, &m.blk_elem, h.blk_elem));
+  TM_CUDA(ctx, upload(o, B, &m.blk_node, h.blk_node));
+  TM_CUDA(ctx, upload(o, B, &m.blk_shared, h.blk_shared));
+  TM_CUDA(ctx, upload(o, B, &m.blk_slot, h.blk_slot));
+  TM_CUDA(ctx, upload(o, B, &m.blk_hang, h.blk_hang));
+  TM_CUDA(ctx, upload(o, B, &m.blk_iptr, h.blk_iptr));
+  TM_CUDA(ctx, upload(o, B, &m.blk_inv, h.blk_inv));
+  TM_CUDA(ctx, upload(o, B, &m.lnode, h.lnode));
+  TM_CUDA(ctx, upload(o, B, &m.hent, h.hent));
+  TM_CUDA(ctx, upload(o, B, &m.iptr, h.iptr));
+  TM_CUDA(ctx, upload(o, B, &m.inv, h.inv));
+  TM_CUDA(ctx, upload(o, B, &m.sh_node, h.sh_node));
+  TM_CUDA(ctx, upload(o, B, &m.sh_ptr, h.sh_ptr));
+  TM_CUDA(ctx, upload(o, B, &m.sh_slot, h.sh_slot));
+  TM_CUDA(ctx, upload(o, B, &m.dg_ptr, h.dg_ptr));
+  TM_CUDA(ctx, upload(o, B, &m.dg_elem, h.dg_elem));
+  TM_CUDA(ctx, upload(o, B, &m.dg_q, h.dg_q));
+  TM_CUDA(ctx, upload(o, B, &m.dg_tab, h.dg_tab));
+  // the host keeps only what tm_mesh_tables / tm_build_rhs need
+  std::vector<int32_t>().swap(h.cellmap);
+  std::vector<int32_t>().swap(h.dg_elem);
+  std::vector<uint16_t>().swap(h.dg_q);
+  std::vector<int32_t>().swap(h.dg_ptr);
+
+  Work &w = ctx->w;
+  std::vector<void *> &wo = w.owned;
+  int64_t &WB = w.bytes;
+  const size_t nv = 3 * (size_t)m.Nn;
+  w.nred = (int64_t)m.nblk + 4 * 152 * 8 + 64;
+  TM_CUDA(ctx, alloc(wo, WB, &w.part64, 3 * (size_t)m.nslot));
+  TM_CUDA(ctx, alloc(wo, WB, &w.part32, 3 * (size_t)m.nslot));
+  TM_CUDA(ctx, alloc(wo, WB, &w.ce64, (size_t)m.Ne));
+  TM_CUDA(ctx, alloc(wo, WB, &w.ce32, (size_t)m.Ne));
+  TM_CUDA(ctx, alloc(wo, WB, &w.red, (size_t)w.nred));
+  TM_CUDA(ctx, alloc(wo, WB, &w.scal, (size_t)kScalDoubles));
+  TM_CUDA(ctx, alloc(wo, WB, &w.ticket, (size_t)16));
+  TM_CUDA(ctx, alloc(wo, WB, &w.status, (size_t)16));
+  TM_CUDA(ctx, alloc(wo, WB, &w.r, nv));
+  TM_CUDA(ctx, alloc(wo, WB, &w.p, nv));
+  TM_CUDA(ctx, alloc(wo, WB, &w.q, nv));
+  TM_CUDA(ctx, alloc(wo, WB, &w.dinv, nv));
+  TM_CUDA(ctx, alloc(wo, WB, &w.r32, nv));
+  TM_CUDA(ctx, alloc(wo, WB, &w.p32, nv));
+  TM_CUDA(ctx, alloc(wo, WB, &w.q32, nv));
+  TM_CUDA(ctx, alloc(wo, WB, &w.dinv32, nv));
+  TM_CUDA(ctx, alloc(wo, WB, &w.x32, nv));
+  TM_CUDA(ctx, cudaDeviceSynchronize());
+  ctx->has_mesh = true;
+  if (info) {
+    info->Ne = m.Ne;
+    info->Nn = m.Nn;
+    info->n_hanging = m.nh;
+    info->n_dirichlet = h.n_dirichlet;
+    info->n_free = m.n_free;
+    info->n_blocks = m.nblk;
+    info->max_local = h.max_local;
+    info->n_shared = m.nsh;
+    info->device_bytes = m.bytes + w.bytes;
+  }
+  return TM_OK;
+}
+
+int tm_mesh_tables(tm_ctx *ctx, int64_t *perm, int32_t *node_xyz, int32_t *conn, int32_t *hang_node,
+                   int32_t *hang_master, uint8_t *node_flags) {
+  if (!ctx) return TM_EINVAL;
+  TM_CHECK_MESH(ctx);
+  const HostMesh &h = ctx->host;
+  if (perm) std::memcpy(perm, h.perm.data(), h.perm.size() * sizeof(int64_t));
+  if (node_xyz) std::memcpy(node_xyz, h.node_xyz.data(), h.node_xyz.size() * sizeof(int32_t));
+  if (conn) std::memcpy(conn, h.conn.data(), h.conn.size() * sizeof(int32_t));
+  if (hang_node) std::memcpy(hang_node, h.hang_node.data(), h.hang_node.size() * sizeof(int32_t));
+  if (hang_master) std::memcpy(hang_master, h.hang_master.data(), h.hang_master.size() * sizeof(int32_t));
+  if (node_flags) std::memcpy(node_flags, h.nflag.data(), h.nflag.size());
+  return TM_OK;
+}
+
+int tm_build_rhs(tm_ctx *ctx, int64_t n_loads, const int32_t *node_xyz, const int32_t *comp, const double *val,
+                 double *f_dev) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (n_loads < 0 || (n_loads > 0 && (!node_xyz || !comp || !val)) || !f_dev)
+    return fail(ctx, TM_EINVAL, "bad load arguments");
+  const HostMesh &h = ctx->host;
+  std::vector<int64_t> idx(n_loads);
+  for (int64_t i = 0; i < n_loads; ++i) {
+    const int32_t x = node_xyz[3 * i], y = node_xyz[3 * i + 1], z = node_xyz[3 * i + 2];
+    if (x < 0 || y < 0 || z < 0 || comp[i] < 0 || comp[i] > 2) return fail(ctx, TM_EINVAL, "bad load");
+    const uint64_t k = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+    auto it = std::lower_bound(h.node_key.begin(), h.node_key.end(), k);
+    if (it == h.node_key.end() || *it != k) return fail(ctx, TM_EINVAL, "load point is not a mesh node");
+    idx[i] = 3 * (int64_t)(it - h.node_key.begin()) + comp[i];
+  }
+  const DeviceMesh &m = ctx->dm;
+  TM_CUDA(ctx, cudaMemsetAsync(f_dev, 0, 3 * (size_t)m.Nn * sizeof(double), ctx->stream));
+  if (n_loads > 0) {
+    int64_t *didx = nullptr;
+    double *dval = nullptr;
+    TM_CUDA(ctx, cudaMalloc(&didx, n_loads * sizeof(int64_t)));
+    cudaError_t e = cudaMalloc(&dval, n_loads * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(didx, idx.data(), n_loads * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dval, val, n_loads * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) {
+      scatter_loads_kernel<<<1, 32, 0, ctx->stream>>>(didx, dval, n_loads, f_dev);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(didx);
+    cudaFree(dval);
+    TM_CUDA(ctx, e);
+  }
+  TM_CUDA(ctx, launch_rhs_fold(m, f_dev, ctx->stream));
+  return TM_OK;
+}
+
+int tm_apply_K(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double *y_dev) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!rho_dev || !x_dev || !y_dev) return fail(ctx, TM_EINVAL, "null pointer");
+  TM_CUDA(ctx, launch_coeff(ctx->dm, ctx->w, rho_dev, ctx->stream));
+  TM_CUDA(ctx, launch_apply<double>(ctx->dm, ctx->w.ce64, x_dev, y_dev, ctx->w.part64, nullptr, nullptr, ctx->stream));
+  return TM_OK;
+}
+
+int tm_apply_K_f32(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float *y_dev) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!rho_dev || !x_dev || !y_dev) return fail(ctx, TM_EINVAL, "null pointer");
+  TM_CUDA(ctx, launch_coeff(ctx->dm, ctx->w, rho_dev, ctx->stream));
+  TM_CUDA(ctx, launch_apply<float>(ctx->dm, ctx->w.ce32, x_dev, y_dev, ctx->w.part32, nullptr, nullptr, ctx->stream));
+  return TM_OK;
+}
+
+int tm_jacobi_diag(tm_ctx *ctx, const double *rho_dev, double *d_dev) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!rho_dev || !d_dev) return fail(ctx, TM_EINVAL, "null pointer");
+  TM_CUDA(ctx, launch_coeff(ctx->dm, ctx->w, rho_dev, ctx->stream));
+  TM_CUDA(ctx, launch_diag(ctx->dm, ctx->w.ce64, d_dev, nullptr, nullptr, ctx->stream));
+  return TM_OK;
+}
+
+int tm_expand(tm_ctx *ctx, const double *u_dev, double *u_full_dev) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!u_dev || !u_full_dev) return fail(ctx, TM_EINVAL, "null pointer");
+  TM_CUDA(ctx, launch_expand(ctx->dm, u_dev, u_full_dev, ctx->stream));
+  return TM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- solver drivers
+namespace {
+
+struct HostScalars {
+  SolveScalars s;
+};
+
+int init_run(tm_ctx *ctx, double stop_ratio2, double stop_abs_rr, int max_it) {
+  SolveScalars s;
+  std::memset(&s, 0, sizeof(s));
+  s.stop_ratio2 = stop_ratio2;
+  s.stop_abs_rr = stop_abs_rr;
+  s.max_it = max_it;
+  TM_CUDA(ctx, cudaMemcpyAsync(solve_scalars(ctx), &s, sizeof(s), cudaMemcpyHostToDevice, ctx->stream));
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return TM_OK;
+}
+
+int read_run(tm_ctx *ctx, SolveScalars *s) {
+  TM_CUDA(ctx, cudaMemcpyAsync(s, solve_scalars(ctx), sizeof(*s), cudaMemcpyDeviceToHost, ctx->stream));
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return TM_OK;
+}
+
+// Enqueue `count` CG iterations on vectors of type T (operator coefficient ce,
+// partial buffer part), solution x of type TX.
+template <typename TX, typename T>
+int enqueue_iterations(tm_ctx *ctx, int count, const T *ce, T *part, TX *x, T *r, T *p, T *q, const T *dinv) {
+  const DeviceMesh &m = ctx->dm;
+  Work &w = ctx->w;
+  SolveScalars *sc = solve_scalars(ctx);
+  const int64_t n = 3 * m.Nn;
+  const int nshared_grid = shared_grid(m.nsh + m.nh);
+  for (int k = 0; k < count; ++k) {
+    TM_CUDA(ctx, launch_apply<T>(m, ce, p, q, part, w.red, &sc->done, ctx->stream));
+    TM_CUDA(ctx, launch_alpha(w.red, m.nblk + nshared_grid, sc, ctx->stream));
+    TM_CUDA(ctx, launch_update<TX, T>(x, p, q, r, dinv, n, sc, w.red, w.ticket, ctx->stream));
+    TM_CUDA(ctx, launch_pupdate<T>(p, r, dinv, n, sc, ctx->stream));
+  }
+  return TM_OK;
+}
+
+template <typename TX, typename T>
+int run_cg(tm_ctx *ctx, int check_every, int *iters_out, int *nonfinite, const T *ce, T *part, TX *x, T *r, T *p,
+           T *q, const T *dinv) {
+  SolveScalars s;
+  int rc = read_run(ctx, &s);
+  if (rc) return rc;
+  while (!s.done) {
+    rc = enqueue_iterations<TX, T>(ctx, check_every, ce, part, x, r, p, q, dinv);
+    if (rc) return rc;
+    rc = read_run(ctx, &s);
+    if (rc) return rc;
+  }
+  *iters_out = s.it;
+  *nonfinite = s.nonfinite;
+  return TM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double *u_dev, const tm_solve_opts *opts,
+                 tm_solve_stats *stats) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!rho_dev || !f_dev || !u_dev || !opts) return fail(ctx, TM_EINVAL, "null pointer");
+  if (!(opts->rtol > 0) || opts->max_iter < 1) return fail(ctx, TM_EINVAL, "need rtol > 0 and max_iter >= 1");
+  if (opts->precision != TM_PREC_FP64 && opts->precision != TM_PREC_MIXED)
+    return fail(ctx, TM_EINVAL, "unknown precision");
+  const DeviceMesh &m = ctx->dm;
+  Work &w = ctx->w;
+  cudaStream_t st = ctx->stream;
+  const int64_t n = 3 * m.Nn;
+  const int check = opts->check_every > 0 ? opts->check_every : 32;
+  tm_solve_stats out;
+  std::memset(&out, 0, sizeof(out));
+
+  TM_CUDA(ctx, cudaEventRecord(ctx->ev0, st));
+  TM_CUDA(ctx, launch_coeff(m, w, rho_dev, st));
+  TM_CUDA(ctx, launch_diag(m, w.ce64, nullptr, w.dinv, w.dinv32, st));
+  TM_CUDA(ctx, launch_mask(m.nflag, u_dev, m.Nn, st));
+  double *ff_dev = scal_at(ctx, 82), *rr_dev = scal_at(ctx, 81);
+  TM_CUDA(ctx, launch_residual64(f_dev, nullptr, nullptr, n, ff_dev, w.red, w.ticket + 1, st));
+  double ff = 0;
+  int rc = read_scalar(ctx, ff_dev, &ff);
+  if (rc) return rc;
+  if (!std::isfinite(ff)) return fail(ctx, TM_ENONFINITE, "non-finite load vector");
+  int status = TM_OK;
+  if (ff == 0.0) {
+    TM_CUDA(ctx, cudaMemsetAsync(u_dev, 0, n * sizeof(double), st));
+    out.rel_residual = 0.0;
+  } else if (opts->precision == TM_PREC_FP64) {
+    const double target = opts->rtol * opts->rtol * ff;
+    int left = opts->max_iter;
+    double rel = 0;
+    for (int restart = 0; restart < 8; ++restart) {
+      // r = f - A u (true residual), p = Dinv r
+      TM_CUDA(ctx, launch_apply<double>(m, w.ce64, u_dev, w.q, w.part64, nullptr, nullptr, st));
+      out.fp64_applies++;
+      rc = init_run(ctx, 0.0, target, left);
+      if (rc) return rc;
+      TM_CUDA(ctx, launch_start<double>(f_dev, w.q, 1.0, w.r, w.p, w.dinv, n, solve_scalars(ctx), w.red, w.ticket + 2, st));
+      int it = 0, nf = 0;
+      rc = run_cg<double, double>(ctx, check, &it, &nf, w.ce64, w.part64, u_dev, w.r, w.p, w.q, w.dinv);
+      if (rc) return rc;
+      out.iterations += it;
+      out.fp64_applies += it;
+      left -= it;
+      if (nf) return fail(ctx, TM_ENONFINITE, "non-finite value in CG");
+      // verify with the true residual
+      TM_CUDA(ctx, launch_apply<double>(m, w.ce64, u_dev, w.q, w.part64, nullptr, nullptr, st));
+      out.fp64_applies++;
+      TM_CUDA(ctx, launch_residual64(f_dev, w.q, nullptr, n, rr_dev, w.red, w.ticket + 1, st));
+      double rr = 0;
+      rc = read_scalar(ctx, rr_dev, &rr);
+      if (rc) return rc;
+      rel = std::sqrt(rr / ff);
+      if (rel <= opts->rtol || left <= 0) break;
+    }
+    out.sweeps = 1;
+    out.rel_residual = rel;
+    if (rel > opts->rtol) status = TM_ENOTCONVERGED;
+  } else {
+    // FP64 iterative refinement around FP32-operator CG sweeps.
+    const double inner = opts->inner_rtol > 0 ? opts->inner_rtol : 1e-3;
+    int left = opts->max_iter;
+    double rel = 0;
+    for (int sweep = 0; sweep < 64; ++sweep) {
+      TM_CUDA(ctx, launch_apply<double>(m, w.ce64, u_dev, w.q, w.part64, nullptr, nullptr, st));
+      out.fp64_applies++;
+      TM_CUDA(ctx, launch_residual64(f_dev, w.q, w.r, n, rr_dev, w.red, w.ticket + 1, st));
+      double rr = 0;
+      rc = read_scalar(ctx, rr_dev, &rr);
+      if (rc) return rc;
+      if (!std::isfinite(rr)) return fail(ctx, TM_ENONFINITE, "non-finite residual");
+      rel = std::sqrt(rr / ff);
+      if (rel <= opts->rtol || left <= 0) break;
+      out.sweeps++;
+      const double scale = 1.0 / std::sqrt(rr);
+      // stop the sweep at the inner reduction, or a little past the outer target
+      const double abs_stop = 0.25 * opts->rtol * opts->rtol * ff / rr;
+      rc = init_run(ctx, inner * inner, abs_stop, left);
+      if (rc) return rc;
+      TM_CUDA(ctx, cudaMemsetAsync(w.x32, 0, n * sizeof(float), st));
+      TM_CUDA(ctx, launch_start<float>(w.r, nullptr, scale, w.r32, w.p32, w.dinv32, n, solve_scalars(ctx), w.red,
+                                       w.ticket + 2, st));
+      int it = 0, nf = 0;
+      rc = run_cg<float, float>(ctx, check, &it, &nf, w.ce32, w.part32, w.x32, w.r32, w.p32, w.q32, w.dinv32);
+      if (rc) return rc;
+      out.iterations += it;
+      out.fp32_applies += it;
+      left -= it;
+      if (nf) return fail(ctx, TM_ENONFINITE, "non-finite value in the FP32 sweep");
+      TM_CUDA(ctx, launch_correct(u_dev, w.x32, 1.0 / scale, n, st));
+    }
+    out.rel_residual = rel;
+    if (rel > opts->rtol) status = TM_ENOTCONVERGED;
+  }
+  TM_CUDA(ctx, cudaEventRecord(ctx->ev1, st));
+  TM_CUDA(ctx, cudaEventSynchronize(ctx->ev1));
+  float ms = 0;
+  TM_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+  out.seconds = ms * 1e-3;
+  if (stats) *stats = out;
+  if (status == TM_ENOTCONVERGED) return fail(ctx, status, "max_iter reached before rtol");
+  return status;
+}
+
+int tm_sensitivity(tm_ctx *ctx, const double *rho_dev, const double *u_full_dev, double *dc_dev,
+                   double *compliance_out) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!rho_dev || !u_full_dev || !dc_dev) return fail(ctx, TM_EINVAL, "null pointer");
+  double *cdev = scal_at(ctx, 80);
+  TM_CUDA(ctx, launch_sensitivity(ctx->dm, rho_dev, u_full_dev, dc_dev, ctx->w.red, ctx->w.ticket + 3, cdev,
+                                  ctx->stream));
+  if (compliance_out) return read_scalar(ctx, cdev, compliance_out);
+  return TM_OK;
+}
+
+int tm_filter(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double rmin, int mode, double *out_dev) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!rho_dev || !x_dev || !out_dev) return fail(ctx, TM_EINVAL, "null pointer");
+  if (mode != 0 && mode != 1) return fail(ctx, TM_EINVAL, "mode must be 0 or 1");
+  if (!(rmin > 0) || rmin > 4.0 * ctx->dm.hmin) return fail(ctx, TM_EINVAL, "rmin must be in (0, 4 h_min]");
+  TM_CUDA(ctx, launch_filter(ctx->dm, rho_dev, x_dev, rmin, mode, out_dev, ctx->stream));
+  return TM_OK;
+}
+
+int tm_oc_update(tm_ctx *ctx, const double *rho_dev, const double *dc_dev, double volfrac, double move, double eta,
+                 double rho_min, double *rho_new_dev, double *change_out) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!rho_dev || !dc_dev || !rho_new_dev) return fail(ctx, TM_EINVAL, "null pointer");
+  if (!(volfrac > 0 && volfrac <= 1) || !(move > 0) || !(eta > 0) || !(rho_min > 0 && rho_min < 1))
+    return fail(ctx, TM_EINVAL, "bad OC parameters");
+  OcState s;
+  std::memset(&s, 0, sizeof(s));
+  s.target = volfrac * ctx->dm.volume;
+  s.tol = 1e-12;
+  TM_CUDA(ctx, cudaMemcpyAsync(oc_state(ctx), &s, sizeof(s), cudaMemcpyHostToDevice, ctx->stream));
+  TM_CUDA(ctx, launch_oc(ctx->dm, rho_dev, dc_dev, eta, move, rho_min, rho_new_dev, ctx->w.red, ctx->w.ticket + 4,
+                         oc_state(ctx), 200, ctx->stream));
+  if (change_out) return read_scalar(ctx, &oc_state(ctx)->change, change_out);
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return TM_OK;
+}
+
+}  // extern "C"

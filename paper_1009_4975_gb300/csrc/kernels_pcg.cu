@@ -1,0 +1,228 @@
+// Fused vector kernels of Jacobi-preconditioned CG (paper Sec. 5: the diagonal
+// rescaling D^-1/2 K D^-1/2 applied implicitly as the preconditioner) with FP64
+// reductions finalised on the device, so the iteration needs no host round trip.
+//
+// Iteration (x: solution, z = Dinv r is never stored):
+//   q = A p ; pq = p.q (fused into the operator's second pass)      alpha = rz / pq
+//   x += alpha p ; r -= alpha q ; rz' = r.Dinv r ; rr = r.r          beta = rz' / rz
+//   p = Dinv r + beta p
+// Every kernel returns immediately once the device flag `done` is set, so a
+// fixed batch of iterations can be enqueued (or graph-captured) ahead of the
+// host's convergence check.
+#include <cuda_runtime.h>
+
+#include "pcg.cuh"
+#include "reduce.cuh"
+#include "tm_internal.h"
+
+namespace amr {
+
+constexpr int kVecThreads = 256;
+
+__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+
+// pq = sum of operator partials; alpha = rz / pq.
+__global__ void alpha_kernel(const double *partials, int n, SolveScalars *sc) {
+  if (sc->done) return;
+  const double pq = sum_partials<kVecThreads>(partials, n);
+  if (threadIdx.x == 0) {
+    sc->pq = pq;
+    sc->alpha = sc->rz / pq;
+    if (!finite(pq) || !finite(sc->alpha) || pq <= 0.0) {
+      sc->nonfinite = 1;
+      sc->done = 1;
+    }
+  }
+}
+
+template <typename TX, typename T>
+__global__ void __launch_bounds__(kVecThreads) update_kernel(TX *x, const T *p, const T *q, T *r, const T *dinv,
+                                                             int64_t n, SolveScalars *sc, double *partials,
+                                                             unsigned int *ticket) {
+  if (sc->done) return;
+  const double alpha = sc->alpha;
+  const T a = (T)alpha;
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += (TX)alpha * (TX)p[i];
+    const T ri = r[i] - a * q[i];
+    r[i] = ri;
+    const double rd = (double)ri;
+    rz += rd * (double)(dinv[i] * ri);
+    rr += rd * rd;
+  }
+  block_sum2<kVecThreads>(rz, rr);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = rz;
+    partials[2 * blockIdx.x + 1] = rr;
+  }
+  if (last_cta(ticket)) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += kVecThreads) {
+      s0 += ((volatile double *)partials)[2 * i];
+      s1 += ((volatile double *)partials)[2 * i + 1];
+    }
+    block_sum2<kVecThreads>(s0, s1);
+    if (threadIdx.x == 0) {
+      sc->beta = s0 / sc->rz;
+      sc->rz = s0;
+      sc->rr = s1;
+      sc->it += 1;
+      if (!finite(s0) || !finite(s1)) {
+        sc->nonfinite = 1;
+        sc->done = 1;
+      } else if (s1 <= sc->stop_rr || sc->it >= sc->max_it) {
+        sc->done = 1;
+        sc->last_beta_skipped = 1;
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) pupdate_kernel(T *p, const T *r, const T *dinv, int64_t n,
+                                                              SolveScalars *sc) {
+  if (sc->done) return;
+  const T beta = (T)sc->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = dinv[i] * r[i] + beta * p[i];
+}
+
+// r = s * (f - q) (q = A x0); p = Dinv r; rz, rr; stop threshold from rr0.
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) start_kernel(const double *f, const double *q, double scale, T *r,
+                                                            T *p, const T *dinv, int64_t n, SolveScalars *sc,
+                                                            double *partials, unsigned int *ticket) {
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T ri = (T)(scale * (f[i] - (q ? q[i] : 0.0)));
+    r[i] = ri;
+    const T zi = dinv[i] * ri;
+    p[i] = zi;
+    rz += (double)ri * (double)zi;
+    rr += (double)ri * (double)ri;
+  }
+  block_sum2<kVecThreads>(rz, rr);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = rz;
+    partials[2 * blockIdx.x + 1] = rr;
+  }
+  if (last_cta(ticket)) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += kVecThreads) {
+      s0 += ((volatile double *)partials)[2 * i];
+      s1 += ((volatile double *)partials)[2 * i + 1];
+    }
+    block_sum2<kVecThreads>(s0, s1);
+    if (threadIdx.x == 0) {
+      sc->rz = s0;
+      sc->rr = s1;
+      sc->rr0 = s1;
+      sc->it = 0;
+      sc->nonfinite = 0;
+      sc->last_beta_skipped = 0;
+      sc->stop_rr = sc->stop_ratio2 * s1;
+      if (sc->stop_abs_rr > sc->stop_rr) sc->stop_rr = sc->stop_abs_rr;
+      sc->done = (s1 <= sc->stop_rr || s1 == 0.0) ? 1 : 0;
+      if (!finite(s0) || !finite(s1)) {
+        sc->nonfinite = 1;
+        sc->done = 1;
+      }
+    }
+  }
+}
+
+// r64 = f - q; rr = r.r (FP64) for the outer residual of iterative refinement.
+__global__ void __launch_bounds__(kVecThreads) residual64_kernel(const double *f, const double *q, double *r,
+                                                                 int64_t n, double *out, double *partials,
+                                                                 unsigned int *ticket) {
+  double rr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = f[i] - (q ? q[i] : 0.0);
+    if (r) r[i] = ri;
+    rr += ri * ri;
+  }
+  rr = block_sum<kVecThreads>(rr);
+  if (threadIdx.x == 0) partials[blockIdx.x] = rr;
+  if (last_cta(ticket)) {
+    const double s = sum_partials<kVecThreads>(partials, gridDim.x);
+    if (threadIdx.x == 0) *out = s;
+  }
+}
+
+// u += s * d (FP64 accumulate of an FP32 correction); d is cleared.
+__global__ void correct_kernel(double *u, float *d, double s, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    u[i] += s * (double)d[i];
+    d[i] = 0.0f;
+  }
+}
+
+__global__ void mask_kernel(const uint8_t *nflag, double *u, int64_t Nn) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Nn; k += (int64_t)gridDim.x * blockDim.x)
+    if (nflag[k]) u[3 * k] = u[3 * k + 1] = u[3 * k + 2] = 0.0;
+}
+
+int vec_grid(int64_t n) {
+  int64_t g = (n + kVecThreads - 1) / kVecThreads;
+  if (g < 1) g = 1;
+  if (g > 152 * 8) g = 152 * 8;
+  return (int)g;
+}
+
+cudaError_t launch_alpha(const double *partials, int n, SolveScalars *sc, cudaStream_t s) {
+  alpha_kernel<<<1, kVecThreads, 0, s>>>(partials, n, sc);
+  return cudaGetLastError();
+}
+
+template <typename TX, typename T>
+cudaError_t launch_update(TX *x, const T *p, const T *q, T *r, const T *dinv, int64_t n, SolveScalars *sc,
+                          double *partials, unsigned int *ticket, cudaStream_t s) {
+  update_kernel<TX, T><<<vec_grid(n), kVecThreads, 0, s>>>(x, p, q, r, dinv, n, sc, partials, ticket);
+  return cudaGetLastError();
+}
+template cudaError_t launch_update<double, double>(double *, const double *, const double *, double *,
+                                                   const double *, int64_t, SolveScalars *, double *,
+                                                   unsigned int *, cudaStream_t);
+template cudaError_t launch_update<float, float>(float *, const float *, const float *, float *, const float *,
+                                                 int64_t, SolveScalars *, double *, unsigned int *, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_pupdate(T *p, const T *r, const T *dinv, int64_t n, SolveScalars *sc, cudaStream_t s) {
+  pupdate_kernel<T><<<vec_grid(n), kVecThreads, 0, s>>>(p, r, dinv, n, sc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_pupdate<double>(double *, const double *, const double *, int64_t, SolveScalars *,
+                                            cudaStream_t);
+template cudaError_t launch_pupdate<float>(float *, const float *, const float *, int64_t, SolveScalars *,
+                                           cudaStream_t);
+
+template <typename T>
+cudaError_t launch_start(const double *f, const double *q, double scale, T *r, T *p, const T *dinv, int64_t n,
+                         SolveScalars *sc, double *partials, unsigned int *ticket, cudaStream_t s) {
+  start_kernel<T><<<vec_grid(n), kVecThreads, 0, s>>>(f, q, scale, r, p, dinv, n, sc, partials, ticket);
+  return cudaGetLastError();
+}
+template cudaError_t launch_start<double>(const double *, const double *, double, double *, double *,
+                                          const double *, int64_t, SolveScalars *, double *, unsigned int *,
+                                          cudaStream_t);
+template cudaError_t launch_start<float>(const double *, const double *, double, float *, float *, const float *,
+                                         int64_t, SolveScalars *, double *, unsigned int *, cudaStream_t);
+
+cudaError_t launch_residual64(const double *f, const double *q, double *r, int64_t n, double *out, double *partials,
+                              unsigned int *ticket, cudaStream_t s) {
+  residual64_kernel<<<vec_grid(n), kVecThreads, 0, s>>>(f, q, r, n, out, partials, ticket);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_correct(double *u, float *d, double scale, int64_t n, cudaStream_t s) {
+  correct_kernel<<<vec_grid(n), kVecThreads, 0, s>>>(u, d, scale, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask(const uint8_t *nflag, double *u, int64_t Nn, cudaStream_t s) {
+  mask_kernel<<<vec_grid(Nn), kVecThreads, 0, s>>>(nflag, u, Nn);
+  return cudaGetLastError();
+}
+
+}  // namespace amr

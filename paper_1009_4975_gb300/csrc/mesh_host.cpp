@@ -1,0 +1,585 @@
+// Host construction of the mesh tables of paper Sec. 6 (hanging-node
+// interpolation, Eq. 6) for a 2:1-balanced octree leaf set, plus the block,
+// colour and diagonal tables the device kernels use.  Integer work only
+// (except the reference element matrix and the diagonal coefficient table).
+//
+// Algorithm (independent of any other implementation in this repository):
+//  1. leaves sorted by Morton key with an LSD radix sort; aligned octants occupy
+//     contiguous Morton intervals, so disjointness is "each interval ends before
+//     the next begins" and coverage is "the lengths add up to the box";
+//  2. nodes = radix-sorted unique corner keys;
+//  3. balance = for every node, the leaves owning the <= 8 finest cells around it
+//     differ by at most one level (dense finest-grid owner map);
+//  4. on a balanced mesh a node hangs exactly when it is the midpoint of a leaf
+//     edge (masters: the edge ends, weight 1/2) or the centre of a leaf face
+//     (masters: the face corners, weight 1/4); each leaf probes its 12 edge
+//     midpoints and 6 face centres against the node set.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+
+#include "tm_internal.h"
+
+namespace amr {
+
+static inline uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x1fffffu;
+  x = (x | (x << 32)) & 0x1f00000000ffffull;
+  x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+  return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+
+// LSD radix sort of keys, returning the permutation (stable).
+static std::vector<int64_t> radix_order(const std::vector<uint64_t> &key) {
+  const size_t n = key.size();
+  uint64_t mx = 0;
+  for (uint64_t k : key) mx |= k;
+  int bits = 0;
+  while (bits < 64 && (mx >> bits)) ++bits;
+  std::vector<int64_t> idx(n), tmp(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  const int R = 11, B = 1 << R;
+  std::vector<size_t> cnt(B + 1);
+  for (int sh = 0; sh < bits; sh += R) {
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (size_t i = 0; i < n; ++i) cnt[((key[idx[i]] >> sh) & (B - 1)) + 1]++;
+    for (int b = 0; b < B; ++b) cnt[b + 1] += cnt[b];
+    for (size_t i = 0; i < n; ++i) tmp[cnt[(key[idx[i]] >> sh) & (B - 1)]++] = idx[i];
+    idx.swap(tmp);
+  }
+  return idx;
+}
+
+void reference_stiffness(double nu, double *K0) {
+  // K0 = sum over 2x2x2 Gauss points of B^T D B / 8 on the unit cube, E = 1.
+  const double lam = nu / ((1 + nu) * (1 - 2 * nu)), mu = 0.5 / (1 + nu);
+  double D[6][6] = {};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) D[a][b] = lam + (a == b ? 2 * mu : 0);
+  D[3][3] = D[4][4] = D[5][5] = mu;
+  const double g = 1.0 / std::sqrt(3.0);
+  const double pts[2] = {0.5 * (1 - g), 0.5 * (1 + g)};
+  std::fill(K0, K0 + 576, 0.0);
+  for (int qa = 0; qa < 2; ++qa)
+    for (int qb = 0; qb < 2; ++qb)
+      for (int qc = 0; qc < 2; ++qc) {
+        const double xi[3] = {pts[qa], pts[qb], pts[qc]};
+        double B[6][24] = {};
+        for (int k = 0; k < 8; ++k) {
+          const int i = k & 1, j = (k >> 1) & 1, m = (k >> 2) & 1;
+          const double f0 = i ? xi[0] : 1 - xi[0], f1 = j ? xi[1] : 1 - xi[1], f2 = m ? xi[2] : 1 - xi[2];
+          const double d0 = i ? 1 : -1, d1 = j ? 1 : -1, d2 = m ? 1 : -1;
+          const double gx = d0 * f1 * f2, gy = f0 * d1 * f2, gz = f0 * f1 * d2;
+          B[0][3 * k] = gx;
+          B[1][3 * k + 1] = gy;
+          B[2][3 * k + 2] = gz;
+          B[3][3 * k] = gy;
+          B[3][3 * k + 1] = gx;
+          B[4][3 * k + 1] = gz;
+          B[4][3 * k + 2] = gy;
+          B[5][3 * k] = gz;
+          B[5][3 * k + 2] = gx;
+        }
+        double DB[6][24];
+        for (int a = 0; a < 6; ++a)
+          for (int c = 0; c < 24; ++c) {
+            double s = 0;
+            for (int b = 0; b < 6; ++b) s += D[a][b] * B[b][c];
+            DB[a][c] = s;
+          }
+        for (int r = 0; r < 24; ++r)
+          for (int c = 0; c < 24; ++c) {
+            double s = 0;
+            for (int a = 0; a < 6; ++a) s += B[a][r] * DB[a][c];
+            K0[r * 24 + c] += 0.125 * s;
+          }
+      }
+}
+
+static inline int64_t find_key(const std::vector<uint64_t> &keys, uint64_t k) {
+  auto it = std::lower_bound(keys.begin(), keys.end(), k);
+  if (it == keys.end() || *it != k) return -1;
+  return it - keys.begin();
+}
+
+std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
+  m = HostMesh();
+  if (d.nx < 1 || d.ny < 1 || d.nz < 1) return "base grid must be at least 1x1x1";
+  if (d.max_level < 0 || d.max_level > 12) return "max_level must be in [0, 12]";
+  if (!(d.h0 > 0)) return "h0 must be positive";
+  if (d.n_leaves < 1 || !d.leaves) return "no leaves";
+  if (!(d.nu > -1.0 && d.nu < 0.5)) return "Poisson ratio must be in (-1, 0.5)";
+  if (!(d.E0 > d.Emin && d.Emin >= 0)) return "need E0 > Emin >= 0";
+  if (!(d.penal >= 1)) return "penalty must be >= 1";
+  const int L = d.max_level;
+  const int64_t fx = (int64_t)d.nx << L, fy = (int64_t)d.ny << L, fz = (int64_t)d.nz << L;
+  if (fx >= (1 << 20) || fy >= (1 << 20) || fz >= (1 << 20)) return "finest grid too large";
+  if (fx * fy * fz > (int64_t)1 << 31) return "finest grid has more than 2^31 cells";
+  m.nx = d.nx; m.ny = d.ny; m.nz = d.nz; m.L = L; m.h0 = d.h0;
+  m.dirichlet_faces = d.dirichlet_faces;
+  m.E0 = d.E0; m.Emin = d.Emin; m.nu = d.nu; m.penal = d.penal;
+  const int64_t Ne = d.n_leaves;
+  m.Ne = Ne;
+
+  // ---- 1. validate, sort, disjoint + cover
+  std::vector<uint64_t> key(Ne);
+  for (int64_t e = 0; e < Ne; ++e) {
+    const int32_t *l = d.leaves + 4 * e;
+    if (l[3] < 0 || l[3] > L) return "leaf level out of range";
+    const int64_t s = (int64_t)1 << (L - l[3]);
+    for (int a = 0; a < 3; ++a) {
+      const int64_t ext = a == 0 ? fx : (a == 1 ? fy : fz);
+      if (l[a] < 0 || l[a] + s > ext) return "leaf outside the domain";
+      if (l[a] % s) return "leaf anchor not aligned to its size";
+    }
+    key[e] = morton3(l[0], l[1], l[2]);
+  }
+  m.perm = radix_order(key);
+  m.leaf.resize(4 * Ne);
+  int64_t covered = 0;
+  for (int64_t i = 0; i < Ne; ++i) {
+    const int32_t *l = d.leaves + 4 * m.perm[i];
+    std::memcpy(&m.leaf[4 * i], l, 16);
+    const int64_t s = (int64_t)1 << (L - l[3]);
+    covered += s * s * s;
+    if (i + 1 < Ne) {
+      const uint64_t end = key[m.perm[i]] + (uint64_t)(s * s * s);
+      if (end > key[m.perm[i + 1]]) return "leaves overlap";
+    }
+  }
+  if (covered != fx * fy * fz) return "leaves do not cover the domain";
+
+  // ---- 2. nodes
+  std::vector<uint64_t> ckey(8 * Ne);
+  for (int64_t e = 0; e < Ne; ++e) {
+    const int32_t *l = &m.leaf[4 * e];
+    const int32_t s = 1 << (L - l[3]);
+    for (int k = 0; k < 8; ++k)
+      ckey[8 * e + k] = morton3(l[0] + s * (k & 1), l[1] + s * ((k >> 1) & 1), l[2] + s * ((k >> 2) & 1));
+  }
+  {
+    std::vector<int64_t> ord = radix_order(ckey);
+    m.conn.resize(8 * Ne);
+    int64_t nn = -1;
+    uint64_t prev = ~0ull;
+    for (int64_t i = 0; i < 8 * Ne; ++i) {
+      const uint64_t k = ckey[ord[i]];
+      if (k != prev) {
+        ++nn;
+        m.node_key.push_back(k);
+        prev = k;
+      }
+      m.conn[ord[i]] = (int32_t)nn;
+    }
+    m.Nn = nn + 1;
+  }
+  const int64_t Nn = m.Nn;
+  m.node_xyz.resize(3 * Nn);
+  for (int64_t e = 0; e < Ne; ++e) {
+    const int32_t *l = &m.leaf[4 * e];
+    const int32_t s = 1 << (L - l[3]);
+    for (int k = 0; k < 8; ++k) {
+      const int32_t n = m.conn[8 * e + k];
+      m.node_xyz[3 * n] = l[0] + s * (k & 1);
+      m.node_xyz[3 * n + 1] = l[1] + s * ((k >> 1) & 1);
+      m.node_xyz[3 * n + 2] = l[2] + s * ((k >> 2) & 1);
+    }
+  }
+
+  // ---- 3. balance via a dense owner map of the finest cells
+  {
+    std::vector<int32_t> &owner = m.cellmap;
+    owner.assign((size_t)(fx * fy * fz), 0);
+    for (int64_t e = 0; e < Ne; ++e) {
+      const int32_t *l = &m.leaf[4 * e];
+      const int32_t s = 1 << (L - l[3]);
+      for (int z = 0; z < s; ++z)
+        for (int y = 0; y < s; ++y) {
+          int32_t *row = &owner[((size_t)(l[2] + z) * fy + (l[1] + y)) * fx + l[0]];
+          for (int x = 0; x < s; ++x) row[x] = (int32_t)e;
+        }
+    }
+    for (int64_t n = 0; n < Nn; ++n) {
+      const int32_t px = m.node_xyz[3 * n], py = m.node_xyz[3 * n + 1], pz = m.node_xyz[3 * n + 2];
+      int lo = 1 << 30, hi = -1;
+      for (int c = 0; c < 8; ++c) {
+        const int64_t cx = px - 1 + (c & 1), cy = py - 1 + ((c >> 1) & 1), cz = pz - 1 + ((c >> 2) & 1);
+        if (cx < 0 || cy < 0 || cz < 0 || cx >= fx || cy >= fy || cz >= fz) continue;
+        const int lv = m.leaf[4 * owner[((size_t)cz * fy + cy) * fx + cx] + 3];
+        lo = std::min(lo, lv);
+        hi = std::max(hi, lv);
+      }
+      if (hi - lo > 1) return "mesh is not 2:1 balanced";
+    }
+  }
+
+  // ---- 4. hanging nodes: edge midpoints and face centres that are nodes
+  m.hang_index.assign(Nn, -1);
+  std::vector<std::array<int32_t, 4>> masters;
+  {
+    static const int edges[12][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3},
+                                     {4, 6}, {5, 7}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+    static const int faces[6][4] = {{0, 2, 4, 6}, {1, 3, 5, 7}, {0, 1, 4, 5},
+                                    {2, 3, 6, 7}, {0, 1, 2, 3}, {4, 5, 6, 7}};
+    for (int64_t e = 0; e < Ne; ++e) {
+      const int32_t *l = &m.leaf[4 * e];
+      const int32_t s = 1 << (L - l[3]);
+      if (s < 2) continue;
+      const int32_t *cn = &m.conn[8 * e];
+      auto probe = [&](const int *cs, int nc) -> std::string {
+        int64_t x = 0, y = 0, z = 0;
+        for (int i = 0; i < nc; ++i) {
+          x += m.node_xyz[3 * cn[cs[i]]];
+          y += m.node_xyz[3 * cn[cs[i]] + 1];
+          z += m.node_xyz[3 * cn[cs[i]] + 2];
+        }
+        x /= nc; y /= nc; z /= nc;
+        const int64_t n = find_key(m.node_key, morton3((uint32_t)x, (uint32_t)y, (uint32_t)z));
+        if (n < 0) return "";
+        std::array<int32_t, 4> ms = {-1, -1, -1, -1};
+        for (int i = 0; i < nc; ++i) ms[i] = cn[cs[i]];
+        std::sort(ms.begin(), ms.begin() + nc);
+        if (m.hang_index[n] < 0) {
+          m.hang_index[n] = (int32_t)masters.size();
+          masters.push_back(ms);
+          m.hang_node.push_back((int32_t)n);
+        } else if (masters[m.hang_index[n]] != ms) {
+          return "inconsistent hanging-node constraints";
+        }
+        return "";
+      };
+      for (auto &ed : edges) {
+        std::string r = probe(ed, 2);
+        if (!r.empty()) return r;
+      }
+      for (auto &fc : faces) {
+        std::string r = probe(fc, 4);
+        if (!r.empty()) return r;
+      }
+    }
+    // ascending node order
+    std::vector<int32_t> ord(m.hang_node.size());
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return m.hang_node[a] < m.hang_node[b]; });
+    std::vector<int32_t> hn(ord.size());
+    m.hang_master.resize(4 * ord.size());
+    for (size_t i = 0; i < ord.size(); ++i) {
+      hn[i] = m.hang_node[ord[i]];
+      for (int j = 0; j < 4; ++j) m.hang_master[4 * i + j] = masters[ord[i]][j];
+      m.hang_index[hn[i]] = (int32_t)i;
+    }
+    m.hang_node.swap(hn);
+    for (size_t i = 0; i < m.hang_node.size(); ++i)
+      for (int j = 0; j < 4; ++j) {
+        const int32_t mm = m.hang_master[4 * i + j];
+        if (mm >= 0 && m.hang_index[mm] >= 0) return "constraint chain (master is hanging)";
+      }
+  }
+
+  // ---- 5. flags
+  m.nflag.assign(Nn, 0);
+  const int64_t ext[3] = {fx, fy, fz};
+  for (int64_t n = 0; n < Nn; ++n) {
+    for (int f = 0; f < 6; ++f)
+      if ((d.dirichlet_faces >> f) & 1) {
+        const int a = f / 2, side = f % 2;
+        if (m.node_xyz[3 * n + a] == (side ? ext[a] : 0)) m.nflag[n] |= 1;
+      }
+    if (m.hang_index[n] >= 0) m.nflag[n] |= 2;
+    if (m.nflag[n] & 1) m.n_dirichlet++;
+    if (!m.nflag[n]) m.n_free_nodes++;
+  }
+
+  m.K0.resize(576);
+  reference_stiffness(d.nu, m.K0.data());
+
+  // ---- 6. operator blocks: chunks of consecutive elements, local nodes, colours
+  // Local nodes of a block: its regular ("effective") nodes -- regular corners
+  // and masters of hanging corners -- shared ones first, then the hanging
+  // corners it uses.  Elements address corners by local id; the hanging slots
+  // are filled from their masters before the element pass and folded back into
+  // them after it.
+  std::vector<int32_t> nblocks_of(Nn, 0);       // number of blocks touching a regular node
+  struct Blk { int64_t e0, e1; };
+  std::vector<Blk> blks;
+  {
+    std::vector<int32_t> mark(Nn, -1);
+    auto count_local = [&](int64_t e0, int64_t e1, int tag) {
+      int cnt = 0;
+      for (int64_t e = e0; e < e1; ++e)
+        for (int k = 0; k < 8; ++k) {
+          const int32_t n = m.conn[8 * e + k];
+          if (mark[n] != tag) { mark[n] = tag; ++cnt; }
+          const int32_t h = m.hang_index[n];
+          if (h >= 0)
+            for (int j = 0; j < 4; ++j) {
+              const int32_t mm = m.hang_master[4 * h + j];
+              if (mm >= 0 && mark[mm] != tag) { mark[mm] = tag; ++cnt; }
+            }
+        }
+      return cnt;
+    };
+    int tag = 0;
+    int64_t e0 = 0;
+    while (e0 < Ne) {
+      int64_t len = std::min<int64_t>(kBlockElems, Ne - e0);
+      while (len > 1 && count_local(e0, e0 + len, tag++) > kMaxLocal) len = (len + 1) / 2;
+      if (count_local(e0, e0 + len, tag++) > kMaxLocal) return "block local-node limit exceeded";
+      blks.push_back({e0, e0 + len});
+      e0 += len;
+    }
+  }
+  const int32_t nblk = (int32_t)blks.size();
+  m.nblk = nblk;
+  std::vector<std::vector<int32_t>> bl(nblk);   // regular nodes per block, ascending
+  for (int32_t b = 0; b < nblk; ++b) {
+    std::vector<int32_t> &v = bl[b];
+    for (int64_t e = blks[b].e0; e < blks[b].e1; ++e)
+      for (int k = 0; k < 8; ++k) {
+        const int32_t n = m.conn[8 * e + k];
+        const int32_t h = m.hang_index[n];
+        if (h < 0) v.push_back(n);
+        else
+          for (int j = 0; j < 4; ++j)
+            if (m.hang_master[4 * h + j] >= 0) v.push_back(m.hang_master[4 * h + j]);
+      }
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+    for (int32_t n : v) nblocks_of[n]++;
+  }
+  m.blk_elem.assign(nblk + 1, 0);
+  m.blk_node.assign(nblk + 1, 0);
+  m.blk_shared.assign(nblk, 0);
+  m.blk_slot.assign(nblk + 1, 0);
+  m.blk_hang.assign(nblk + 1, 0);
+  m.blk_iptr.assign(nblk + 1, 0);
+  m.blk_inv.assign(nblk, 0);
+  std::vector<int32_t> local_of(Nn, -1);
+  int32_t max_local = 0;
+  for (int32_t b = 0; b < nblk; ++b) {
+    const std::vector<int32_t> &v = bl[b];
+    std::vector<int32_t> order;
+    order.reserve(v.size());
+    for (int32_t n : v) if (nblocks_of[n] > 1) order.push_back(n);
+    const int32_t nshared = (int32_t)order.size();
+    for (int32_t n : v) if (nblocks_of[n] == 1) order.push_back(n);
+    const int32_t nreg = (int32_t)order.size();
+    for (int32_t i = 0; i < nreg; ++i) local_of[order[i]] = i;
+    m.blk_node[b + 1] = m.blk_node[b] + nreg;
+    m.blk_shared[b] = nshared;
+    m.blk_slot[b + 1] = m.blk_slot[b] + nshared;
+    m.lnode.insert(m.lnode.end(), order.begin(), order.end());
+    // hanging nodes used by this block: local ids nreg, nreg+1, ... in first-use order
+    std::vector<int32_t> used_h;
+    const int64_t e0 = blks[b].e0, e1 = blks[b].e1;
+    for (int64_t e = e0; e < e1; ++e)
+      for (int k = 0; k < 8; ++k) {
+        const int32_t n = m.conn[8 * e + k];
+        if (m.hang_index[n] >= 0 && local_of[n] < 0) {
+          local_of[n] = nreg + (int32_t)used_h.size();
+          used_h.push_back(m.hang_index[n]);
+        }
+      }
+    const int32_t nloc = nreg + (int32_t)used_h.size();
+    if (nloc > kMaxLocal) return "block local-node limit exceeded";
+    max_local = std::max(max_local, nloc);
+    m.blk_hang[b + 1] = m.blk_hang[b] + (int32_t)used_h.size();
+    std::vector<std::vector<uint16_t>> lists(nloc);
+    for (int64_t e = e0; e < e1; ++e)
+      for (int k = 0; k < 8; ++k) lists[local_of[m.conn[8 * e + k]]].push_back((uint16_t)(8 * (e - e0) + k));
+    for (size_t j = 0; j < used_h.size(); ++j) {
+      const int32_t h = used_h[j];
+      const bool quarter = m.hang_master[4 * h + 2] >= 0;
+      for (int q = 0; q < 4; ++q) {
+        const int32_t mm = m.hang_master[4 * h + q];
+        m.hent.push_back(mm >= 0 ? (uint16_t)local_of[mm] : (uint16_t)0xFFFF);
+        if (mm >= 0) lists[local_of[mm]].push_back((uint16_t)(kFoldBit | (quarter ? kQuarterBit : 0) | j));
+      }
+    }
+    if (used_h.size() >= (size_t)kQuarterBit) return "too many hanging nodes in a block";
+    m.blk_inv[b] = (int32_t)m.inv.size();
+    m.blk_iptr[b + 1] = m.blk_iptr[b] + nloc + 1;
+    uint32_t off = 0;
+    for (int32_t i = 0; i < nloc; ++i) {
+      m.iptr.push_back((uint16_t)off);
+      m.inv.insert(m.inv.end(), lists[i].begin(), lists[i].end());
+      off += (uint32_t)lists[i].size();
+    }
+    if (off > 0xFFFF) return "inverse list of a block too long";
+    m.iptr.push_back((uint16_t)off);
+    m.blk_elem[b + 1] = (int32_t)e1;
+    for (int32_t n : order) local_of[n] = -1;
+    for (int32_t h : used_h) local_of[m.hang_node[h]] = -1;
+  }
+  m.max_local = max_local;
+
+  // ---- 7. second-pass CSR over shared nodes: slots in ascending block order
+  {
+    std::vector<int32_t> cnt(Nn + 1, 0);
+    for (int32_t b = 0; b < nblk; ++b)
+      for (int32_t i = 0; i < m.blk_shared[b]; ++i) cnt[m.lnode[m.blk_node[b] + i] + 1]++;
+    std::vector<int32_t> start(Nn + 1, 0);
+    for (int64_t n = 0; n < Nn; ++n) start[n + 1] = start[n] + cnt[n + 1];
+    std::vector<int32_t> fill(start.begin(), start.end() - 1);
+    m.sh_slot.assign(start[Nn], 0);
+    for (int32_t b = 0; b < nblk; ++b)
+      for (int32_t i = 0; i < m.blk_shared[b]; ++i) {
+        const int32_t n = m.lnode[m.blk_node[b] + i];
+        m.sh_slot[fill[n]++] = m.blk_slot[b] + i;
+      }
+    m.sh_ptr.push_back(0);
+    for (int64_t n = 0; n < Nn; ++n)
+      if (cnt[n + 1] > 0) {
+        m.sh_node.push_back((int32_t)n);
+        m.sh_ptr.push_back(start[n + 1]);
+      }
+    // sh_ptr must index into sh_slot compacted by node: start[] is already compact
+  }
+
+  // ---- 8. Jacobi diagonal coefficients: d_{m,c} = sum_e c_e q_{e,m,c}
+  {
+    std::map<std::array<int64_t, 3>, int> tab_index;
+    std::vector<std::vector<std::pair<int32_t, uint16_t>>> rows(Nn);
+    {
+      // entry 0: a corner that is its own node in an element without hanging corners
+      const double q = m.K0[0];
+      std::array<int64_t, 3> kq;
+      for (int c = 0; c < 3; ++c) std::memcpy(&kq[c], &q, 8);
+      tab_index[kq] = 0;
+      m.dg_tab.insert(m.dg_tab.end(), {q, q, q});
+    }
+    for (int64_t e = 0; e < Ne; ++e) {
+      bool plain = true;
+      for (int k = 0; k < 8; ++k) plain &= m.hang_index[m.conn[8 * e + k]] < 0;
+      if (plain) {
+        for (int k = 0; k < 8; ++k) rows[m.conn[8 * e + k]].push_back({(int32_t)e, (uint16_t)0});
+        continue;
+      }
+      // corner expansion: (node, weight) pairs
+      int32_t nodes[32];
+      double wts[32];
+      int corner_of[32];
+      int np = 0;
+      for (int k = 0; k < 8; ++k) {
+        const int32_t n = m.conn[8 * e + k];
+        const int32_t h = m.hang_index[n];
+        if (h < 0) {
+          nodes[np] = n; wts[np] = 1.0; corner_of[np++] = k;
+        } else {
+          int nm = 0;
+          for (int j = 0; j < 4; ++j) nm += m.hang_master[4 * h + j] >= 0;
+          for (int j = 0; j < nm; ++j) {
+            nodes[np] = m.hang_master[4 * h + j]; wts[np] = 1.0 / nm; corner_of[np++] = k;
+          }
+        }
+      }
+      int32_t uniq[32];
+      int nu_ = 0;
+      for (int i = 0; i < np; ++i) {
+        bool seen = false;
+        for (int j = 0; j < nu_; ++j) seen |= uniq[j] == nodes[i];
+        if (!seen) uniq[nu_++] = nodes[i];
+      }
+      for (int u = 0; u < nu_; ++u) {
+        double v[8] = {};
+        for (int i = 0; i < np; ++i)
+          if (nodes[i] == uniq[u]) v[corner_of[i]] += wts[i];
+        double q[3];
+        for (int c = 0; c < 3; ++c) {
+          double s = 0;
+          for (int a = 0; a < 8; ++a)
+            for (int b2 = 0; b2 < 8; ++b2) s += v[a] * v[b2] * m.K0[(3 * a + c) * 24 + 3 * b2 + c];
+          q[c] = s;
+        }
+        std::array<int64_t, 3> kq;
+        for (int c = 0; c < 3; ++c) std::memcpy(&kq[c], &q[c], 8);
+        auto it = tab_index.find(kq);
+        int qi;
+        if (it == tab_index.end()) {
+          qi = (int)tab_index.size();
+          if (qi >= 65535) return "too many distinct diagonal coefficients";
+          tab_index[kq] = qi;
+          m.dg_tab.insert(m.dg_tab.end(), q, q + 3);
+        } else {
+          qi = it->second;
+        }
+        rows[uniq[u]].push_back({(int32_t)e, (uint16_t)qi});
+      }
+    }
+    m.dg_ptr.assign(Nn + 1, 0);
+    for (int64_t n = 0; n < Nn; ++n) m.dg_ptr[n + 1] = m.dg_ptr[n] + (int32_t)rows[n].size();
+    m.dg_elem.resize(m.dg_ptr[Nn]);
+    m.dg_q.resize(m.dg_ptr[Nn]);
+    for (int64_t n = 0; n < Nn; ++n)
+      for (size_t i = 0; i < rows[n].size(); ++i) {
+        m.dg_elem[m.dg_ptr[n] + i] = rows[n][i].first;
+        m.dg_q[m.dg_ptr[n] + i] = rows[n][i].second;
+      }
+  }
+  return "";
+}
+
+}  // namespace amr
+
+// ---------------------------------------------------------------- host-only C ABI
+struct tm_tables {
+  amr::HostMesh m;
+};
+
+extern "C" {
+
+int tm_tables_build(const tm_mesh_desc *d, tm_tables **out, tm_mesh_info *info, char *err, int err_len) {
+  if (!d || !out) return TM_EINVAL;
+  *out = nullptr;
+  tm_tables *t = new tm_tables();
+  std::string msg = amr::build_host_mesh(*d, t->m);
+  if (!msg.empty()) {
+    if (err && err_len > 0) {
+      std::strncpy(err, msg.c_str(), (size_t)err_len - 1);
+      err[err_len - 1] = 0;
+    }
+    delete t;
+    return TM_EINVAL;
+  }
+  const amr::HostMesh &m = t->m;
+  if (info) {
+    info->Ne = m.Ne;
+    info->Nn = m.Nn;
+    info->n_hanging = (int64_t)m.hang_node.size();
+    info->n_dirichlet = m.n_dirichlet;
+    info->n_free = 3 * m.n_free_nodes;
+    info->n_blocks = m.nblk;
+    info->max_local = m.max_local;
+    info->n_shared = (int64_t)m.sh_node.size();
+    info->device_bytes = 0;
+  }
+  *out = t;
+  return TM_OK;
+}
+
+int tm_tables_copy(const tm_tables *t, int64_t *perm, int32_t *node_xyz, int32_t *conn, int32_t *hang_node,
+                   int32_t *hang_master, uint8_t *node_flags) {
+  if (!t) return TM_EINVAL;
+  const amr::HostMesh &h = t->m;
+  if (perm) std::memcpy(perm, h.perm.data(), h.perm.size() * sizeof(int64_t));
+  if (node_xyz) std::memcpy(node_xyz, h.node_xyz.data(), h.node_xyz.size() * sizeof(int32_t));
+  if (conn) std::memcpy(conn, h.conn.data(), h.conn.size() * sizeof(int32_t));
+  if (hang_node) std::memcpy(hang_node, h.hang_node.data(), h.hang_node.size() * sizeof(int32_t));
+  if (hang_master) std::memcpy(hang_master, h.hang_master.data(), h.hang_master.size() * sizeof(int32_t));
+  if (node_flags) std::memcpy(node_flags, h.nflag.data(), h.nflag.size());
+  return TM_OK;
+}
+
+void tm_tables_free(tm_tables *t) { delete t; }
+
+}  // extern "C"

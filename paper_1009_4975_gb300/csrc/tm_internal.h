@@ -1,0 +1,157 @@
+// Internal declarations shared by the translation units of libtm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tm.h"
+
+namespace amr {
+
+// Operator kernel geometry: one CTA per block of consecutive (Morton-ordered)
+// elements.  A block's "local nodes" are the non-hanging nodes its elements
+// touch directly or through a hanging corner's masters.
+constexpr int kBlockElems = 256;     // elements per block (ragged last block)
+constexpr int kMaxLocal = 1024;      // local nodes per block
+constexpr int kFoldBit = 0x8000;     // inverse-list entry names a hanging node to fold in
+constexpr int kQuarterBit = 0x4000;  // ... whose weight is 1/4 (else 1/2)
+
+// ---------------------------------------------------------------- host tables
+struct HostMesh {
+  int nx = 0, ny = 0, nz = 0, L = 0;
+  double h0 = 0;
+  uint32_t dirichlet_faces = 0;
+  double E0 = 1, Emin = 0, nu = 0.3, penal = 3;
+  int64_t Ne = 0, Nn = 0;
+  std::vector<int32_t> leaf;          // 4 per element, canonical order
+  std::vector<int64_t> perm;          // canonical element -> input leaf
+  std::vector<uint64_t> node_key;     // Morton key per node (sorted)
+  std::vector<int32_t> node_xyz;      // 3 per node
+  std::vector<int32_t> conn;          // 8 per element
+  std::vector<uint8_t> nflag;         // bit 0 Dirichlet, bit 1 hanging
+  std::vector<int32_t> hang_node;     // ascending
+  std::vector<int32_t> hang_master;   // 4 per hanging node, -1 padded, ascending
+  std::vector<int32_t> hang_index;    // node -> hanging index or -1
+  int64_t n_dirichlet = 0, n_free_nodes = 0;
+
+  // operator blocks (consecutive canonical elements).  Local node ids of a
+  // block: regular nodes first (shared ones, then interior), then the hanging
+  // nodes its elements use.  The inverse list of a local node names the
+  // (element, corner) slots it fills -- entry e_local * 8 + k -- and, for a
+  // regular node, the hanging nodes it is a master of -- entry kFoldBit |
+  // (kQuarterBit if the hanging node has 4 masters) | hanging index.
+  int32_t nblk = 0, max_local = 0;
+  std::vector<int32_t> blk_elem;      // nblk+1: element ranges
+  std::vector<int32_t> blk_node;      // nblk+1: regular local node ranges in lnode
+  std::vector<int32_t> blk_shared;    // nblk: regular local nodes [0, shared) are shared
+  std::vector<int32_t> blk_slot;      // nblk+1: slot range of the block's shared nodes
+  std::vector<int32_t> blk_hang;      // nblk+1: hanging ranges in hent
+  std::vector<int32_t> blk_iptr;      // nblk+1: ranges in iptr (local nodes + 1)
+  std::vector<int32_t> blk_inv;       // nblk: base of the block's entries in inv
+  std::vector<int32_t> lnode;         // regular local node -> global node
+  std::vector<uint16_t> hent;         // 4 per hanging local node: masters' local ids (0xFFFF pad)
+  std::vector<uint16_t> iptr;         // inverse-list offsets, relative to blk_inv[b]
+  std::vector<uint16_t> inv;          // inverse-list entries
+  // second pass over shared nodes
+  std::vector<int32_t> sh_node;       // shared node ids
+  std::vector<int32_t> sh_ptr;        // CSR into sh_slot
+  std::vector<int32_t> sh_slot;
+  // Jacobi diagonal: node-centric CSR of (element, coefficient-triple index)
+  std::vector<int32_t> dg_ptr;        // Nn+1
+  std::vector<int32_t> dg_elem;
+  std::vector<uint16_t> dg_q;
+  std::vector<double> dg_tab;         // 3 per distinct triple
+  // the reference element matrix (unit cube, E = 1), host copy
+  std::vector<double> K0;             // 24 x 24
+  std::vector<int32_t> cellmap;       // finest cell (x fastest) -> canonical element
+};
+
+// Returns "" on success or an error message.
+std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m);
+void reference_stiffness(double nu, double *K0 /* 576 */);
+uint64_t morton3(uint32_t x, uint32_t y, uint32_t z);
+
+// ---------------------------------------------------------------- device state
+template <typename T>
+struct DBuf {
+  T *p = nullptr;
+  size_t n = 0;
+};
+
+struct DeviceMesh {
+  int64_t Ne = 0, Nn = 0, nh = 0, nsh = 0;
+  int32_t nblk = 0;
+  int fx = 0, fy = 0, fz = 0;         // finest grid extents
+  int L = 0;
+  double h0 = 0, hmin = 0;
+  double E0 = 1, Emin = 0, penal = 3, nu = 0.3;
+  double lam = 0, mu = 0;             // Lame constants for E = 1
+  double k0diag = 0;
+  double volume = 0;                  // |Omega|
+  int64_t n_free = 0;
+  int32_t *leaf = nullptr;            // 4 per element (canonical)
+  int32_t *cellmap = nullptr;         // finest cell -> element (canonical)
+  int32_t *conn = nullptr;            // 8 per element (canonical)
+  uint8_t *nflag = nullptr;
+  int32_t *hang_node = nullptr;
+  int32_t *hang_master = nullptr;     // 4 per
+  int32_t *blk_elem = nullptr, *blk_node = nullptr, *blk_shared = nullptr, *blk_slot = nullptr,
+          *blk_hang = nullptr, *blk_iptr = nullptr, *blk_inv = nullptr;
+  int32_t *lnode = nullptr;
+  uint16_t *hent = nullptr, *iptr = nullptr, *inv = nullptr;
+  int32_t max_local = 0;
+  int32_t *sh_node = nullptr, *sh_ptr = nullptr, *sh_slot = nullptr;
+  int32_t *dg_ptr = nullptr, *dg_elem = nullptr;
+  uint16_t *dg_q = nullptr;
+  double *dg_tab = nullptr;
+  int64_t nslot = 0;
+  std::vector<void *> owned;
+  int64_t bytes = 0;
+};
+
+// Work buffers of one context (sized for the current mesh).
+struct Work {
+  double *part64 = nullptr;    // 3 * nslot, partial sums of shared nodes (FP64 operator)
+  float *part32 = nullptr;     // 3 * nslot (FP32 operator)
+  double *ce64 = nullptr;      // Ne, coefficients E_e h_e (canonical order)
+  float *ce32 = nullptr;
+  double *red = nullptr;       // reduction partials
+  double *scal = nullptr;      // device scalars
+  unsigned int *ticket = nullptr;  // last-block counters
+  int *status = nullptr;       // device status word
+  // solver vectors (3 * Nn)
+  double *r = nullptr, *p = nullptr, *q = nullptr, *dinv = nullptr, *d = nullptr;
+  float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *dinv32 = nullptr, *x32 = nullptr;
+  int64_t nred = 0;
+  std::vector<void *> owned;
+  int64_t bytes = 0;
+};
+
+}  // namespace amr
+
+struct tm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  bool has_mesh = false;
+  amr::HostMesh host;
+  amr::DeviceMesh dm;
+  amr::Work w;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace amr {
+// device-side launchers of the operator file; each returns the launch's cudaError_t
+cudaError_t launch_coeff(const DeviceMesh &m, const Work &w, const double *rho, cudaStream_t s);
+template <typename T>
+cudaError_t launch_apply(const DeviceMesh &m, const T *ce, const T *x, T *y, T *part, double *dot_partials,
+                         const int *done, cudaStream_t s);
+cudaError_t launch_diag(const DeviceMesh &m, const double *ce, double *d, double *dinv, float *dinv32,
+                        cudaStream_t s);
+cudaError_t launch_expand(const DeviceMesh &m, const double *u, double *uf, cudaStream_t s);
+cudaError_t launch_rhs_fold(const DeviceMesh &m, double *f, cudaStream_t s);
+int shared_grid(int64_t n);
+}  // namespace amr

@@ -1,0 +1,286 @@
+"""ctypes binding of libtm (include/tm.h): argument marshalling only.
+
+Every function has the name of its C entry point and forwards to it; device
+arrays are torch CUDA tensors (their data pointers are passed through), host
+arrays are numpy arrays.  There is no fallback: if libtm.so is missing or the
+GPU is unusable the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtm.so")
+
+TM_OK, TM_EINVAL, TM_ECUDA, TM_ENOTCONVERGED, TM_ENONFINITE, TM_ETIMEOUT, TM_ENOMEM, TM_ESTATE = range(8)
+TM_PREC_FP64, TM_PREC_MIXED = 0, 1
+_NAMES = {1: "TM_EINVAL", 2: "TM_ECUDA", 3: "TM_ENOTCONVERGED", 4: "TM_ENONFINITE", 5: "TM_ETIMEOUT",
+          6: "TM_ENOMEM", 7: "TM_ESTATE"}
+
+
+class TmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class tm_mesh_desc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("max_level", C.c_int32),
+                ("h0", C.c_double), ("n_leaves", C.c_int64), ("leaves", C.POINTER(C.c_int32)),
+                ("dirichlet_faces", C.c_uint32), ("E0", C.c_double), ("Emin", C.c_double), ("nu", C.c_double),
+                ("penal", C.c_double)]
+
+
+class tm_mesh_info(C.Structure):
+    _fields_ = [("Ne", C.c_int64), ("Nn", C.c_int64), ("n_hanging", C.c_int64), ("n_dirichlet", C.c_int64),
+                ("n_free", C.c_int64), ("n_blocks", C.c_int32), ("max_local", C.c_int32),
+                ("n_shared", C.c_int64), ("device_bytes", C.c_int64)]
+
+
+class tm_solve_opts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
+                ("inner_rtol", C.c_double), ("check_every", C.c_int32)]
+
+
+class tm_solve_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("sweeps", C.c_int32), ("rel_residual", C.c_double),
+                ("seconds", C.c_double), ("fp64_applies", C.c_int32), ("fp32_applies", C.c_int32)]
+
+
+EXPORTS = ["tm_create", "tm_destroy", "tm_set_stream", "tm_last_error", "tm_mesh_upload", "tm_mesh_tables",
+           "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_jacobi_diag", "tm_pcg_solve", "tm_expand",
+           "tm_sensitivity", "tm_filter", "tm_oc_update"]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtm.so (built by paper_1009_4975_gb300.build).  Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtm.so not built ({path}); run paper_1009_4975_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "tm_create": [C.POINTER(vp), C.c_int, vp],
+        "tm_destroy": [vp],
+        "tm_set_stream": [vp, vp],
+        "tm_mesh_upload": [vp, C.POINTER(tm_mesh_desc), C.POINTER(tm_mesh_info)],
+        "tm_mesh_tables": [vp, vp, vp, vp, vp, vp, vp],
+        "tm_build_rhs": [vp, i64, vp, vp, vp, vp],
+        "tm_apply_K": [vp, vp, vp, vp],
+        "tm_apply_K_f32": [vp, vp, vp, vp],
+        "tm_jacobi_diag": [vp, vp, vp],
+        "tm_pcg_solve": [vp, vp, vp, vp, C.POINTER(tm_solve_opts), C.POINTER(tm_solve_stats)],
+        "tm_expand": [vp, vp, vp],
+        "tm_sensitivity": [vp, vp, vp, vp, C.POINTER(dbl)],
+        "tm_filter": [vp, vp, vp, dbl, C.c_int, vp],
+        "tm_oc_update": [vp, vp, vp, dbl, dbl, dbl, dbl, vp, C.POINTER(dbl)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    lib.tm_tables_build.argtypes = [C.POINTER(tm_mesh_desc), C.POINTER(vp), C.POINTER(tm_mesh_info), C.c_char_p,
+                                    C.c_int]
+    lib.tm_tables_build.restype = C.c_int
+    lib.tm_tables_copy.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.tm_tables_copy.restype = C.c_int
+    lib.tm_tables_free.argtypes = [vp]
+    lib.tm_tables_free.restype = None
+    lib.tm_last_error.argtypes = [vp]
+    lib.tm_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor, with dtype and size checks."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Ctx:
+    """A library context bound to one device and stream; holds at most one mesh."""
+
+    def __init__(self, handle, device):
+        self.handle = handle
+        self.device = device
+        self.info = None
+
+    def check(self, rc):
+        if rc != TM_OK:
+            raise TmError(rc, load_library().tm_last_error(self.handle).decode())
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tm_destroy(self.handle)
+            self.handle = None
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def tm_create(device: int = 0, stream=None) -> Ctx:
+    lib = load_library()
+    h = C.c_void_p()
+    rc = lib.tm_create(C.byref(h), device, _stream_ptr(stream))
+    if rc != TM_OK:
+        raise TmError(rc, f"tm_create failed on device {device}")
+    return Ctx(h, device)
+
+
+def tm_destroy(ctx: Ctx):
+    if ctx.handle:
+        load_library().tm_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def tm_set_stream(ctx: Ctx, stream=None):
+    ctx.check(load_library().tm_set_stream(ctx.handle, _stream_ptr(stream)))
+
+
+def tm_last_error(ctx: Ctx) -> str:
+    return load_library().tm_last_error(ctx.handle).decode()
+
+
+def tm_mesh_upload(ctx: Ctx, nx, ny, nz, max_level, h0, leaves, dirichlet_faces=1, E0=1.0, Emin=1e-9, nu=0.3,
+                   penal=3.0) -> dict:
+    lv = np.ascontiguousarray(np.asarray(leaves, np.int32).reshape(-1, 4))
+    d = tm_mesh_desc(nx, ny, nz, max_level, h0, lv.shape[0], lv.ctypes.data_as(C.POINTER(C.c_int32)),
+                     dirichlet_faces, E0, Emin, nu, penal)
+    info = tm_mesh_info()
+    ctx.check(load_library().tm_mesh_upload(ctx.handle, C.byref(d), C.byref(info)))
+    ctx.info = {k: getattr(info, k) for k, _ in tm_mesh_info._fields_}
+    return ctx.info
+
+
+def _table_arrays(i):
+    Ne, Nn, nh = i["Ne"], i["Nn"], i["n_hanging"]
+    return {"perm": np.empty(Ne, np.int64), "node_xyz": np.empty((Nn, 3), np.int32),
+            "conn": np.empty((Ne, 8), np.int32), "hang_node": np.empty(nh, np.int32),
+            "hang_master": np.empty((nh, 4), np.int32), "node_flags": np.empty(Nn, np.uint8)}
+
+
+def tm_mesh_tables(ctx: Ctx) -> dict:
+    out = _table_arrays(ctx.info)
+    ctx.check(load_library().tm_mesh_tables(ctx.handle, *[C.c_void_p(a.ctypes.data) for a in out.values()]))
+    return out
+
+
+def tm_tables_build(nx, ny, nz, max_level, h0, leaves, dirichlet_faces=1, E0=1.0, Emin=1e-9, nu=0.3,
+                    penal=3.0):
+    """Host-only table construction; returns (info, tables) or raises TmError(TM_EINVAL)."""
+    lib = load_library()
+    lv = np.ascontiguousarray(np.asarray(leaves, np.int32).reshape(-1, 4))
+    d = tm_mesh_desc(nx, ny, nz, max_level, h0, lv.shape[0], lv.ctypes.data_as(C.POINTER(C.c_int32)),
+                     dirichlet_faces, E0, Emin, nu, penal)
+    info = tm_mesh_info()
+    h = C.c_void_p()
+    err = C.create_string_buffer(512)
+    rc = lib.tm_tables_build(C.byref(d), C.byref(h), C.byref(info), err, 512)
+    if rc != TM_OK:
+        raise TmError(rc, err.value.decode())
+    try:
+        i = {k: getattr(info, k) for k, _ in tm_mesh_info._fields_}
+        out = _table_arrays(i)
+        rc = lib.tm_tables_copy(h, *[C.c_void_p(a.ctypes.data) for a in out.values()])
+        if rc != TM_OK:
+            raise TmError(rc, "tm_tables_copy failed")
+        return i, out
+    finally:
+        lib.tm_tables_free(h)
+
+
+def tm_build_rhs(ctx: Ctx, node_xyz, comp, val, f):
+    nx = np.ascontiguousarray(np.asarray(node_xyz, np.int32).reshape(-1, 3))
+    cp = np.ascontiguousarray(np.asarray(comp, np.int32).ravel())
+    vl = np.ascontiguousarray(np.asarray(val, np.float64).ravel())
+    import torch
+    ctx.check(load_library().tm_build_rhs(ctx.handle, nx.shape[0], C.c_void_p(nx.ctypes.data),
+                                          C.c_void_p(cp.ctypes.data), C.c_void_p(vl.ctypes.data),
+                                          _ptr(f, torch.float64, 3 * ctx.info["Nn"], "f")))
+
+
+def _vec(ctx, t, dtype, name):
+    return _ptr(t, dtype, 3 * ctx.info["Nn"], name)
+
+
+def _elem(ctx, t, name):
+    import torch
+    return _ptr(t, torch.float64, ctx.info["Ne"], name)
+
+
+def tm_apply_K(ctx: Ctx, rho, x, y):
+    import torch
+    ctx.check(load_library().tm_apply_K(ctx.handle, _elem(ctx, rho, "rho"), _vec(ctx, x, torch.float64, "x"),
+                                        _vec(ctx, y, torch.float64, "y")))
+
+
+def tm_apply_K_f32(ctx: Ctx, rho, x, y):
+    import torch
+    ctx.check(load_library().tm_apply_K_f32(ctx.handle, _elem(ctx, rho, "rho"), _vec(ctx, x, torch.float32, "x"),
+                                            _vec(ctx, y, torch.float32, "y")))
+
+
+def tm_jacobi_diag(ctx: Ctx, rho, d):
+    import torch
+    ctx.check(load_library().tm_jacobi_diag(ctx.handle, _elem(ctx, rho, "rho"), _vec(ctx, d, torch.float64, "d")))
+
+
+def tm_pcg_solve(ctx: Ctx, rho, f, u, rtol=1e-8, max_iter=100000, precision=TM_PREC_FP64, inner_rtol=1e-3,
+                 check_every=64, raise_on_error=True) -> dict:
+    import torch
+    o = tm_solve_opts(rtol, max_iter, precision, inner_rtol, check_every)
+    s = tm_solve_stats()
+    rc = load_library().tm_pcg_solve(ctx.handle, _elem(ctx, rho, "rho"), _vec(ctx, f, torch.float64, "f"),
+                                     _vec(ctx, u, torch.float64, "u"), C.byref(o), C.byref(s))
+    stats = {k: getattr(s, k) for k, _ in tm_solve_stats._fields_}
+    stats["status"] = rc
+    if raise_on_error and rc != TM_OK:
+        ctx.check(rc)
+    return stats
+
+
+def tm_expand(ctx: Ctx, u, u_full):
+    import torch
+    ctx.check(load_library().tm_expand(ctx.handle, _vec(ctx, u, torch.float64, "u"),
+                                       _vec(ctx, u_full, torch.float64, "u_full")))
+
+
+def tm_sensitivity(ctx: Ctx, rho, u_full, dc) -> float:
+    import torch
+    c = C.c_double()
+    ctx.check(load_library().tm_sensitivity(ctx.handle, _elem(ctx, rho, "rho"),
+                                            _vec(ctx, u_full, torch.float64, "u_full"), _elem(ctx, dc, "dc"),
+                                            C.byref(c)))
+    return c.value
+
+
+def tm_filter(ctx: Ctx, rho, x, rmin, mode, out):
+    ctx.check(load_library().tm_filter(ctx.handle, _elem(ctx, rho, "rho"), _elem(ctx, x, "x"), rmin, mode,
+                                       _elem(ctx, out, "out")))
+
+
+def tm_oc_update(ctx: Ctx, rho, dc, volfrac, move, eta, rho_min, rho_new) -> float:
+    ch = C.c_double()
+    ctx.check(load_library().tm_oc_update(ctx.handle, _elem(ctx, rho, "rho"), _elem(ctx, dc, "dc"), volfrac, move,
+                                          eta, rho_min, _elem(ctx, rho_new, "rho_new"), C.byref(ch)))
+    return ch.value

@@ -1,0 +1,105 @@
+"""Host-side checks of libtm (no GPU): the library loads, exports every entry point
+include/tm.h declares, and its integer mesh tables match the oracle bit for bit."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mesh as M
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tm():
+    from paper_1009_4975_gb300 import build
+    build.build()
+    import paper_1009_4975_gb300 as P
+    P.load_library()
+    return P
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "tm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tm_[A-Za-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(tm):
+    lib = tm.load_library()
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(tm.EXPORTS) == names
+
+
+def _oracle_tables(w):
+    d = w.dom
+    m = M.build_mesh(d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, dirichlet_faces=w.dirichlet_faces)
+    hn = m.hanging_ids()
+    hm = np.full((hn.size, 4), -1, np.int64)
+    for i, h in enumerate(hn):
+        ms = [j for j, _ in m.hanging[h]]
+        hm[i, :len(ms)] = ms
+    flags = m.dirichlet.astype(np.uint8)
+    flags[hn] |= 2
+    return m, hn, hm, flags
+
+
+@pytest.mark.parametrize("make", [W.config1, W.config1b, W.small_truss])
+def test_tables_bit_exact_against_oracle(tm, make):
+    w = make()
+    d = w.dom
+    info, t = tm.tm_tables_build(d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, dirichlet_faces=w.dirichlet_faces)
+    m, hn, hm, flags = _oracle_tables(w)
+    assert info["Ne"] == m.Ne and info["Nn"] == m.Nn and info["n_hanging"] == hn.size
+    assert np.array_equal(t["perm"], m.perm)
+    assert np.array_equal(t["node_xyz"], m.nodes)
+    assert np.array_equal(t["conn"], m.conn)
+    assert np.array_equal(t["hang_node"], hn)
+    assert np.array_equal(t["hang_master"], hm)
+    assert np.array_equal(t["node_flags"], flags)
+    fn = (flags == 0).sum()
+    assert info["n_free"] == 3 * fn
+    assert 0 < info["max_local"] <= 1024
+
+
+def test_tables_other_dirichlet_faces(tm):
+    w = W.config1()
+    d = w.dom
+    faces = 0b100101          # x = 0, y = 0, z = max
+    info, t = tm.tm_tables_build(d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, dirichlet_faces=faces)
+    m = M.build_mesh(d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, dirichlet_faces=faces)
+    assert np.array_equal(t["node_flags"] & 1, m.dirichlet.astype(np.uint8))
+
+
+def test_rejects_invalid_leaf_sets(tm):
+    dom = W.Domain(2, 1, 1, 2, 1.0)
+    ok = W.uniform_leaves(dom)
+    tm.tm_tables_build(2, 1, 1, 2, 1.0, ok)
+    cases = {
+        "gap": ok[:1],
+        "overlap": np.concatenate([ok, W.refine(dom, ok[:1], [True])[:1]]),
+        "misaligned": ok + np.array([[0, 0, 0, 0], [1, 0, 0, 0]]),
+        "outside": ok + np.array([[0, 0, 0, 0], [0, 4, 0, 0]]),
+        "level": ok + np.array([[0, 0, 0, 3], [0, 0, 0, 0]]),
+    }
+    one = W.refine(dom, ok, [True, False])
+    cases["unbalanced"] = W.refine(dom, one, (one[:, 3] == 1) & (one[:, 0] == 2) & (one[:, 1] == 0) & (one[:, 2] == 0))
+    for name, lv in cases.items():
+        with pytest.raises(tm.TmError) as ei:
+            tm.tm_tables_build(2, 1, 1, 2, 1.0, lv)
+        assert ei.value.code == tm.TM_EINVAL, name
+    # the balanced repair is accepted
+    tm.tm_tables_build(2, 1, 1, 2, 1.0, W.balance(dom, cases["unbalanced"]))
+
+
+def test_python_binding_fails_loudly_without_gpu(tm):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(tm.TmError):
+        tm.tm_create(0, stream=0)
