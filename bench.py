@@ -1,0 +1,370 @@
+"""Benchmark of the FE solve inside one SIMP/OC optimisation iteration on a 2:1-balanced octree
+cantilever mesh (base 48x24x24, three refinement levels along a seeded truss, ~2M elements,
+~5.4M unknowns), through the C ABI of libtm.
+
+One step = one optimisation iteration on the fixed mesh: Jacobi-PCG solve of C^T K(rho) C u = f to
+a relative residual of 1e-8 (FP32 operator inside FP64 iterative refinement, warm-started from the
+previous u), expansion u_full = C u, compliance sensitivities, the volume-weighted filter of Eq. 5
+and the OC update.  Metric: GDOF*iter/s = unknowns * CG iterations / solve-step seconds.
+
+Arms:
+  (default)            the GPU library; prints one JSON line (rank 0).
+  --impl reference     the oracle (FP64 CPU Jacobi-PCG on its assembled sparse matrix) timed on
+                       the host cores on a bounded sample of the same mesh.
+Launch with torchrun for N > 1: every rank runs an independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FE solve time to 1e-8 rel residual, GDOF·iter/s: chosen vs FP64 PCG, 1 GB300"
+UNIT = "GDOF*iter/s"
+ALGO_BYTES_PER_ELEM_F32 = 60.0     # conn 32 + c_e 4 + x 12 + y 12 (FP32 operator)
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("kernels_apply.cu", "element.cuh"):
+        with open(os.path.join(ROOT, "paper_1009_4975_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_per_launch():
+    """DRAM bytes of one operator application from the committed ncu summary, if it was taken
+    on the current kernel source (matching hash); else None."""
+    path = os.path.join(ROOT, "profiles", "apply_f32_cantilever_48x24x24_L3.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    kv = {}
+    for line in txt.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if kv.get("kernel_source_sha256_16") != _kernel_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_application"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_1009_4975_gb300 as P
+    from paper_1009_4975_gb300 import build
+    import workloads as W
+
+    build.build()
+    w = W.config2()
+    d = w.dom
+    stream = torch.cuda.current_stream()
+    ctx = P.tm_create(local, stream=stream)
+    t0 = time.perf_counter()
+    info = P.tm_mesh_upload(ctx, d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, w.dirichlet_faces, w.E0, w.Emin, w.nu,
+                            w.penal)
+    mesh_s = time.perf_counter() - t0
+    perm = P.tm_mesh_tables(ctx)["perm"]
+    dev = torch.device("cuda", local)
+    Ne, Nn, nfree = info["Ne"], info["Nn"], info["n_free"]
+    rho = torch.as_tensor(w.rho[perm], device=dev)
+    rho_new = torch.empty_like(rho)
+    f = torch.zeros(3 * Nn, dtype=torch.float64, device=dev)
+    P.tm_build_rhs(ctx, w.load_nodes, w.load_comp, w.load_val, f)
+    u = torch.zeros_like(f)
+    uf = torch.zeros_like(f)
+    dc = torch.zeros_like(rho)
+    dch = torch.zeros_like(rho)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    rmin = w.r_min
+
+    def step(rho_in, rho_out, prec=P.TM_PREC_MIXED):
+        st = P.tm_pcg_solve(ctx, rho_in, f, u, rtol=1e-8, max_iter=200000, precision=prec, check_every=64)
+        P.tm_expand(ctx, u, uf)
+        comp = P.tm_sensitivity(ctx, rho_in, uf, dc)
+        P.tm_filter(ctx, rho_in, dc, rmin, 0, dch)
+        chg = P.tm_oc_update(ctx, rho_in, dch, 0.2, 0.2, 0.5, w.rho_min, rho_out)
+        return st, comp, chg
+
+    cur, nxt = rho, rho_new
+    for _ in range(args.warmup):
+        step(cur, nxt)
+        cur, nxt = nxt, cur
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device-resident inputs
+    clocks = Clocks(local)
+    P.tm_profile(ctx, True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    step_ms, iters, comps, solve_ms = [], 0, [], 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, comp, chg = step(cur, nxt)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        iters += st["iterations"]
+        solve_ms += 1e3 * st["seconds"]
+        comps.append(comp)
+        cur, nxt = nxt, cur
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    prof = P.tm_profile_read(ctx)
+    P.tm_profile(ctx, False)
+    total_ms = float(sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([total_ms, float(iters)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        tsum = t.clone()
+        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
+        total_ms_job, iters_job = float(tmax[0]), float(tsum[1])
+    else:
+        total_ms_job, iters_job = total_ms, float(iters)
+    value = nfree * iters_job / (total_ms_job * 1e-3) / 1e9
+
+    # ---- end to end: host (pinned) inputs copied in and results copied out each step
+    rho_h = torch.empty(Ne, dtype=torch.float64, pin_memory=True)
+    rho_h.copy_(cur.cpu())
+    f_h = f.cpu().pin_memory()
+    u_h = u.cpu().pin_memory()
+    out_rho_h = torch.empty_like(rho_h).pin_memory()
+    out_u_h = torch.empty_like(u_h).pin_memory()
+    e2e_steps = max(1, min(args.steps, 2))
+    h2d = rho_h.numel() * 8 + f_h.numel() * 8 + u_h.numel() * 8
+    d2h = out_rho_h.numel() * 8 + out_u_h.numel() * 8 + 8
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(e2e_steps):
+        cur.copy_(rho_h, non_blocking=True)
+        f.copy_(f_h, non_blocking=True)
+        u.copy_(u_h, non_blocking=True)
+        st, comp, chg = step(cur, nxt)
+        out_rho_h.copy_(nxt, non_blocking=True)
+        out_u_h.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_iters += st["iterations"]
+        rho_h.copy_(out_rho_h)
+        u_h.copy_(out_u_h)
+    e2e_s = time.perf_counter() - te
+    e2e_value = nfree * e2e_iters / e2e_s / 1e9
+
+    # ---- FP64 Jacobi-PCG on the next design's system (the solve the next step would do), bounded
+    u64 = u.clone()
+    st64 = P.tm_pcg_solve(ctx, nxt, f, u64, rtol=1e-8, max_iter=args.fp64_iters, precision=P.TM_PREC_FP64,
+                          check_every=64, raise_on_error=False)
+    fp64 = {"gdof_iter_per_s": nfree * st64["iterations"] / st64["seconds"] / 1e9,
+            "ms_per_iter": 1e3 * st64["seconds"] / max(st64["iterations"], 1),
+            "iterations": st64["iterations"], "rel_residual": st64["rel_residual"],
+            "converged": st64["status"] == 0}
+
+    if rank != 0:
+        return
+    peak, peak_kind = _peaks()
+    a_ms = prof["apply32_ms"] / max(prof["apply32_count"], 1)
+    algo = ALGO_BYTES_PER_ELEM_F32 * Ne
+    achieved = algo / (a_ms * 1e-3) / 1e9
+    traffic = _traffic_per_launch()
+    cpu = cpu_baseline(args, w) if (args.cpu_baseline and ws == 1) else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 operator, f64 refinement/reductions",
+        "data": "synthetic (seeded octree truss cantilever)",
+        "config": {"workload": w.name, "elements": Ne, "nodes": Nn, "unknowns": nfree,
+                   "hanging_nodes": info["n_hanging"], "solver": "mixed: FP32-operator Jacobi-PCG sweeps in FP64 "
+                   "iterative refinement, rtol 1e-8, warm start", "step": "solve+expand+sensitivity+filter+OC",
+                   "l2": "flushed (512 MB write) before every step", "parallelism": f"replicas x{ws}"},
+        "time_to_tolerance_ms": solve_ms / args.steps,
+        "cg_iterations_per_step": iters / args.steps,
+        "compliance": comps,
+        "mesh_upload_s": mesh_s,
+        "fp64_pcg": fp64,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "roofline": {"bound": "hbm", "kernel": "operator application (apply_blocks_kernel<float> + "
+                     "apply_shared_kernel<float>)", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "algorithmic_bytes": algo, "avg_ms": a_ms,
+                     "launches_timed": prof["apply32_count"]},
+        "gpu_launches": prof["launches"],
+        "clocks": clk,
+        "wall_s": wall,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _sample_workload(w=None):
+    """Bounded sample of the benchmark mesh: its leaves inside the first two base-cell layers at
+    the clamped face, as a mesh of its own (domain 2 x 24 x 24 base cells, same levels)."""
+    import workloads as W
+    w = W.config2() if w is None else w
+    d = w.dom
+    s = 1 << d.L
+    keep = w.leaves[:, 0] < 2 * s
+    dom = W.Domain(2, d.ny, d.nz, d.L, d.h0)
+    ln, lc, lv = W.load_at(dom, 2 * d.h0, 0.5, 0.5)
+    return W.Workload(w.name + "_first2layers", dom, w.leaves[keep], w.rho[keep], ln, lc, lv)
+
+
+def cpu_baseline(args, full=None):
+    from oracle import fem as F
+    from oracle import mesh as M
+    from oracle import solve as S
+    w = _sample_workload(full)
+    d = w.dom
+    m = M.build_mesh(d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, dirichlet_faces=w.dirichlet_faces)
+    A, f, C = F.reduced_system(m, w.rho[m.perm], w.load_nodes, w.load_comp, w.load_val, w.E0, w.Emin, w.nu,
+                               w.penal)
+    n = A.shape[0]
+    iters = args.cpu_iters
+    u, it, rr, sec = S.jacobi_pcg(A, f, rtol=1e-30, max_iter=iters)
+    value = n * it / sec / 1e9
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{it} Jacobi-PCG iterations (scipy CSR SpMV, FP64) on the benchmark mesh's leaves in "
+                      f"the first 2 base-cell layers at the clamped face: {m.Ne} elements, {n} unknowns",
+            "seconds": sec}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    vals = []
+    cb = None
+    for _ in range(max(args.steps, 1)):
+        cb = cpu_baseline(args)
+        vals.append(cb["value"])
+    wall = time.perf_counter() - t0
+    value = sum(vals) / len(vals)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": 0, "ms_per_step": 1e3 * wall / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded octree truss cantilever)",
+            "impl": "reference", "config": {"workload": "cantilever_48x24x24_L3_truss (bounded sample)"},
+            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": value,
+                             "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-iters", type=int, default=400, help="FP64 PCG iterations for its throughput figure")
+    ap.add_argument("--cpu-iters", type=int, default=600, help="oracle PCG iterations of the CPU baseline")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

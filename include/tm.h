@@ -103,6 +103,15 @@ typedef struct {
   int32_t fp32_applies;       /* FP32 operator applications                       */
 } tm_solve_stats;
 
+/* Counters of tm_profile / tm_profile_read. */
+typedef struct {
+  int64_t launches;           /* kernels this context launched since tm_profile    */
+  int64_t apply32_count;      /* FP32 operator applications timed                  */
+  int64_t apply64_count;      /* FP64 operator applications timed                  */
+  double apply32_ms;          /* their summed CUDA-event time (both passes)        */
+  double apply64_ms;
+} tm_profile_data;
+
 /* Create a context on CUDA device `device`, enqueueing on `cuda_stream`
  * (cudaStream_t or NULL).  *out receives the context; TM_ECUDA if the device is
  * unusable. */
@@ -190,6 +199,15 @@ int tm_filter(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double rm
  * *change_out (host, may be NULL) receives max |rho_new - rho|. */
 int tm_oc_update(tm_ctx *ctx, const double *rho_dev, const double *dc_dev, double volfrac, double move,
                  double eta, double rho_min, double *rho_new_dev, double *change_out);
+
+/* Instrumentation (no counterpart in the paper): tm_profile(ctx, 1) resets the
+ * counters and starts timing every operator application with a CUDA-event
+ * pair on the context's stream (both passes of the operator; applications a CG
+ * batch enqueued past convergence return at once and are not counted);
+ * tm_profile(ctx, 0) stops timing.  tm_profile_read synchronises the stream
+ * and returns the counters. */
+int tm_profile(tm_ctx *ctx, int enable);
+int tm_profile_read(tm_ctx *ctx, tm_profile_data *out);
 
 #ifdef __cplusplus
 }

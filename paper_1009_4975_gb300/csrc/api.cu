@@ -73,15 +73,86 @@ SolveScalars *solve_scalars(tm_ctx *c) { return reinterpret_cast<SolveScalars *>
 OcState *oc_state(tm_ctx *c) { return reinterpret_cast<OcState *>(c->w.scal + 64); }
 double *scal_at(tm_ctx *c, int i) { return c->w.scal + i; }
 
+// Operator launches with optional CUDA-event timing (tm_profile): each timed
+// application records an event pair on the context's stream; pairs are read
+// back at the next synchronisation point.
+template <typename T>
+int timed_apply(tm_ctx *ctx, const T *ce, const T *x, T *y, T *part, double *dotp, SolveScalars *sc,
+                bool zero_hanging, const int *done) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ctx->prof_on) {
+    if (ctx->ev_free.size() < 2) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        TM_CUDA(ctx, cudaEventCreate(&e));
+        ctx->ev_free.push_back(e);
+      }
+    }
+    e0 = ctx->ev_free.back(); ctx->ev_free.pop_back();
+    e1 = ctx->ev_free.back(); ctx->ev_free.pop_back();
+    TM_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+  }
+  TM_CUDA(ctx, launch_apply<T>(ctx->dm, ce, x, y, part, dotp, sc, ctx->w.ticket + 5, zero_hanging, done, ctx->stream));
+  ctx->launches += 2;
+  if (ctx->prof_on) {
+    TM_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+    ctx->ev_pending.push_back({e0, e1, sizeof(T) == 4 ? 1 : 0});
+  }
+  return TM_OK;
+}
+
+// Accumulate completed event pairs (all of them when `all`, after a sync).
+int drain_profile(tm_ctx *ctx, bool all) {
+  std::vector<tm_ctx::Pending> keep;
+  for (const auto &pe : ctx->ev_pending) {
+    if (!all && cudaEventQuery(pe.e1) != cudaSuccess) {
+      keep.push_back(pe);
+      continue;
+    }
+    float ms = 0;
+    TM_CUDA(ctx, cudaEventElapsedTime(&ms, pe.e0, pe.e1));
+    // an apply skipped by the device-side done flag is not a launch that did work
+    if (pe.kind == 1) { ctx->prof.apply32_ms += ms; ctx->prof.apply32_count++; }
+    else { ctx->prof.apply64_ms += ms; ctx->prof.apply64_count++; }
+    ctx->ev_free.push_back(pe.e0);
+    ctx->ev_free.push_back(pe.e1);
+  }
+  ctx->ev_pending.swap(keep);
+  return TM_OK;
+}
+
 int read_scalar(tm_ctx *ctx, const double *dev, double *out) {
   TM_CUDA(ctx, cudaMemcpyAsync(out, dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return TM_OK;
 }
 
-__global__ void scatter_loads_kernel(const int64_t *idx, const double *val, int64_t n, double *f) {
+// f = C^T f_full for a few point loads: a load on a hanging node goes to its
+// masters with the interpolation weights; loads on Dirichlet DOFs vanish.  One
+// thread walks the loads in order (deterministic; loads are few).
+__global__ void scatter_loads_kernel(const int64_t *idx, const double *val, int64_t n, const uint8_t *nflag,
+                                     const int32_t *hang_node, const int32_t *hang_master, int64_t nh, double *f) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  for (int64_t i = 0; i < n; ++i) f[idx[i]] += val[i];
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t node = idx[i] / 3;
+    const int c = (int)(idx[i] % 3);
+    if (nflag[node] & 2) {
+      int64_t lo = 0, hi = nh - 1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (hang_node[mid] < node) lo = mid + 1;
+        else hi = mid;
+      }
+      const int nm = hang_master[4 * lo + 2] < 0 ? 2 : 4;
+      const double w = nm == 2 ? 0.5 : 0.25;
+      for (int q = 0; q < nm; ++q) {
+        const int mm = hang_master[4 * lo + q];
+        if (!(nflag[mm] & 1)) f[3 * (int64_t)mm + c] += w * val[i];
+      }
+    } else if (!(nflag[node] & 1)) {
+      f[idx[i]] += val[i];
+    }
+  }
 }
 
 }  // namespace
@@ -112,6 +183,11 @@ int tm_destroy(tm_ctx *ctx) {
   cudaStreamSynchronize(ctx->stream);
   release(ctx->dm.owned);
   release(ctx->w.owned);
+  for (auto &pe : ctx->ev_pending) {
+    cudaEventDestroy(pe.e0);
+    cudaEventDestroy(pe.e1);
+  }
+  for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   delete ctx;
@@ -167,12 +243,12 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
   TM_CUDA(ctx, upload(o, B, &m.blk_iptr, h.blk_iptr));
   TM_CUDA(ctx, upload(o, B, &m.blk_inv, h.blk_inv));
   TM_CUDA(ctx, upload(o, B, &m.lnode, h.lnode));
+  TM_CUDA(ctx, upload(o, B, &m.lslot, h.lslot));
   TM_CUDA(ctx, upload(o, B, &m.hent, h.hent));
   TM_CUDA(ctx, upload(o, B, &m.iptr, h.iptr));
   TM_CUDA(ctx, upload(o, B, &m.inv, h.inv));
   TM_CUDA(ctx, upload(o, B, &m.sh_node, h.sh_node));
   TM_CUDA(ctx, upload(o, B, &m.sh_ptr, h.sh_ptr));
-  TM_CUDA(ctx, upload(o, B, &m.sh_slot, h.sh_slot));
   TM_CUDA(ctx, upload(o, B, &m.dg_ptr, h.dg_ptr));
   TM_CUDA(ctx, upload(o, B, &m.dg_elem, h.dg_elem));
   TM_CUDA(ctx, upload(o, B, &m.dg_q, h.dg_q));
@@ -261,7 +337,8 @@ int tm_build_rhs(tm_ctx *ctx, int64_t n_loads, const int32_t *node_xyz, const in
     if (e == cudaSuccess) e = cudaMemcpyAsync(didx, idx.data(), n_loads * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dval, val, n_loads * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) {
-      scatter_loads_kernel<<<1, 32, 0, ctx->stream>>>(didx, dval, n_loads, f_dev);
+      scatter_loads_kernel<<<1, 32, 0, ctx->stream>>>(didx, dval, n_loads, m.nflag, m.hang_node, m.hang_master,
+                                                       m.nh, f_dev);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -269,7 +346,6 @@ int tm_build_rhs(tm_ctx *ctx, int64_t n_loads, const int32_t *node_xyz, const in
     cudaFree(dval);
     TM_CUDA(ctx, e);
   }
-  TM_CUDA(ctx, launch_rhs_fold(m, f_dev, ctx->stream));
   return TM_OK;
 }
 
@@ -278,8 +354,10 @@ int tm_apply_K(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double *
   TM_CHECK_MESH(ctx);
   if (!rho_dev || !x_dev || !y_dev) return fail(ctx, TM_EINVAL, "null pointer");
   TM_CUDA(ctx, launch_coeff(ctx->dm, ctx->w, rho_dev, ctx->stream));
-  TM_CUDA(ctx, launch_apply<double>(ctx->dm, ctx->w.ce64, x_dev, y_dev, ctx->w.part64, nullptr, nullptr, ctx->stream));
-  return TM_OK;
+  ctx->launches += 1;
+  int rc = timed_apply<double>(ctx, ctx->w.ce64, x_dev, y_dev, ctx->w.part64, nullptr, nullptr, true, nullptr);
+  if (rc) return rc;
+  return drain_profile(ctx, false);
 }
 
 int tm_apply_K_f32(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float *y_dev) {
@@ -287,8 +365,10 @@ int tm_apply_K_f32(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float
   TM_CHECK_MESH(ctx);
   if (!rho_dev || !x_dev || !y_dev) return fail(ctx, TM_EINVAL, "null pointer");
   TM_CUDA(ctx, launch_coeff(ctx->dm, ctx->w, rho_dev, ctx->stream));
-  TM_CUDA(ctx, launch_apply<float>(ctx->dm, ctx->w.ce32, x_dev, y_dev, ctx->w.part32, nullptr, nullptr, ctx->stream));
-  return TM_OK;
+  ctx->launches += 1;
+  int rc = timed_apply<float>(ctx, ctx->w.ce32, x_dev, y_dev, ctx->w.part32, nullptr, nullptr, true, nullptr);
+  if (rc) return rc;
+  return drain_profile(ctx, false);
 }
 
 int tm_jacobi_diag(tm_ctx *ctx, const double *rho_dev, double *d_dev) {
@@ -297,6 +377,7 @@ int tm_jacobi_diag(tm_ctx *ctx, const double *rho_dev, double *d_dev) {
   if (!rho_dev || !d_dev) return fail(ctx, TM_EINVAL, "null pointer");
   TM_CUDA(ctx, launch_coeff(ctx->dm, ctx->w, rho_dev, ctx->stream));
   TM_CUDA(ctx, launch_diag(ctx->dm, ctx->w.ce64, d_dev, nullptr, nullptr, ctx->stream));
+  ctx->launches += 2;
   return TM_OK;
 }
 
@@ -305,6 +386,29 @@ int tm_expand(tm_ctx *ctx, const double *u_dev, double *u_full_dev) {
   TM_CHECK_MESH(ctx);
   if (!u_dev || !u_full_dev) return fail(ctx, TM_EINVAL, "null pointer");
   TM_CUDA(ctx, launch_expand(ctx->dm, u_dev, u_full_dev, ctx->stream));
+  ctx->launches += ctx->dm.nh > 0 ? 2 : 1;
+  return TM_OK;
+}
+
+int tm_profile(tm_ctx *ctx, int enable) {
+  TM_CHECK_CTX(ctx);
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  int rc = drain_profile(ctx, true);
+  if (rc) return rc;
+  ctx->prof_on = enable != 0;
+  ctx->launches = 0;
+  ctx->prof = tm_profile_data();
+  return TM_OK;
+}
+
+int tm_profile_read(tm_ctx *ctx, tm_profile_data *out) {
+  TM_CHECK_CTX(ctx);
+  if (!out) return fail(ctx, TM_EINVAL, "null pointer");
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  int rc = drain_profile(ctx, true);
+  if (rc) return rc;
+  *out = ctx->prof;
+  out->launches = ctx->launches;
   return TM_OK;
 }
 
@@ -312,10 +416,6 @@ int tm_expand(tm_ctx *ctx, const double *u_dev, double *u_full_dev) {
 
 // ---------------------------------------------------------------- solver drivers
 namespace {
-
-struct HostScalars {
-  SolveScalars s;
-};
 
 int init_run(tm_ctx *ctx, double stop_ratio2, double stop_abs_rr, int max_it) {
   SolveScalars s;
@@ -331,23 +431,22 @@ int init_run(tm_ctx *ctx, double stop_ratio2, double stop_abs_rr, int max_it) {
 int read_run(tm_ctx *ctx, SolveScalars *s) {
   TM_CUDA(ctx, cudaMemcpyAsync(s, solve_scalars(ctx), sizeof(*s), cudaMemcpyDeviceToHost, ctx->stream));
   TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  return TM_OK;
+  return drain_profile(ctx, false);
 }
 
-// Enqueue `count` CG iterations on vectors of type T (operator coefficient ce,
-// partial buffer part), solution x of type TX.
+// Enqueue `count` CG iterations on vectors of type T (operator coefficients ce,
+// partials part), solution x of type TX.  Four launches per iteration.
 template <typename TX, typename T>
 int enqueue_iterations(tm_ctx *ctx, int count, const T *ce, T *part, TX *x, T *r, T *p, T *q, const T *dinv) {
-  const DeviceMesh &m = ctx->dm;
   Work &w = ctx->w;
   SolveScalars *sc = solve_scalars(ctx);
-  const int64_t n = 3 * m.Nn;
-  const int nshared_grid = shared_grid(m.nsh + m.nh);
+  const int64_t n = 3 * ctx->dm.Nn;
   for (int k = 0; k < count; ++k) {
-    TM_CUDA(ctx, launch_apply<T>(m, ce, p, q, part, w.red, &sc->done, ctx->stream));
-    TM_CUDA(ctx, launch_alpha(w.red, m.nblk + nshared_grid, sc, ctx->stream));
+    int rc = timed_apply<T>(ctx, ce, p, q, part, w.red, sc, false, &sc->done);
+    if (rc) return rc;
     TM_CUDA(ctx, launch_update<TX, T>(x, p, q, r, dinv, n, sc, w.red, w.ticket, ctx->stream));
     TM_CUDA(ctx, launch_pupdate<T>(p, r, dinv, n, sc, ctx->stream));
+    ctx->launches += 2;
   }
   return TM_OK;
 }
@@ -359,9 +458,20 @@ int run_cg(tm_ctx *ctx, int check_every, int *iters_out, int *nonfinite, const T
   int rc = read_run(ctx, &s);
   if (rc) return rc;
   while (!s.done) {
+    const int it_before = s.it;
+    const size_t base = ctx->ev_pending.size();
     rc = enqueue_iterations<TX, T>(ctx, check_every, ce, part, x, r, p, q, dinv);
     if (rc) return rc;
-    rc = read_run(ctx, &s);
+    TM_CUDA(ctx, cudaMemcpyAsync(&s, solve_scalars(ctx), sizeof(s), cudaMemcpyDeviceToHost, ctx->stream));
+    TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    // applications enqueued after convergence returned at once: not timed work
+    const size_t real = base + (size_t)(s.it - it_before);
+    while (ctx->ev_pending.size() > real) {
+      ctx->ev_free.push_back(ctx->ev_pending.back().e0);
+      ctx->ev_free.push_back(ctx->ev_pending.back().e1);
+      ctx->ev_pending.pop_back();
+    }
+    rc = drain_profile(ctx, true);
     if (rc) return rc;
   }
   *iters_out = s.it;
@@ -395,6 +505,7 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
   TM_CUDA(ctx, launch_mask(m.nflag, u_dev, m.Nn, st));
   double *ff_dev = scal_at(ctx, 82), *rr_dev = scal_at(ctx, 81);
   TM_CUDA(ctx, launch_residual64(f_dev, nullptr, nullptr, n, ff_dev, w.red, w.ticket + 1, st));
+  ctx->launches += 4;
   double ff = 0;
   int rc = read_scalar(ctx, ff_dev, &ff);
   if (rc) return rc;
@@ -407,13 +518,16 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
     const double target = opts->rtol * opts->rtol * ff;
     int left = opts->max_iter;
     double rel = 0;
+    TM_CUDA(ctx, cudaMemsetAsync(w.q, 0, n * sizeof(double), st));
     for (int restart = 0; restart < 8; ++restart) {
       // r = f - A u (true residual), p = Dinv r
-      TM_CUDA(ctx, launch_apply<double>(m, w.ce64, u_dev, w.q, w.part64, nullptr, nullptr, st));
+      rc = timed_apply<double>(ctx, w.ce64, u_dev, w.q, w.part64, nullptr, nullptr, true, nullptr);
+      if (rc) return rc;
       out.fp64_applies++;
       rc = init_run(ctx, 0.0, target, left);
       if (rc) return rc;
       TM_CUDA(ctx, launch_start<double>(f_dev, w.q, 1.0, w.r, w.p, w.dinv, n, solve_scalars(ctx), w.red, w.ticket + 2, st));
+      ctx->launches += 1;
       int it = 0, nf = 0;
       rc = run_cg<double, double>(ctx, check, &it, &nf, w.ce64, w.part64, u_dev, w.r, w.p, w.q, w.dinv);
       if (rc) return rc;
@@ -422,9 +536,11 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
       left -= it;
       if (nf) return fail(ctx, TM_ENONFINITE, "non-finite value in CG");
       // verify with the true residual
-      TM_CUDA(ctx, launch_apply<double>(m, w.ce64, u_dev, w.q, w.part64, nullptr, nullptr, st));
+      rc = timed_apply<double>(ctx, w.ce64, u_dev, w.q, w.part64, nullptr, nullptr, true, nullptr);
+      if (rc) return rc;
       out.fp64_applies++;
       TM_CUDA(ctx, launch_residual64(f_dev, w.q, nullptr, n, rr_dev, w.red, w.ticket + 1, st));
+      ctx->launches += 1;
       double rr = 0;
       rc = read_scalar(ctx, rr_dev, &rr);
       if (rc) return rc;
@@ -439,10 +555,13 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
     const double inner = opts->inner_rtol > 0 ? opts->inner_rtol : 1e-3;
     int left = opts->max_iter;
     double rel = 0;
+    TM_CUDA(ctx, cudaMemsetAsync(w.q32, 0, n * sizeof(float), st));
     for (int sweep = 0; sweep < 64; ++sweep) {
-      TM_CUDA(ctx, launch_apply<double>(m, w.ce64, u_dev, w.q, w.part64, nullptr, nullptr, st));
+      rc = timed_apply<double>(ctx, w.ce64, u_dev, w.q, w.part64, nullptr, nullptr, true, nullptr);
+      if (rc) return rc;
       out.fp64_applies++;
       TM_CUDA(ctx, launch_residual64(f_dev, w.q, w.r, n, rr_dev, w.red, w.ticket + 1, st));
+      ctx->launches += 1;
       double rr = 0;
       rc = read_scalar(ctx, rr_dev, &rr);
       if (rc) return rc;
@@ -458,6 +577,7 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
       TM_CUDA(ctx, cudaMemsetAsync(w.x32, 0, n * sizeof(float), st));
       TM_CUDA(ctx, launch_start<float>(w.r, nullptr, scale, w.r32, w.p32, w.dinv32, n, solve_scalars(ctx), w.red,
                                        w.ticket + 2, st));
+      ctx->launches += 1;
       int it = 0, nf = 0;
       rc = run_cg<float, float>(ctx, check, &it, &nf, w.ce32, w.part32, w.x32, w.r32, w.p32, w.q32, w.dinv32);
       if (rc) return rc;
@@ -466,6 +586,7 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
       left -= it;
       if (nf) return fail(ctx, TM_ENONFINITE, "non-finite value in the FP32 sweep");
       TM_CUDA(ctx, launch_correct(u_dev, w.x32, 1.0 / scale, n, st));
+      ctx->launches += 1;
     }
     out.rel_residual = rel;
     if (rel > opts->rtol) status = TM_ENOTCONVERGED;
@@ -475,6 +596,8 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
   float ms = 0;
   TM_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
   out.seconds = ms * 1e-3;
+  rc = drain_profile(ctx, false);
+  if (rc) return rc;
   if (stats) *stats = out;
   if (status == TM_ENOTCONVERGED) return fail(ctx, status, "max_iter reached before rtol");
   return status;
@@ -488,6 +611,7 @@ int tm_sensitivity(tm_ctx *ctx, const double *rho_dev, const double *u_full_dev,
   double *cdev = scal_at(ctx, 80);
   TM_CUDA(ctx, launch_sensitivity(ctx->dm, rho_dev, u_full_dev, dc_dev, ctx->w.red, ctx->w.ticket + 3, cdev,
                                   ctx->stream));
+  ctx->launches += 1;
   if (compliance_out) return read_scalar(ctx, cdev, compliance_out);
   return TM_OK;
 }
@@ -499,6 +623,7 @@ int tm_filter(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double rm
   if (mode != 0 && mode != 1) return fail(ctx, TM_EINVAL, "mode must be 0 or 1");
   if (!(rmin > 0) || rmin > 4.0 * ctx->dm.hmin) return fail(ctx, TM_EINVAL, "rmin must be in (0, 4 h_min]");
   TM_CUDA(ctx, launch_filter(ctx->dm, rho_dev, x_dev, rmin, mode, out_dev, ctx->stream));
+  ctx->launches += 1;
   return TM_OK;
 }
 
@@ -516,6 +641,7 @@ int tm_oc_update(tm_ctx *ctx, const double *rho_dev, const double *dc_dev, doubl
   TM_CUDA(ctx, cudaMemcpyAsync(oc_state(ctx), &s, sizeof(s), cudaMemcpyHostToDevice, ctx->stream));
   TM_CUDA(ctx, launch_oc(ctx->dm, rho_dev, dc_dev, eta, move, rho_min, rho_new_dev, ctx->w.red, ctx->w.ticket + 4,
                          oc_state(ctx), 200, ctx->stream));
+  ctx->launches += 202;
   if (change_out) return read_scalar(ctx, &oc_state(ctx)->change, change_out);
   TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return TM_OK;

@@ -1,7 +1,6 @@
 // Operator kernels: y = C^T K(rho) C x on the A-space (paper Eq. 6-7), the
 // element coefficients c_e = (Emin + rho_e^p (E0 - Emin)) h_e (Eq. 2), the
-// Jacobi diagonal of Sec. 5, the expansion u_full = C u (Eq. 9) and the load
-// fold f = C^T f_full.
+// Jacobi diagonal of Sec. 5 and the expansion u_full = C u (Eq. 9).
 //
 // Operator layout (one CTA per block of consecutive elements, tables built by
 // mesh_host.cpp).  A block's local nodes are its regular nodes followed by the
@@ -22,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include "element.cuh"
+#include "pcg.cuh"
 #include "reduce.cuh"
 #include "tm_internal.h"
 
@@ -33,7 +33,7 @@ constexpr int kRow = 25;                    // padded per-element row of the slo
 template <typename T>
 struct ApplyParams {
   const int32_t *blk_elem, *blk_node, *blk_shared, *blk_slot, *blk_hang, *blk_iptr, *blk_inv;
-  const int32_t *lnode;
+  const int32_t *lnode, *lslot;
   const uint16_t *hent, *iptr, *inv;
   const uint8_t *nflag;
   const T *ce;
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(T) == 4 ? 4 : 2) apply_b
     const int g = P.lnode[n0 + i];
     if (P.nflag[g] & 1) s0 = s1 = s2 = T(0);
     if (i < nshared) {
-      T *dst = P.part + 3 * (size_t)(slot0 + i);
+      T *dst = P.part + 3 * (size_t)P.lslot[slot0 + i];
       dst[0] = s0; dst[1] = s1; dst[2] = s2;
     } else {
       T *dst = P.y + 3 * (size_t)g;
@@ -159,14 +159,17 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(T) == 4 ? 4 : 2) apply_b
   }
 }
 
-// Second pass: shared nodes sum their slots in ascending block order; hanging
-// DOFs of y are zeroed.  Optional x . y partials continue after the first pass.
+// Second pass: each shared node sums its contiguous run of partials (one per
+// block touching it, in ascending block order); optionally hanging DOFs of y are
+// zeroed.  With dot partials, the last CTA also finishes p^T A p and sets
+// alpha = rz / pq for CG (when sc is given).
 template <typename T>
-__global__ void __launch_bounds__(256) apply_shared_kernel(const int32_t *sh_node, const int32_t *sh_ptr,
-                                                           const int32_t *sh_slot, int64_t nsh,
+__global__ void __launch_bounds__(256) apply_shared_kernel(const int32_t *sh_node, const int32_t *sh_ptr, int64_t nsh,
                                                            const int32_t *hang_node, int64_t nh,
                                                            const uint8_t *nflag, const T *part, const T *x,
-                                                           T *y, double *dotp, const int *done) {
+                                                           T *y, double *dotp, int nblk_partials,
+                                                           SolveScalars *sc, unsigned int *ticket,
+                                                           const int *done) {
   if (done && *(volatile const int *)done) return;
   double dot = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nsh + nh;
@@ -175,15 +178,15 @@ __global__ void __launch_bounds__(256) apply_shared_kernel(const int32_t *sh_nod
       const int g = sh_node[i];
       T s0 = T(0), s1 = T(0), s2 = T(0);
       for (int j = sh_ptr[i]; j < sh_ptr[i + 1]; ++j) {
-        const T *src = part + 3 * (size_t)sh_slot[j];
+        const T *src = part + 3 * (size_t)j;
         s0 += src[0]; s1 += src[1]; s2 += src[2];
       }
-      if (nflag[g] & 1) s0 = s1 = s2 = T(0);
       T *dst = y + 3 * (size_t)g;
       dst[0] = s0; dst[1] = s1; dst[2] = s2;
-      if (dotp && !(nflag[g] & 1)) {
+      if (dotp) {
         const T *xv = x + 3 * (size_t)g;
-        dot += (double)xv[0] * (double)s0 + (double)xv[1] * (double)s1 + (double)xv[2] * (double)s2;
+        if (!(nflag[g] & 1))
+          dot += (double)xv[0] * (double)s0 + (double)xv[1] * (double)s1 + (double)xv[2] * (double)s2;
       }
     } else {
       T *dst = y + 3 * (size_t)hang_node[i - nsh];
@@ -192,7 +195,18 @@ __global__ void __launch_bounds__(256) apply_shared_kernel(const int32_t *sh_nod
   }
   if (dotp) {
     dot = block_sum<256>(dot);
-    if (threadIdx.x == 0) dotp[blockIdx.x] = dot;
+    if (threadIdx.x == 0) dotp[nblk_partials + blockIdx.x] = dot;
+    if (sc && last_cta(ticket)) {
+      const double pq = sum_partials<256>(dotp, nblk_partials + gridDim.x);
+      if (threadIdx.x == 0) {
+        sc->pq = pq;
+        sc->alpha = sc->rz / pq;
+        if (!isfinite(pq) || !isfinite(sc->alpha) || pq <= 0.0) {
+          sc->nonfinite = 1;
+          sc->done = 1;
+        }
+      }
+    }
   }
 }
 
@@ -205,7 +219,8 @@ int shared_grid(int64_t n) {
 
 template <typename T>
 cudaError_t launch_apply(const DeviceMesh &m, const T *ce, const T *x, T *y, T *part, double *dot_partials,
-                         const int *done, cudaStream_t s) {
+                         SolveScalars *sc, unsigned int *ticket, bool zero_hanging, const int *done,
+                         cudaStream_t s) {
   static size_t configured = 0;
   const size_t smem = apply_smem_bytes<T>(m.max_local);
   if (smem > configured) {
@@ -216,22 +231,23 @@ cudaError_t launch_apply(const DeviceMesh &m, const T *ce, const T *x, T *y, T *
   }
   ApplyParams<T> P;
   P.blk_elem = m.blk_elem; P.blk_node = m.blk_node; P.blk_shared = m.blk_shared; P.blk_slot = m.blk_slot;
-  P.blk_hang = m.blk_hang; P.blk_iptr = m.blk_iptr; P.blk_inv = m.blk_inv; P.lnode = m.lnode; P.hent = m.hent;
-  P.iptr = m.iptr; P.inv = m.inv; P.nflag = m.nflag; P.ce = ce; P.x = x; P.y = y; P.part = part;
+  P.blk_hang = m.blk_hang; P.blk_iptr = m.blk_iptr; P.blk_inv = m.blk_inv; P.lnode = m.lnode; P.lslot = m.lslot;
+  P.hent = m.hent; P.iptr = m.iptr; P.inv = m.inv; P.nflag = m.nflag; P.ce = ce; P.x = x; P.y = y; P.part = part;
   P.dotp = dot_partials; P.done = done; P.lam = (T)m.lam; P.mu = (T)m.mu;
   if (m.nblk > 0) apply_blocks_kernel<T><<<m.nblk, kApplyThreads, smem, s>>>(P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  apply_shared_kernel<T><<<shared_grid(m.nsh + m.nh), 256, 0, s>>>(
-      m.sh_node, m.sh_ptr, m.sh_slot, m.nsh, m.hang_node, m.nh, m.nflag, part, x, y,
-      dot_partials ? dot_partials + m.nblk : nullptr, done);
+  const int64_t items = m.nsh + (zero_hanging ? m.nh : 0);
+  apply_shared_kernel<T><<<shared_grid(items), 256, 0, s>>>(m.sh_node, m.sh_ptr, m.nsh, m.hang_node,
+                                                            zero_hanging ? m.nh : 0, m.nflag, part, x, y,
+                                                            dot_partials, m.nblk, sc, ticket, done);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_apply<double>(const DeviceMesh &, const double *, const double *, double *, double *,
-                                          double *, const int *, cudaStream_t);
+                                          double *, SolveScalars *, unsigned int *, bool, const int *, cudaStream_t);
 template cudaError_t launch_apply<float>(const DeviceMesh &, const float *, const float *, float *, float *,
-                                         double *, const int *, cudaStream_t);
+                                         double *, SolveScalars *, unsigned int *, bool, const int *, cudaStream_t);
 
 // ---------------------------------------------------------------- coefficients
 __device__ __forceinline__ double simp_power(double r, double p) {
@@ -325,38 +341,6 @@ cudaError_t launch_expand(const DeviceMesh &m, const double *u, double *uf, cuda
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || m.nh == 0) return e;
   expand_hanging_kernel<<<shared_grid(m.nh), 256, 0, s>>>(m.hang_node, m.hang_master, m.nh, m.nflag, u, uf);
-  return cudaGetLastError();
-}
-
-// f (full nodal loads) -> C^T f in place: each hanging node's load goes to its
-// free masters with the interpolation weights; constrained entries become 0.
-// One thread walks the hanging list in order (loads are few and this runs once).
-__global__ void rhs_fold_kernel(const int32_t *hang_node, const int32_t *hang_master, int64_t nh,
-                                const uint8_t *nflag, double *f, int64_t Nn) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  for (int64_t i = 0; i < nh; ++i) {
-    const int h = hang_node[i];
-    const double f0 = f[3 * h], f1 = f[3 * h + 1], f2 = f[3 * h + 2];
-    if (f0 == 0.0 && f1 == 0.0 && f2 == 0.0) continue;
-    const int nm = hang_master[4 * i + 2] < 0 ? 2 : 4;
-    const double w = nm == 2 ? 0.5 : 0.25;
-    for (int q = 0; q < nm; ++q) {
-      const int mm = hang_master[4 * i + q];
-      f[3 * mm] += w * f0; f[3 * mm + 1] += w * f1; f[3 * mm + 2] += w * f2;
-    }
-  }
-}
-
-__global__ void mask_constrained_kernel(const uint8_t *nflag, double *f, int64_t Nn) {
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < Nn; n += (int64_t)gridDim.x * blockDim.x)
-    if (nflag[n]) f[3 * n] = f[3 * n + 1] = f[3 * n + 2] = 0.0;
-}
-
-cudaError_t launch_rhs_fold(const DeviceMesh &m, double *f, cudaStream_t s) {
-  if (m.nh > 0) rhs_fold_kernel<<<1, 32, 0, s>>>(m.hang_node, m.hang_master, m.nh, m.nflag, f, m.Nn);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  mask_constrained_kernel<<<shared_grid(m.Nn), 256, 0, s>>>(m.nflag, f, m.Nn);
   return cudaGetLastError();
 }
 

@@ -3,7 +3,7 @@
 // reductions finalised on the device, so the iteration needs no host round trip.
 //
 // Iteration (x: solution, z = Dinv r is never stored):
-//   q = A p ; pq = p.q (fused into the operator's second pass)      alpha = rz / pq
+//   q = A p ; pq = p.q and alpha = rz / pq (fused into the operator's passes)
 //   x += alpha p ; r -= alpha q ; rz' = r.Dinv r ; rr = r.r          beta = rz' / rz
 //   p = Dinv r + beta p
 // Every kernel returns immediately once the device flag `done` is set, so a
@@ -21,20 +21,6 @@ constexpr int kVecThreads = 256;
 
 __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 
-// pq = sum of operator partials; alpha = rz / pq.
-__global__ void alpha_kernel(const double *partials, int n, SolveScalars *sc) {
-  if (sc->done) return;
-  const double pq = sum_partials<kVecThreads>(partials, n);
-  if (threadIdx.x == 0) {
-    sc->pq = pq;
-    sc->alpha = sc->rz / pq;
-    if (!finite(pq) || !finite(sc->alpha) || pq <= 0.0) {
-      sc->nonfinite = 1;
-      sc->done = 1;
-    }
-  }
-}
-
 template <typename TX, typename T>
 __global__ void __launch_bounds__(kVecThreads) update_kernel(TX *x, const T *p, const T *q, T *r, const T *dinv,
                                                              int64_t n, SolveScalars *sc, double *partials,
@@ -42,15 +28,15 @@ __global__ void __launch_bounds__(kVecThreads) update_kernel(TX *x, const T *p, 
   if (sc->done) return;
   const double alpha = sc->alpha;
   const T a = (T)alpha;
-  double rz = 0.0, rr = 0.0;
+  DotAcc<T> arz, arr;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     x[i] += (TX)alpha * (TX)p[i];
     const T ri = r[i] - a * q[i];
     r[i] = ri;
-    const double rd = (double)ri;
-    rz += rd * (double)(dinv[i] * ri);
-    rr += rd * rd;
+    arz.add_prod(ri, dinv[i] * ri);
+    arr.add_prod(ri, ri);
   }
+  double rz = arz.value(), rr = arr.value();
   block_sum2<kVecThreads>(rz, rr);
   if (threadIdx.x == 0) {
     partials[2 * blockIdx.x] = rz;
@@ -93,15 +79,16 @@ template <typename T>
 __global__ void __launch_bounds__(kVecThreads) start_kernel(const double *f, const double *q, double scale, T *r,
                                                             T *p, const T *dinv, int64_t n, SolveScalars *sc,
                                                             double *partials, unsigned int *ticket) {
-  double rz = 0.0, rr = 0.0;
+  DotAcc<T> arz, arr;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const T ri = (T)(scale * (f[i] - (q ? q[i] : 0.0)));
     r[i] = ri;
     const T zi = dinv[i] * ri;
     p[i] = zi;
-    rz += (double)ri * (double)zi;
-    rr += (double)ri * (double)ri;
+    arz.add_prod(ri, zi);
+    arr.add_prod(ri, ri);
   }
+  double rz = arz.value(), rr = arr.value();
   block_sum2<kVecThreads>(rz, rr);
   if (threadIdx.x == 0) {
     partials[2 * blockIdx.x] = rz;
@@ -168,11 +155,6 @@ int vec_grid(int64_t n) {
   if (g < 1) g = 1;
   if (g > 152 * 8) g = 152 * 8;
   return (int)g;
-}
-
-cudaError_t launch_alpha(const double *partials, int n, SolveScalars *sc, cudaStream_t s) {
-  alpha_kernel<<<1, kVecThreads, 0, s>>>(partials, n, sc);
-  return cudaGetLastError();
 }
 
 template <typename TX, typename T>

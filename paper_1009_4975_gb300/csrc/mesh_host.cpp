@@ -423,7 +423,10 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
   }
   m.max_local = max_local;
 
-  // ---- 7. second-pass CSR over shared nodes: slots in ascending block order
+  // ---- 7. second pass over shared nodes: the partials of a shared node are
+  // contiguous (node-major CSR, ascending block order inside a node), so the
+  // second pass streams them; each block writes its shared nodes' partials to
+  // their CSR positions (lslot).
   {
     std::vector<int32_t> cnt(Nn + 1, 0);
     for (int32_t b = 0; b < nblk; ++b)
@@ -431,11 +434,11 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     std::vector<int32_t> start(Nn + 1, 0);
     for (int64_t n = 0; n < Nn; ++n) start[n + 1] = start[n] + cnt[n + 1];
     std::vector<int32_t> fill(start.begin(), start.end() - 1);
-    m.sh_slot.assign(start[Nn], 0);
+    m.lslot.assign(m.blk_slot[nblk], 0);
     for (int32_t b = 0; b < nblk; ++b)
       for (int32_t i = 0; i < m.blk_shared[b]; ++i) {
         const int32_t n = m.lnode[m.blk_node[b] + i];
-        m.sh_slot[fill[n]++] = m.blk_slot[b] + i;
+        m.lslot[m.blk_slot[b] + i] = fill[n]++;
       }
     m.sh_ptr.push_back(0);
     for (int64_t n = 0; n < Nn; ++n)
@@ -443,7 +446,6 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
         m.sh_node.push_back((int32_t)n);
         m.sh_ptr.push_back(start[n + 1]);
       }
-    // sh_ptr must index into sh_slot compacted by node: start[] is already compact
   }
 
   // ---- 8. Jacobi diagonal coefficients: d_{m,c} = sum_e c_e q_{e,m,c}

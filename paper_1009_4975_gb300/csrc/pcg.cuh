@@ -16,7 +16,6 @@ struct SolveScalars {
 };
 
 int vec_grid(int64_t n);
-cudaError_t launch_alpha(const double *partials, int n, SolveScalars *sc, cudaStream_t s);
 template <typename TX, typename T>
 cudaError_t launch_update(TX *x, const T *p, const T *q, T *r, const T *dinv, int64_t n, SolveScalars *sc,
                           double *partials, unsigned int *ticket, cudaStream_t s);

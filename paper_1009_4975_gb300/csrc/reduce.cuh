@@ -78,4 +78,37 @@ __device__ __forceinline__ double sum_partials(const volatile double *p, int n) 
   return block_sum<NT>(s);
 }
 
+// Sum of exact products in FP32 pairs (the Dot2 scheme of Ogita, Rump and Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005): the product
+// error comes from an FMA, the addition error from TwoSum, and the collected
+// errors are carried in a second FP32 word.  The result is accurate as if
+// accumulated in twice the working precision; it is converted to FP64 before
+// the cross-thread reduction.  For FP64 inputs it is a plain FP64 sum.
+struct Acc2 {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float se = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += se + pe;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+template <typename T>
+struct DotAcc {
+  double s = 0.0;
+  __device__ __forceinline__ void add_prod(T a, T b) { s += (double)a * (double)b; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+  Acc2 a;
+  __device__ __forceinline__ void add_prod(float x, float y) { a.add_prod(x, y); }
+  __device__ __forceinline__ double value() const { return a.value(); }
+};
+
 }  // namespace amr

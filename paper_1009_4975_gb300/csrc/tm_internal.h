@@ -47,18 +47,18 @@ struct HostMesh {
   std::vector<int32_t> blk_elem;      // nblk+1: element ranges
   std::vector<int32_t> blk_node;      // nblk+1: regular local node ranges in lnode
   std::vector<int32_t> blk_shared;    // nblk: regular local nodes [0, shared) are shared
-  std::vector<int32_t> blk_slot;      // nblk+1: slot range of the block's shared nodes
+  std::vector<int32_t> blk_slot;      // nblk+1: the block's shared nodes' range in lslot
   std::vector<int32_t> blk_hang;      // nblk+1: hanging ranges in hent
   std::vector<int32_t> blk_iptr;      // nblk+1: ranges in iptr (local nodes + 1)
   std::vector<int32_t> blk_inv;       // nblk: base of the block's entries in inv
   std::vector<int32_t> lnode;         // regular local node -> global node
+  std::vector<int32_t> lslot;         // shared local node -> its partial's position (node-major CSR)
   std::vector<uint16_t> hent;         // 4 per hanging local node: masters' local ids (0xFFFF pad)
   std::vector<uint16_t> iptr;         // inverse-list offsets, relative to blk_inv[b]
   std::vector<uint16_t> inv;          // inverse-list entries
   // second pass over shared nodes
   std::vector<int32_t> sh_node;       // shared node ids
-  std::vector<int32_t> sh_ptr;        // CSR into sh_slot
-  std::vector<int32_t> sh_slot;
+  std::vector<int32_t> sh_ptr;        // CSR: partials of shared node i are [sh_ptr[i], sh_ptr[i+1])
   // Jacobi diagonal: node-centric CSR of (element, coefficient-triple index)
   std::vector<int32_t> dg_ptr;        // Nn+1
   std::vector<int32_t> dg_elem;
@@ -100,10 +100,10 @@ struct DeviceMesh {
   int32_t *hang_master = nullptr;     // 4 per
   int32_t *blk_elem = nullptr, *blk_node = nullptr, *blk_shared = nullptr, *blk_slot = nullptr,
           *blk_hang = nullptr, *blk_iptr = nullptr, *blk_inv = nullptr;
-  int32_t *lnode = nullptr;
+  int32_t *lnode = nullptr, *lslot = nullptr;
   uint16_t *hent = nullptr, *iptr = nullptr, *inv = nullptr;
   int32_t max_local = 0;
-  int32_t *sh_node = nullptr, *sh_ptr = nullptr, *sh_slot = nullptr;
+  int32_t *sh_node = nullptr, *sh_ptr = nullptr;
   int32_t *dg_ptr = nullptr, *dg_elem = nullptr;
   uint16_t *dg_q = nullptr;
   double *dg_tab = nullptr;
@@ -141,17 +141,30 @@ struct tm_ctx {
   amr::DeviceMesh dm;
   amr::Work w;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // profiling (tm_profile): kernel launch count and CUDA-event operator timing
+  bool prof_on = false;
+  int64_t launches = 0;
+  tm_profile_data prof = tm_profile_data();
+  struct Pending {
+    cudaEvent_t e0, e1;
+    int kind;  // 1: FP32 operator, 0: FP64 operator
+  };
+  std::vector<Pending> ev_pending;
+  std::vector<cudaEvent_t> ev_free;
 };
 
 namespace amr {
 // device-side launchers of the operator file; each returns the launch's cudaError_t
 cudaError_t launch_coeff(const DeviceMesh &m, const Work &w, const double *rho, cudaStream_t s);
+struct SolveScalars;
+// y = C^T K C x.  With dot_partials: also x . y; with sc: alpha = sc->rz / (x . y)
+// computed by the last CTA of the second pass (ticket: its counter).
 template <typename T>
 cudaError_t launch_apply(const DeviceMesh &m, const T *ce, const T *x, T *y, T *part, double *dot_partials,
-                         const int *done, cudaStream_t s);
+                         SolveScalars *sc, unsigned int *ticket, bool zero_hanging, const int *done,
+                         cudaStream_t s);
 cudaError_t launch_diag(const DeviceMesh &m, const double *ce, double *d, double *dinv, float *dinv32,
                         cudaStream_t s);
 cudaError_t launch_expand(const DeviceMesh &m, const double *u, double *uf, cudaStream_t s);
-cudaError_t launch_rhs_fold(const DeviceMesh &m, double *f, cudaStream_t s);
 int shared_grid(int64_t n);
 }  // namespace amr

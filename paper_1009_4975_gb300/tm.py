@@ -50,9 +50,14 @@ class tm_solve_stats(C.Structure):
                 ("seconds", C.c_double), ("fp64_applies", C.c_int32), ("fp32_applies", C.c_int32)]
 
 
+class tm_profile_data(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("apply32_count", C.c_int64), ("apply64_count", C.c_int64),
+                ("apply32_ms", C.c_double), ("apply64_ms", C.c_double)]
+
+
 EXPORTS = ["tm_create", "tm_destroy", "tm_set_stream", "tm_last_error", "tm_mesh_upload", "tm_mesh_tables",
            "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_jacobi_diag", "tm_pcg_solve", "tm_expand",
-           "tm_sensitivity", "tm_filter", "tm_oc_update"]
+           "tm_sensitivity", "tm_filter", "tm_oc_update", "tm_profile", "tm_profile_read"]
 
 _lib = None
 
@@ -81,6 +86,8 @@ def load_library(path: str = LIB_PATH):
         "tm_sensitivity": [vp, vp, vp, vp, C.POINTER(dbl)],
         "tm_filter": [vp, vp, vp, dbl, C.c_int, vp],
         "tm_oc_update": [vp, vp, vp, dbl, dbl, dbl, dbl, vp, C.POINTER(dbl)],
+        "tm_profile": [vp, C.c_int],
+        "tm_profile_read": [vp, C.POINTER(tm_profile_data)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -284,3 +291,13 @@ def tm_oc_update(ctx: Ctx, rho, dc, volfrac, move, eta, rho_min, rho_new) -> flo
     ctx.check(load_library().tm_oc_update(ctx.handle, _elem(ctx, rho, "rho"), _elem(ctx, dc, "dc"), volfrac, move,
                                           eta, rho_min, _elem(ctx, rho_new, "rho_new"), C.byref(ch)))
     return ch.value
+
+
+def tm_profile(ctx: Ctx, enable: bool = True):
+    ctx.check(load_library().tm_profile(ctx.handle, 1 if enable else 0))
+
+
+def tm_profile_read(ctx: Ctx) -> dict:
+    d = tm_profile_data()
+    ctx.check(load_library().tm_profile_read(ctx.handle, C.byref(d)))
+    return {k: getattr(d, k) for k, _ in tm_profile_data._fields_}
