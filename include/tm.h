@@ -163,6 +163,23 @@ int tm_apply_K(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double *
  * of TM_PREC_MIXED). */
 int tm_apply_K_f32(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float *y_dev);
 
+/* The FP32 operator of tm_apply_K_f32 for callers that cannot allocate device
+ * memory at call time -- code running while a CUDA stream is being captured into
+ * a graph, callers under a strict memory budget, or hosts that forbid
+ * cudaMalloc/cudaFree after start-up.  It has no counterpart in the paper.
+ * It allocates nothing: its scratch (the element coefficients and the
+ * shared-node partials) lives in one statically sized device array of 32 MiB
+ * that every GPU loading the library holds until the process exits.  The caller
+ * passes rho, x and y as for tm_apply_K_f32; the uploaded mesh must have at most
+ * 2,097,152 elements and 2,097,152 shared-node partials, else TM_EINVAL names
+ * the sizes.  The first call on a device looks up the array's device address
+ * (module set-up, once per device, with that device current): make that first
+ * call before any stream capture.  All calls share the one array and every call
+ * overwrites all of it that it reads, so nothing carries over between calls;
+ * calls that overlap on the GPU (other streams, other contexts of the same
+ * device) race on it. */
+int tm_apply_K_f32_static(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float *y_dev);
+
 /* d_dev = diag(C^T K(rho) C) on the A-space (1 at constrained DOFs): the
  * diagonal D of the rescaling D^-1/2 K D^-1/2 of Sec. 5. */
 int tm_jacobi_diag(tm_ctx *ctx, const double *rho_dev, double *d_dev);

@@ -371,6 +371,24 @@ int tm_apply_K_f32(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float
   return drain_profile(ctx, false);
 }
 
+int tm_apply_K_f32_static(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float *y_dev) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!rho_dev || !x_dev || !y_dev) return fail(ctx, TM_EINVAL, "null pointer");
+  const DeviceMesh &m = ctx->dm;
+  if (m.Ne > kStaticElems || m.nslot > kStaticSlots)
+    return fail(ctx, TM_EINVAL,
+                "mesh too large for the static scratch of tm_apply_K_f32_static: " + std::to_string(m.Ne) +
+                    " elements (max " + std::to_string(kStaticElems) + "), " + std::to_string(m.nslot) +
+                    " shared-node partials (max " + std::to_string(kStaticSlots) + ")");
+  float *ce = nullptr, *part = nullptr;
+  TM_CUDA(ctx, static_scratch(ctx->device, &ce, &part));
+  TM_CUDA(ctx, launch_coeff_f32(m, rho_dev, ce, ctx->stream));
+  TM_CUDA(ctx, launch_apply<float>(m, ce, x_dev, y_dev, part, nullptr, nullptr, nullptr, true, nullptr, ctx->stream));
+  ctx->launches += 3;
+  return TM_OK;
+}
+
 int tm_jacobi_diag(tm_ctx *ctx, const double *rho_dev, double *d_dev) {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);

@@ -264,13 +264,39 @@ __global__ void coeff_kernel(const int32_t *leaf, const double *rho, int64_t Ne,
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < Ne; e += (int64_t)gridDim.x * blockDim.x) {
     const double h = ldexp(h0, -leaf[4 * e + 3]);
     const double c = (Emin + simp_power(rho[e], penal) * (E0 - Emin)) * h;
-    ce64[e] = c;
+    if (ce64) ce64[e] = c;
     ce32[e] = (float)c;
   }
 }
 
 cudaError_t launch_coeff(const DeviceMesh &m, const Work &w, const double *rho, cudaStream_t s) {
   coeff_kernel<<<shared_grid(m.Ne), 256, 0, s>>>(m.leaf, rho, m.Ne, m.E0, m.Emin, m.penal, m.h0, w.ce64, w.ce32);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- no-allocation operator
+// Scratch of tm_apply_K_f32_static: the FP32 coefficients (kStaticElems) followed by
+// the shared-node partials (3 * kStaticSlots), 32 MiB in all, resident on every
+// device that loads the library.  Host code cannot use the symbol as a device
+// address; its address is fetched once per device with that device current.
+static __device__ __align__(256) float g_static_scratch[kStaticElems + 3 * kStaticSlots];
+static float *g_static_ptr[kStaticMaxDevices];
+
+cudaError_t static_scratch(int device, float **ce, float **part) {
+  if (device < 0 || device >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+  if (!g_static_ptr[device]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[device] = static_cast<float *>(p);
+  }
+  *ce = g_static_ptr[device];
+  *part = g_static_ptr[device] + kStaticElems;
+  return cudaSuccess;
+}
+
+cudaError_t launch_coeff_f32(const DeviceMesh &m, const double *rho, float *ce32, cudaStream_t s) {
+  coeff_kernel<<<shared_grid(m.Ne), 256, 0, s>>>(m.leaf, rho, m.Ne, m.E0, m.Emin, m.penal, m.h0, nullptr, ce32);
   return cudaGetLastError();
 }
 

@@ -167,4 +167,11 @@ cudaError_t launch_diag(const DeviceMesh &m, const double *ce, double *d, double
                         cudaStream_t s);
 cudaError_t launch_expand(const DeviceMesh &m, const double *u, double *uf, cudaStream_t s);
 int shared_grid(int64_t n);
+
+// Static scratch of the no-allocation operator entry point (kernels_apply.cu).
+constexpr int64_t kStaticElems = int64_t(1) << 21;   // coefficients: meshes up to 2,097,152 elements
+constexpr int64_t kStaticSlots = int64_t(1) << 21;   // shared-node partials: up to 2,097,152
+constexpr int kStaticMaxDevices = 64;
+cudaError_t static_scratch(int device, float **ce, float **part);
+cudaError_t launch_coeff_f32(const DeviceMesh &m, const double *rho, float *ce32, cudaStream_t s);
 }  // namespace amr

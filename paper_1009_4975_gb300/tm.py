@@ -56,7 +56,7 @@ class tm_profile_data(C.Structure):
 
 
 EXPORTS = ["tm_create", "tm_destroy", "tm_set_stream", "tm_last_error", "tm_mesh_upload", "tm_mesh_tables",
-           "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_jacobi_diag", "tm_pcg_solve", "tm_expand",
+           "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_apply_K_f32_static", "tm_jacobi_diag", "tm_pcg_solve", "tm_expand",
            "tm_sensitivity", "tm_filter", "tm_oc_update", "tm_profile", "tm_profile_read"]
 
 _lib = None
@@ -80,6 +80,7 @@ def load_library(path: str = LIB_PATH):
         "tm_build_rhs": [vp, i64, vp, vp, vp, vp],
         "tm_apply_K": [vp, vp, vp, vp],
         "tm_apply_K_f32": [vp, vp, vp, vp],
+        "tm_apply_K_f32_static": [vp, vp, vp, vp],
         "tm_jacobi_diag": [vp, vp, vp],
         "tm_pcg_solve": [vp, vp, vp, vp, C.POINTER(tm_solve_opts), C.POINTER(tm_solve_stats)],
         "tm_expand": [vp, vp, vp],
@@ -245,6 +246,14 @@ def tm_apply_K_f32(ctx: Ctx, rho, x, y):
     import torch
     ctx.check(load_library().tm_apply_K_f32(ctx.handle, _elem(ctx, rho, "rho"), _vec(ctx, x, torch.float32, "x"),
                                             _vec(ctx, y, torch.float32, "y")))
+
+
+def tm_apply_K_f32_static(ctx: Ctx, rho, x, y):
+    """FP32 operator that allocates nothing (scratch in a static device array); see include/tm.h."""
+    import torch
+    ctx.check(load_library().tm_apply_K_f32_static(ctx.handle, _elem(ctx, rho, "rho"),
+                                                   _vec(ctx, x, torch.float32, "x"),
+                                                   _vec(ctx, y, torch.float32, "y")))
 
 
 def tm_jacobi_diag(ctx: Ctx, rho, d):
