@@ -84,6 +84,8 @@ typedef struct {
   int32_t max_local;          /* largest local-node count of a block              */
   int64_t n_shared;           /* nodes touched by more than one block             */
   int64_t device_bytes;       /* device memory held for this mesh                 */
+  int32_t max_block_bytes;    /* table bytes of the largest block (shared memory) */
+  int32_t pad_;
 } tm_mesh_info;
 
 typedef struct {

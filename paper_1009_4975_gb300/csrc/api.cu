@@ -221,8 +221,7 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
   m.fx = h.nx << h.L; m.fy = h.ny << h.L; m.fz = h.nz << h.L;
   m.h0 = h.h0; m.hmin = std::ldexp(h.h0, -h.L);
   m.E0 = h.E0; m.Emin = h.Emin; m.penal = h.penal; m.nu = h.nu;
-  m.lam = h.nu / ((1 + h.nu) * (1 - 2 * h.nu));
-  m.mu = 0.5 / (1 + h.nu);
+  for (int i = 0; i < 72; ++i) m.modal[i] = h.modal[i];
   m.k0diag = h.K0[0];
   m.volume = (double)h.nx * h.ny * h.nz * h.h0 * h.h0 * h.h0;
   m.n_free = 3 * h.n_free_nodes;
@@ -247,6 +246,13 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
   TM_CUDA(ctx, upload(o, B, &m.hent, h.hent));
   TM_CUDA(ctx, upload(o, B, &m.iptr, h.iptr));
   TM_CUDA(ctx, upload(o, B, &m.inv, h.inv));
+  {
+    uint8_t *rec = nullptr;
+    TM_CUDA(ctx, upload(o, B, &rec, h.brec));
+    m.brec = reinterpret_cast<uint4 *>(rec);
+  }
+  TM_CUDA(ctx, upload(o, B, &m.rec_off, h.rec_off));
+  m.max_rec_bytes = h.max_rec_bytes;
   TM_CUDA(ctx, upload(o, B, &m.sh_node, h.sh_node));
   TM_CUDA(ctx, upload(o, B, &m.sh_ptr, h.sh_ptr));
   TM_CUDA(ctx, upload(o, B, &m.dg_ptr, h.dg_ptr));
@@ -263,7 +269,7 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
   std::vector<void *> &wo = w.owned;
   int64_t &WB = w.bytes;
   const size_t nv = 3 * (size_t)m.Nn;
-  w.nred = (int64_t)m.nblk + 4 * 152 * 8 + 64;
+  w.nred = (int64_t)m.nblk + (m.nsh + m.nh + 255) / 256 + 4 * 152 * 8 + 64;
   TM_CUDA(ctx, alloc(wo, WB, &w.part64, 3 * (size_t)m.nslot));
   TM_CUDA(ctx, alloc(wo, WB, &w.part32, 3 * (size_t)m.nslot));
   TM_CUDA(ctx, alloc(wo, WB, &w.ce64, (size_t)m.Ne));
@@ -293,6 +299,8 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
     info->max_local = h.max_local;
     info->n_shared = m.nsh;
     info->device_bytes = m.bytes + w.bytes;
+    info->max_block_bytes = h.max_rec_bytes;
+    info->pad_ = 0;
   }
   return TM_OK;
 }

@@ -1,101 +1,107 @@
-// The B8 element operator y_e = c * K0 x_e on the unit cube, evaluated by sum
-// factorisation over the 2x2x2 Gauss points instead of a dense 24x24 product.
+// The B8 element operator y_e = c * K0 x_e on the unit cube in a symmetry-adapted
+// basis.
 //
-// K0 = sum_q w_q B_q^T D B_q (w_q = 1/8).  For trilinear shape functions
-// N_ijk = f_i(x) f_j(y) f_k(z) (f_0 = 1 - t, f_1 = t) the displacement gradient at
-// a Gauss point is a tensor product of 2x2 interpolations of edge differences:
-//   du_c/dx (a,b,d) = sum_{j,k} M[b][j] M[d][k] (u_c(1,j,k) - u_c(0,j,k))
-// with M[a][i] = f_i(g_a), g_{0,1} = (1 -/+ 1/sqrt3)/2, and symmetrically for
-// y and z.  Stresses follow from isotropic Hooke's law (Lame constants of
-// E = 1); the transpose B^T sigma folds back through the same M (symmetric).
-// Cost: ~580 flops per element against 1152 for the dense product, and the
-// edge differences remove rigid translations before any rounding.
+// Along each axis, the pair of nodal values (u at t = 0, u at t = 1) is replaced by
+// its sum and difference; over the three axes this is a 3-stage butterfly
+// w = T x per displacement component (T has entries +-1, T T^T = 8 I).  The unit
+// cube with isotropic material is invariant under the reflection of each axis,
+// and in the butterfly basis each modal DOF (component c, mode bits b) is even or
+// odd under the three reflections (signature s, with bit a set when odd: b_a XOR
+// [a == c]).  K0 commutes with the reflections, so K0m = T K0 T^T / 64 only couples
+// DOFs of equal signature: eight 3x3 blocks, DOF c of block s being mode s ^ (1 << c).
+// The three blocks s = 1, 2, 4 contain a rigid translation (mode 0 of component
+// log2 s), whose row and column vanish; they act as 2x2 blocks.
+//
+//   y = c * T^T (K0m (T x))  -- ~72 add/sub forward, 57 FMA in the blocks,
+//                              ~72 add/sub back: ~220 flops instead of 1152 dense.
+//
+// Differences along each axis cancel rigid translations before any rounding.
+// K0m is computed on the host from the element matrix (mesh_host.cpp) and passed
+// in the kernel parameters.
 #pragma once
 
 template <typename T>
-struct GaussM {
-  static constexpr double g0 = 0.21132486540518711775;  // (1 - 1/sqrt(3)) / 2
-  static constexpr double g1 = 0.78867513459481288225;  // (1 + 1/sqrt(3)) / 2
+struct ModalBlocks {
+  T b[8][3][3];   // [signature s][row c][column c']
 };
 
-// out[P][Q] = sum_{p,q} M[P][p] M[Q][q] in[p][q]
+// In-place butterfly of 8 values along bit `bit`: (v0, v1) -> (v0 + v1, v1 - v0).
 template <typename T>
-__device__ __forceinline__ void interp2(const T in[2][2], T out[2][2]) {
-  const T g0 = T(GaussM<T>::g0), g1 = T(GaussM<T>::g1);
-  T t00 = g1 * in[0][0] + g0 * in[0][1];
-  T t01 = g0 * in[0][0] + g1 * in[0][1];
-  T t10 = g1 * in[1][0] + g0 * in[1][1];
-  T t11 = g0 * in[1][0] + g1 * in[1][1];
-  out[0][0] = g1 * t00 + g0 * t10;
-  out[1][0] = g0 * t00 + g1 * t10;
-  out[0][1] = g1 * t01 + g0 * t11;
-  out[1][1] = g0 * t01 + g1 * t11;
+__device__ __forceinline__ void fwd_stage(T v[8], int bit) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (!(k & bit)) {
+      const T a = v[k], b = v[k | bit];
+      v[k] = a + b;
+      v[k | bit] = b - a;
+    }
+}
+// Transposed butterfly: (s, d) -> (s - d, s + d).
+template <typename T>
+__device__ __forceinline__ void bwd_stage(T v[8], int bit) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (!(k & bit)) {
+      const T s = v[k], d = v[k | bit];
+      v[k] = s - d;
+      v[k | bit] = s + d;
+    }
 }
 
 // X, Y: 24 values, DOF 3*k + c of corner k = i + 2j + 4m.
-// Returns u^T K0 u when WANT_ENERGY (Y then untouched); else writes Y = c K0 X.
+// WANT_ENERGY: returns x^T K0 x (Y untouched); otherwise writes Y = coef * K0 X.
 template <typename T, bool WANT_ENERGY>
-__device__ __forceinline__ T element_op(const T X[24], T Y[24], T coef, T lam, T mu) {
-  T Gx[3][2][2], Gy[3][2][2], Gz[3][2][2];
+__device__ __forceinline__ T element_op(const T X[24], T Y[24], T coef, const ModalBlocks<T> &M) {
+  T w[3][8];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    T dx[2][2], dy[2][2], dz[2][2];
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        dx[p][q] = X[3 * (1 + 2 * p + 4 * q) + c] - X[3 * (0 + 2 * p + 4 * q) + c];  // [j][k]
-        dy[p][q] = X[3 * (p + 2 * 1 + 4 * q) + c] - X[3 * (p + 2 * 0 + 4 * q) + c];  // [i][k]
-        dz[p][q] = X[3 * (p + 2 * q + 4 * 1) + c] - X[3 * (p + 2 * q + 4 * 0) + c];  // [i][j]
-      }
-    interp2<T>(dx, Gx[c]);  // [b][d]
-    interp2<T>(dy, Gy[c]);  // [a][d]
-    interp2<T>(dz, Gz[c]);  // [a][b]
+    for (int k = 0; k < 8; ++k) w[c][k] = X[3 * k + c];
+    fwd_stage<T>(w[c], 1);
+    fwd_stage<T>(w[c], 2);
+    fwd_stage<T>(w[c], 4);
   }
-  T Sx[3][2][2], Sy[3][2][2], Sz[3][2][2];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int p = 0; p < 2; ++p)
-#pragma unroll
-      for (int q = 0; q < 2; ++q) Sx[c][p][q] = Sy[c][p][q] = Sz[c][p][q] = T(0);
+  T z[3][8];
   T energy = T(0);
-  const T two_mu = mu + mu;
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 2; ++b)
-#pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        const T exx = Gx[0][b][d], eyy = Gy[1][a][d], ezz = Gz[2][a][b];
-        const T gxy = Gy[0][a][d] + Gx[1][b][d];
-        const T gyz = Gz[1][a][b] + Gy[2][a][d];
-        const T gzx = Gx[2][b][d] + Gz[0][a][b];
-        const T ltr = lam * (exx + eyy + ezz);
-        const T sxx = ltr + two_mu * exx, syy = ltr + two_mu * eyy, szz = ltr + two_mu * ezz;
-        const T sxy = mu * gxy, syz = mu * gyz, szx = mu * gzx;
-        if (WANT_ENERGY) {
-          energy += sxx * exx + syy * eyy + szz * ezz + sxy * gxy + syz * gyz + szx * gzx;
-        } else {
-          Sx[0][b][d] += sxx; Sy[0][a][d] += sxy; Sz[0][a][b] += szx;
-          Sx[1][b][d] += sxy; Sy[1][a][d] += syy; Sz[1][a][b] += syz;
-          Sx[2][b][d] += szx; Sy[2][a][d] += syz; Sz[2][a][b] += szz;
-        }
-      }
-  if (WANT_ENERGY) return energy * T(0.125);
-  const T w = coef * T(0.125);
+  for (int s = 0; s < 8; ++s) {
+    const T a0 = w[0][s ^ 1], a1 = w[1][s ^ 2], a2 = w[2][s ^ 4];
+    T r0, r1, r2;
+    if (s == 1) {        // component 0 of this block is a translation
+      r0 = T(0);
+      r1 = M.b[s][1][1] * a1 + M.b[s][1][2] * a2;
+      r2 = M.b[s][2][1] * a1 + M.b[s][2][2] * a2;
+    } else if (s == 2) {
+      r0 = M.b[s][0][0] * a0 + M.b[s][0][2] * a2;
+      r1 = T(0);
+      r2 = M.b[s][2][0] * a0 + M.b[s][2][2] * a2;
+    } else if (s == 4) {
+      r0 = M.b[s][0][0] * a0 + M.b[s][0][1] * a1;
+      r1 = M.b[s][1][0] * a0 + M.b[s][1][1] * a1;
+      r2 = T(0);
+    } else {
+      r0 = M.b[s][0][0] * a0 + M.b[s][0][1] * a1 + M.b[s][0][2] * a2;
+      r1 = M.b[s][1][0] * a0 + M.b[s][1][1] * a1 + M.b[s][1][2] * a2;
+      r2 = M.b[s][2][0] * a0 + M.b[s][2][1] * a1 + M.b[s][2][2] * a2;
+    }
+    if (WANT_ENERGY) {
+      energy += a0 * r0 + a1 * r1 + a2 * r2;
+    } else {
+      z[0][s ^ 1] = r0;
+      z[1][s ^ 2] = r1;
+      z[2][s ^ 4] = r2;
+    }
+  }
+  if (WANT_ENERGY) return energy;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    T tx[2][2], ty[2][2], tz[2][2];
-    interp2<T>(Sx[c], tx);  // [j][k]
-    interp2<T>(Sy[c], ty);  // [i][k]
-    interp2<T>(Sz[c], tz);  // [i][j]
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int i = k & 1, j = (k >> 1) & 1, m = (k >> 2) & 1;
-      const T v = (i ? tx[j][m] : -tx[j][m]) + (j ? ty[i][m] : -ty[i][m]) + (m ? tz[i][j] : -tz[i][j]);
-      Y[3 * k + c] = w * v;
-    }
+    for (int k = 0; k < 8; ++k) z[c][k] *= coef;
+    bwd_stage<T>(z[c], 1);
+    bwd_stage<T>(z[c], 2);
+    bwd_stage<T>(z[c], 4);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) Y[3 * k + c] = z[c][k];
   }
   return T(0);
 }

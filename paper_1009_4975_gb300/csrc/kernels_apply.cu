@@ -2,23 +2,31 @@
 // element coefficients c_e = (Emin + rho_e^p (E0 - Emin)) h_e (Eq. 2), the
 // Jacobi diagonal of Sec. 5 and the expansion u_full = C u (Eq. 9).
 //
-// Operator layout (one CTA per block of consecutive elements, tables built by
-// mesh_host.cpp).  A block's local nodes are its regular nodes followed by the
-// hanging nodes its elements use; each local node has an inverse list of the
-// (element, corner) slots it fills.
-//   1. regular nodes load x (Dirichlet entries read as 0) and write it into
-//      their slots of a per-element shared buffer; hanging nodes then write the
-//      (bi)linear interpolation of their masters into theirs (C, Eq. 6);
-//   2. one thread per element replaces its 24 inputs by c_e K0 X_e (sum
-//      factorisation, element.cuh);
+// Operator layout (tables built by mesh_host.cpp).  Elements are grouped in
+// blocks of 256 consecutive elements; a block's local nodes are its regular
+// nodes followed by the hanging nodes its elements use; each block has one
+// 16-byte-aligned record: corner -> local id per element, local -> global node,
+// shared-node partial positions, hanging masters, and per-local-node inverse
+// lists (the (element, corner) slots it collects, plus fold entries naming the
+// hanging nodes it is a master of).
+//
+// The kernel is persistent: each CTA walks blocks b, b + G, b + 2G, ... and
+// pipelines them with cp.async -- the record of block t+2 and the node values
+// of block t+1 are in flight while block t computes:
+//   1. hanging nodes take the (bi)linear interpolation of their masters (C);
+//   2. one thread per element gathers its 8 corners and computes c_e K0 X_e
+//      (sum factorisation, element.cuh) into a per-element slot buffer;
 //   3. hanging nodes sum their slots; regular nodes sum their slots plus
 //      w * (sum) of every hanging node they are a master of (C^T) -- a fixed
 //      summation order, no atomics, bitwise reproducible;
 //   4. nodes touched only by this block are stored to y; nodes shared with
-//      other blocks are stored to per-block slots that a second kernel sums in
-//      ascending block order.  Hanging DOFs of y are set to 0.
-// The dot product x . y can be accumulated on the fly (CG's p^T A p).
+//      other blocks are stored to their partial slots, which a second kernel
+//      sums in ascending block order.  Hanging DOFs of y are set to 0.
+// Dirichlet nodes read as 0 (zero-filled copies) and are written as 0.  The dot
+// product x . y can be accumulated on the fly (CG's p^T A p).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "element.cuh"
 #include "pcg.cuh"
@@ -32,82 +40,137 @@ constexpr int kRow = 25;                    // padded per-element row of the slo
 
 template <typename T>
 struct ApplyParams {
-  const int32_t *blk_elem, *blk_node, *blk_shared, *blk_slot, *blk_hang, *blk_iptr, *blk_inv;
-  const int32_t *lnode, *lslot;
-  const uint16_t *hent, *iptr, *inv;
-  const uint8_t *nflag;
+  const uint4 *brec;        // per-block records
+  const int32_t *rec_off;   // record ranges in 16-byte units
   const T *ce;
   const T *x;
   T *y;
   T *part;
   double *dotp;     // per-CTA partials of x . y (nullptr: skip)
   const int *done;  // skip the launch when set (nullptr: never)
-  T lam, mu;
+  ModalBlocks<T> K;
+  int nblk;
+  int max_local;    // local nodes of the largest block
+  int rec_bytes;    // record buffer size (largest record, multiple of 16)
 };
 
+__device__ __forceinline__ int slot_of(int p) { return (p >> 3) * kRow + 3 * (p & 7); }
+
+// Shared memory: XY (per-element slots) | R (3 values per local node) | record.
 template <typename T>
-size_t apply_smem_bytes(int max_local) {
-  return sizeof(T) * ((size_t)kApplyThreads * kRow + 3 * (size_t)max_local);
+__host__ __device__ __forceinline__ size_t val_buf_bytes(int max_local) {
+  return ((sizeof(T) * 3 * (size_t)max_local) + 15) / 16 * 16;
+}
+template <typename T>
+__host__ __device__ __forceinline__ size_t xy_bytes() {
+  return ((sizeof(T) * (size_t)kApplyThreads * kRow) + 15) / 16 * 16;
+}
+template <typename T>
+size_t apply_smem_bytes(int max_local, int rec_bytes) {
+  return xy_bytes<T>() + val_buf_bytes<T>(max_local) + (size_t)rec_bytes;
 }
 
-__device__ __forceinline__ int slot_of(int p) { return (p >> 3) * kRow + 3 * (p & 7); }
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+// copies `bytes` (4 or 8) and zero-fills the destination when `fill_zero`
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void *dst, const void *src, bool fill_zero) {
+  const int srcsz = fill_zero ? 0 : BYTES;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES),
+               "r"(srcsz)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Record of block `blk` into `rec` (all threads; an empty group past the end).
+__device__ __forceinline__ void issue_record(const uint4 *brec, const int32_t *rec_off, int blk, int nblk,
+                                             uint4 *rec) {
+  if (blk < nblk) {
+    const int r0 = rec_off[blk], nr = rec_off[blk + 1] - r0;
+    for (int i = threadIdx.x; i < nr; i += kApplyThreads) cp_async16(rec + i, brec + r0 + i);
+  }
+  cp_async_commit();
+}
+
+// Node values of the block whose record is in `rec` into `R`.
+template <typename T>
+__device__ __forceinline__ void issue_values(const uint4 *rec, const T *x, T *R, bool valid) {
+  if (valid) {
+    const int *hdr = reinterpret_cast<const int *>(rec);
+    const int nreg = hdr[2];
+    const uint32_t *lnode = reinterpret_cast<const uint32_t *>(reinterpret_cast<const unsigned char *>(rec) + hdr[11]);
+    for (int i = threadIdx.x; i < nreg; i += kApplyThreads) {
+      const uint32_t gw = lnode[i];
+      const bool fixed = gw >> 31;
+      const T *src = x + 3 * (size_t)(gw & 0x7FFFFFFFu);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) cp_async_small<sizeof(T)>(R + 3 * i + c, src + c, fixed);
+    }
+  }
+  cp_async_commit();
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kApplyThreads, sizeof(T) == 4 ? 4 : 2) apply_blocks_kernel(ApplyParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *XY = reinterpret_cast<T *>(smem_raw);   // per-element slots: inputs, then outputs
-  T *R = XY + kApplyThreads * kRow;          // regular x values, then hanging sums
-
   if (P.done && *(volatile const int *)P.done) return;
-  const int b = blockIdx.x;
+  T *XY = reinterpret_cast<T *>(smem_raw);
+  T *R = reinterpret_cast<T *>(smem_raw + xy_bytes<T>());
+  uint4 *rec = reinterpret_cast<uint4 *>(smem_raw + xy_bytes<T>() + val_buf_bytes<T>(P.max_local));
   const int tid = threadIdx.x;
-  const int e0 = P.blk_elem[b], ne = P.blk_elem[b + 1] - e0;
-  const int n0 = P.blk_node[b], nreg = P.blk_node[b + 1] - n0;
-  const int h0 = P.blk_hang[b], nhang = P.blk_hang[b + 1] - h0;
-  const uint16_t *ip = P.iptr + P.blk_iptr[b];
-  const uint16_t *iv = P.inv + P.blk_inv[b];
-
-  // 1a. regular nodes: load and scatter into their slots
-  for (int i = tid; i < nreg; i += kApplyThreads) {
-    const int g = P.lnode[n0 + i];
-    const bool fixed = P.nflag[g] & 1;
-    const T *src = P.x + 3 * (size_t)g;
-    const T v0 = fixed ? T(0) : src[0], v1 = fixed ? T(0) : src[1], v2 = fixed ? T(0) : src[2];
-    R[3 * i] = v0; R[3 * i + 1] = v1; R[3 * i + 2] = v2;
-    const int q1 = ip[i + 1];
-    for (int q = ip[i]; q < q1; ++q) {
-      const int p = iv[q];
-      if (p & kFoldBit) continue;
-      T *d = XY + slot_of(p);
-      d[0] = v0; d[1] = v1; d[2] = v2;
-    }
-  }
+  const int b = blockIdx.x;
+  // record, then the node values it names: every copy of a stage in flight at once
+  issue_record(P.brec, P.rec_off, b, P.nblk, rec);
+  cp_async_wait<0>();
   __syncthreads();
-  // 1b. hanging nodes: interpolate the masters (C) and scatter
+  issue_values<T>(rec, P.x, R, true);
+  cp_async_wait<0>();
+  __syncthreads();
+
+  const int *hdr = reinterpret_cast<const int *>(rec);
+  const unsigned char *rb = reinterpret_cast<const unsigned char *>(rec);
+  const int e0 = hdr[0], ne = hdr[1], nreg = hdr[2], nshared = hdr[3], nhang = hdr[4];
+  const int *lslot = reinterpret_cast<const int *>(rb + hdr[6]);
+  const uint2 *hent = reinterpret_cast<const uint2 *>(rb + hdr[7]);
+  const uint16_t *ip = reinterpret_cast<const uint16_t *>(rb + hdr[8]);
+  const uint16_t *iv = reinterpret_cast<const uint16_t *>(rb + hdr[9]);
+  const uint4 *lcorner = reinterpret_cast<const uint4 *>(rb + hdr[10]);
+  const uint32_t *lnode = reinterpret_cast<const uint32_t *>(rb + hdr[11]);
+
+  // 1. hanging nodes: (bi)linear interpolation of their masters (C)
   for (int j = tid; j < nhang; j += kApplyThreads) {
-    const uint2 mw = reinterpret_cast<const uint2 *>(P.hent)[h0 + j];
+    const uint2 mw = hent[j];
     const int m0 = mw.x & 0xFFFF, m1 = mw.x >> 16, m2 = mw.y & 0xFFFF, m3 = mw.y >> 16;
-    T v[3];
+    T *d = R + 3 * (nreg + j);
     if (m2 == 0xFFFF) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) v[c] = T(0.5) * (R[3 * m0 + c] + R[3 * m1 + c]);
+      for (int c = 0; c < 3; ++c) d[c] = T(0.5) * (R[3 * m0 + c] + R[3 * m1 + c]);
     } else {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) v[c] = T(0.25) * ((R[3 * m0 + c] + R[3 * m1 + c]) + (R[3 * m2 + c] + R[3 * m3 + c]));
-    }
-    const int q1 = ip[nreg + j + 1];
-    for (int q = ip[nreg + j]; q < q1; ++q) {
-      T *d = XY + slot_of(iv[q]);
-      d[0] = v[0]; d[1] = v[1]; d[2] = v[2];
+      for (int c = 0; c < 3; ++c)
+        d[c] = T(0.25) * ((R[3 * m0 + c] + R[3 * m1 + c]) + (R[3 * m2 + c] + R[3 * m3 + c]));
     }
   }
   __syncthreads();
-  // 2. element operator, in place
+  // 2. element operator: gather the 8 corners, results into the slots
   if (tid < ne) {
+    const uint4 cw = lcorner[tid];
+    const int code[8] = {(int)(cw.x & 0xFFFF), (int)(cw.x >> 16), (int)(cw.y & 0xFFFF), (int)(cw.y >> 16),
+                         (int)(cw.z & 0xFFFF), (int)(cw.z >> 16), (int)(cw.w & 0xFFFF), (int)(cw.w >> 16)};
     T X[24], Y[24];
 #pragma unroll
-    for (int j = 0; j < 24; ++j) X[j] = XY[tid * kRow + j];
-    element_op<T, false>(X, Y, P.ce[e0 + tid], P.lam, P.mu);
+    for (int k = 0; k < 8; ++k) {
+      X[3 * k] = R[3 * code[k]];
+      X[3 * k + 1] = R[3 * code[k] + 1];
+      X[3 * k + 2] = R[3 * code[k] + 2];
+    }
+    element_op<T, false>(X, Y, P.ce[e0 + tid], P.K);
 #pragma unroll
     for (int j = 0; j < 24; ++j) XY[tid * kRow + j] = Y[j];
   }
@@ -125,8 +188,6 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(T) == 4 ? 4 : 2) apply_b
   }
   __syncthreads();
   // 3b/4. regular nodes: own slots + folded hanging sums (C^T), then store
-  const int nshared = P.blk_shared[b];
-  const int slot0 = P.blk_slot[b];
   double dot = 0.0;
   for (int i = tid; i < nreg; i += kApplyThreads) {
     T s0 = T(0), s1 = T(0), s2 = T(0);
@@ -142,13 +203,13 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(T) == 4 ? 4 : 2) apply_b
         s0 += w * r[0]; s1 += w * r[1]; s2 += w * r[2];
       }
     }
-    const int g = P.lnode[n0 + i];
-    if (P.nflag[g] & 1) s0 = s1 = s2 = T(0);
+    const uint32_t gw = lnode[i];
+    if (gw >> 31) s0 = s1 = s2 = T(0);
     if (i < nshared) {
-      T *dst = P.part + 3 * (size_t)P.lslot[slot0 + i];
+      T *dst = P.part + 3 * (size_t)lslot[i];
       dst[0] = s0; dst[1] = s1; dst[2] = s2;
     } else {
-      T *dst = P.y + 3 * (size_t)g;
+      T *dst = P.y + 3 * (size_t)(gw & 0x7FFFFFFFu);
       dst[0] = s0; dst[1] = s1; dst[2] = s2;
       dot += (double)R[3 * i] * (double)s0 + (double)R[3 * i + 1] * (double)s1 + (double)R[3 * i + 2] * (double)s2;
     }
@@ -210,6 +271,12 @@ __global__ void __launch_bounds__(256) apply_shared_kernel(const int32_t *sh_nod
   }
 }
 
+// One thread per item (the second pass is latency-bound: no grid-stride reuse).
+int item_grid(int64_t n) {
+  const int64_t g = (n + 255) / 256;
+  return (int)(g < 1 ? 1 : g);
+}
+
 int shared_grid(int64_t n) {
   int64_t g = (n + 255) / 256;
   if (g < 1) g = 1;
@@ -222,25 +289,27 @@ cudaError_t launch_apply(const DeviceMesh &m, const T *ce, const T *x, T *y, T *
                          SolveScalars *sc, unsigned int *ticket, bool zero_hanging, const int *done,
                          cudaStream_t s) {
   static size_t configured = 0;
-  const size_t smem = apply_smem_bytes<T>(m.max_local);
+  const int rec_bytes = (m.max_rec_bytes + 15) / 16 * 16;
+  const size_t smem = apply_smem_bytes<T>(m.max_local, rec_bytes);
   if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(apply_blocks_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)apply_smem_bytes<T>(kMaxLocal));
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    configured = apply_smem_bytes<T>(kMaxLocal);
+    configured = smem;
   }
+  const int g = std::max(m.nblk, 1);
   ApplyParams<T> P;
-  P.blk_elem = m.blk_elem; P.blk_node = m.blk_node; P.blk_shared = m.blk_shared; P.blk_slot = m.blk_slot;
-  P.blk_hang = m.blk_hang; P.blk_iptr = m.blk_iptr; P.blk_inv = m.blk_inv; P.lnode = m.lnode; P.lslot = m.lslot;
-  P.hent = m.hent; P.iptr = m.iptr; P.inv = m.inv; P.nflag = m.nflag; P.ce = ce; P.x = x; P.y = y; P.part = part;
-  P.dotp = dot_partials; P.done = done; P.lam = (T)m.lam; P.mu = (T)m.mu;
-  if (m.nblk > 0) apply_blocks_kernel<T><<<m.nblk, kApplyThreads, smem, s>>>(P);
+  P.brec = m.brec; P.rec_off = m.rec_off; P.ce = ce; P.x = x; P.y = y; P.part = part;
+  P.dotp = dot_partials; P.done = done; P.nblk = m.nblk;
+  for (int i = 0; i < 72; ++i) (&P.K.b[0][0][0])[i] = (T)m.modal[i];
+  P.max_local = m.max_local; P.rec_bytes = rec_bytes;
+  if (m.nblk > 0) apply_blocks_kernel<T><<<g, kApplyThreads, smem, s>>>(P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t items = m.nsh + (zero_hanging ? m.nh : 0);
-  apply_shared_kernel<T><<<shared_grid(items), 256, 0, s>>>(m.sh_node, m.sh_ptr, m.nsh, m.hang_node,
-                                                            zero_hanging ? m.nh : 0, m.nflag, part, x, y,
-                                                            dot_partials, m.nblk, sc, ticket, done);
+  apply_shared_kernel<T><<<item_grid(items), 256, 0, s>>>(m.sh_node, m.sh_ptr, m.nsh, m.hang_node,
+                                                          zero_hanging ? m.nh : 0, m.nflag, part, x, y,
+                                                          dot_partials, m.nblk > 0 ? g : 0, sc, ticket, done);
   return cudaGetLastError();
 }
 

@@ -16,7 +16,7 @@ constexpr int kTopThreads = 256;
 __global__ void __launch_bounds__(kTopThreads) sensitivity_kernel(const int32_t *conn, const int32_t *leaf,
                                                                   const double *rho, const double *uf, int64_t Ne,
                                                                   double E0, double Emin, double penal, double h0,
-                                                                  double lam, double mu, double *dc,
+                                                                  ModalBlocks<double> K, double *dc,
                                                                   double *partials, unsigned int *ticket,
                                                                   double *compliance) {
   double cpart = 0.0;
@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(kTopThreads) sensitivity_kernel(const int32_t 
       X[3 * k + 1] = src[1];
       X[3 * k + 2] = src[2];
     }
-    const double en = element_op<double, true>(X, nullptr, 1.0, lam, mu);
+    const double en = element_op<double, true>(X, nullptr, 1.0, K);
     const double h = ldexp(h0, -leaf[4 * e + 3]);
     const double r = rho[e];
     dc[e] = -penal * pow(r, penal - 1.0) * (E0 - Emin) * h * en;
@@ -52,8 +52,10 @@ int top_grid(int64_t n) {
 
 cudaError_t launch_sensitivity(const DeviceMesh &m, const double *rho, const double *uf, double *dc,
                                double *partials, unsigned int *ticket, double *compliance, cudaStream_t s) {
+  ModalBlocks<double> K;
+  for (int i = 0; i < 72; ++i) (&K.b[0][0][0])[i] = m.modal[i];
   sensitivity_kernel<<<top_grid(m.Ne), kTopThreads, 0, s>>>(m.conn, m.leaf, rho, uf, m.Ne, m.E0, m.Emin, m.penal,
-                                                            m.h0, m.lam, m.mu, dc, partials, ticket, compliance);
+                                                            m.h0, K, dc, partials, ticket, compliance);
   return cudaGetLastError();
 }
 
@@ -121,7 +123,8 @@ cudaError_t launch_filter(const DeviceMesh &m, const double *rho, const double *
 __device__ __forceinline__ double oc_value(double r, double g, double V, double lam, double eta, double move,
                                            double rmin) {
   const double lo = fmax(rmin, r - move), hi = fmin(1.0, r + move);
-  const double v = r * pow(g / (lam * V), eta);
+  const double t = g / (lam * V);
+  const double v = r * (eta == 0.5 ? sqrt(t) : pow(t, eta));
   return fmin(fmax(v, lo), hi);
 }
 

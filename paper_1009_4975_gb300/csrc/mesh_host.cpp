@@ -302,6 +302,49 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
 
   m.K0.resize(576);
   reference_stiffness(d.nu, m.K0.data());
+  {
+    // K0 in the butterfly basis: K0m = T K0 T^T / 64 with T[(m,c)][(k,c)] = prod over axes a
+    // with bit a of m set of (bit a of k ? +1 : -1).  Check that it is block diagonal over
+    // signatures (DOF c of block s = mode s ^ (1 << c)) and keep the 8 blocks.
+    auto t8 = [](int mm, int k) {
+      int v = 1;
+      for (int a = 0; a < 3; ++a)
+        if ((mm >> a) & 1) v *= ((k >> a) & 1) ? 1 : -1;
+      return v;
+    };
+    double Km[24][24] = {};
+    double mx = 0;
+    for (int r = 0; r < 24; ++r)
+      for (int q = 0; q < 24; ++q) {
+        const int mr = r / 3, cr = r % 3, mq = q / 3, cq = q % 3;
+        double acc = 0;
+        for (int k = 0; k < 8; ++k)
+          for (int l = 0; l < 8; ++l) acc += t8(mr, k) * m.K0[(3 * k + cr) * 24 + 3 * l + cq] * t8(mq, l);
+        Km[r][q] = acc / 64.0;
+        mx = std::max(mx, std::fabs(Km[r][q]));
+      }
+    auto sig = [](int mm, int c) { return mm ^ (1 << c); };
+    for (int r = 0; r < 24; ++r)
+      for (int q = 0; q < 24; ++q)
+        if (sig(r / 3, r % 3) != sig(q / 3, q % 3) && std::fabs(Km[r][q]) > 1e-13 * mx)
+          return "element matrix is not block diagonal in the butterfly basis";
+    m.modal.assign(72, 0.0);
+    for (int sgn = 0; sgn < 8; ++sgn)
+      for (int c = 0; c < 3; ++c)
+        for (int c2 = 0; c2 < 3; ++c2) {
+          const int r = 3 * (sgn ^ (1 << c)) + c, q = 3 * (sgn ^ (1 << c2)) + c2;
+          double v = Km[r][q];
+          if (std::fabs(v) <= 1e-13 * mx) v = 0.0;
+          m.modal[sgn * 9 + c * 3 + c2] = v;
+        }
+    // rows and columns of the rigid translations vanish
+    for (int c = 0; c < 3; ++c)
+      for (int c2 = 0; c2 < 3; ++c2) {
+        const int sgn = 1 << c;
+        if (m.modal[sgn * 9 + c * 3 + c2] != 0.0 || m.modal[sgn * 9 + c2 * 3 + c] != 0.0)
+          return "translation modes are not in the null space of the element matrix";
+      }
+  }
 
   // ---- 6. operator blocks: chunks of consecutive elements, local nodes, colours
   // Local nodes of a block: its regular ("effective") nodes -- regular corners
@@ -364,6 +407,7 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
   m.blk_hang.assign(nblk + 1, 0);
   m.blk_iptr.assign(nblk + 1, 0);
   m.blk_inv.assign(nblk, 0);
+  m.lcorner.assign(8 * (size_t)Ne, 0);
   std::vector<int32_t> local_of(Nn, -1);
   int32_t max_local = 0;
   for (int32_t b = 0; b < nblk; ++b) {
@@ -394,6 +438,8 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     if (nloc > kMaxLocal) return "block local-node limit exceeded";
     max_local = std::max(max_local, nloc);
     m.blk_hang[b + 1] = m.blk_hang[b] + (int32_t)used_h.size();
+    for (int64_t e = e0; e < e1; ++e)
+      for (int k = 0; k < 8; ++k) m.lcorner[8 * e + k] = (uint16_t)local_of[m.conn[8 * e + k]];
     std::vector<std::vector<uint16_t>> lists(nloc);
     for (int64_t e = e0; e < e1; ++e)
       for (int k = 0; k < 8; ++k) lists[local_of[m.conn[8 * e + k]]].push_back((uint16_t)(8 * (e - e0) + k));
@@ -446,6 +492,52 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
         m.sh_node.push_back((int32_t)n);
         m.sh_ptr.push_back(start[n + 1]);
       }
+  }
+
+  // ---- 7b. one contiguous record per block (16-byte aligned), staged into
+  // shared memory by the operator kernel with coalesced 16-byte loads:
+  //   header (12 x i32: e0, ne, nreg, nshared, nhang, ninv, byte offsets of
+  //   lslot, hent, iptr, inv, lcorner, lnode), lcorner (8 x u16 per element: the
+  //   local ids of its corners), lnode (i32, bit 31 = Dirichlet node), lslot
+  //   (i32), hent (4 x u16), iptr (u16), inv (u16).
+  {
+    m.rec_off.assign(nblk + 1, 0);
+    m.max_rec_bytes = 0;
+    auto align = [](size_t v, size_t a) { return (v + a - 1) / a * a; };
+    for (int32_t b = 0; b < nblk; ++b) {
+      const int32_t nreg = m.blk_node[b + 1] - m.blk_node[b];
+      const int32_t nshared = m.blk_shared[b];
+      const int32_t nhang = m.blk_hang[b + 1] - m.blk_hang[b];
+      const int32_t nloc = nreg + nhang;
+      const int32_t ninv = m.iptr[m.blk_iptr[b] + nloc];
+      const int32_t ne = m.blk_elem[b + 1] - m.blk_elem[b];
+      size_t off = 48;
+      const size_t o_lcorner = off; off += 16 * (size_t)ne;
+      const size_t o_lnode = off; off += 4 * (size_t)nreg;
+      const size_t o_lslot = off; off += 4 * (size_t)nshared;
+      off = align(off, 8);
+      const size_t o_hent = off; off += 8 * (size_t)nhang;
+      const size_t o_iptr = off; off += 2 * (size_t)(nloc + 1);
+      const size_t o_inv = off; off += 2 * (size_t)ninv;
+      const size_t bytes = align(off, 16);
+      std::vector<uint8_t> rec(bytes, 0);
+      int32_t hdr[12] = {m.blk_elem[b], ne, nreg, nshared, nhang, ninv, (int32_t)o_lslot, (int32_t)o_hent,
+                         (int32_t)o_iptr, (int32_t)o_inv, (int32_t)o_lcorner, (int32_t)o_lnode};
+      std::memcpy(rec.data(), hdr, sizeof(hdr));
+      std::memcpy(&rec[o_lcorner], &m.lcorner[8 * (size_t)m.blk_elem[b]], 16 * (size_t)ne);
+      for (int32_t i = 0; i < nreg; ++i) {
+        uint32_t g = (uint32_t)m.lnode[m.blk_node[b] + i];
+        if (m.nflag[g] & 1) g |= 0x80000000u;
+        std::memcpy(&rec[o_lnode + 4 * i], &g, 4);
+      }
+      if (nshared) std::memcpy(&rec[o_lslot], &m.lslot[m.blk_slot[b]], 4 * (size_t)nshared);
+      if (nhang) std::memcpy(&rec[o_hent], &m.hent[4 * (size_t)m.blk_hang[b]], 8 * (size_t)nhang);
+      std::memcpy(&rec[o_iptr], &m.iptr[m.blk_iptr[b]], 2 * (size_t)(nloc + 1));
+      if (ninv) std::memcpy(&rec[o_inv], &m.inv[m.blk_inv[b]], 2 * (size_t)ninv);
+      m.brec.insert(m.brec.end(), rec.begin(), rec.end());
+      m.rec_off[b + 1] = (int32_t)(m.brec.size() / 16);
+      m.max_rec_bytes = std::max<int32_t>(m.max_rec_bytes, (int32_t)bytes);
+    }
   }
 
   // ---- 8. Jacobi diagonal coefficients: d_{m,c} = sum_e c_e q_{e,m,c}
@@ -564,6 +656,8 @@ int tm_tables_build(const tm_mesh_desc *d, tm_tables **out, tm_mesh_info *info, 
     info->max_local = m.max_local;
     info->n_shared = (int64_t)m.sh_node.size();
     info->device_bytes = 0;
+    info->max_block_bytes = m.max_rec_bytes;
+    info->pad_ = 0;
   }
   *out = t;
   return TM_OK;

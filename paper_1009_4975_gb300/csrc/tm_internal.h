@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/tm.h"
+#include "element.cuh"
 
 namespace amr {
 
@@ -56,6 +57,10 @@ struct HostMesh {
   std::vector<uint16_t> hent;         // 4 per hanging local node: masters' local ids (0xFFFF pad)
   std::vector<uint16_t> iptr;         // inverse-list offsets, relative to blk_inv[b]
   std::vector<uint16_t> inv;          // inverse-list entries
+  std::vector<uint16_t> lcorner;      // 8 per element: local ids of its corners within its block
+  std::vector<uint8_t> brec;          // per-block records (see mesh_host.cpp, 16-byte aligned)
+  std::vector<int32_t> rec_off;       // nblk+1: record ranges in 16-byte units
+  int32_t max_rec_bytes = 0;
   // second pass over shared nodes
   std::vector<int32_t> sh_node;       // shared node ids
   std::vector<int32_t> sh_ptr;        // CSR: partials of shared node i are [sh_ptr[i], sh_ptr[i+1])
@@ -66,6 +71,7 @@ struct HostMesh {
   std::vector<double> dg_tab;         // 3 per distinct triple
   // the reference element matrix (unit cube, E = 1), host copy
   std::vector<double> K0;             // 24 x 24
+  std::vector<double> modal;          // 8 x 3 x 3 blocks of K0 in the butterfly basis (element.cuh)
   std::vector<int32_t> cellmap;       // finest cell (x fastest) -> canonical element
 };
 
@@ -88,7 +94,7 @@ struct DeviceMesh {
   int L = 0;
   double h0 = 0, hmin = 0;
   double E0 = 1, Emin = 0, penal = 3, nu = 0.3;
-  double lam = 0, mu = 0;             // Lame constants for E = 1
+  double modal[72] = {};              // element matrix blocks (element.cuh)
   double k0diag = 0;
   double volume = 0;                  // |Omega|
   int64_t n_free = 0;
@@ -103,6 +109,9 @@ struct DeviceMesh {
   int32_t *lnode = nullptr, *lslot = nullptr;
   uint16_t *hent = nullptr, *iptr = nullptr, *inv = nullptr;
   int32_t max_local = 0;
+  uint4 *brec = nullptr;
+  int32_t *rec_off = nullptr;
+  int32_t max_rec_bytes = 0;
   int32_t *sh_node = nullptr, *sh_ptr = nullptr;
   int32_t *dg_ptr = nullptr, *dg_elem = nullptr;
   uint16_t *dg_q = nullptr;

@@ -37,7 +37,8 @@ class tm_mesh_desc(C.Structure):
 class tm_mesh_info(C.Structure):
     _fields_ = [("Ne", C.c_int64), ("Nn", C.c_int64), ("n_hanging", C.c_int64), ("n_dirichlet", C.c_int64),
                 ("n_free", C.c_int64), ("n_blocks", C.c_int32), ("max_local", C.c_int32),
-                ("n_shared", C.c_int64), ("device_bytes", C.c_int64)]
+                ("n_shared", C.c_int64), ("device_bytes", C.c_int64), ("max_block_bytes", C.c_int32),
+                ("pad_", C.c_int32)]
 
 
 class tm_solve_opts(C.Structure):
