@@ -283,8 +283,8 @@ def run_gpu(args):
         "fp64_pcg": fp64,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
-        "roofline": {"bound": "hbm", "kernel": "operator application (apply_blocks_kernel<float> + "
-                     "apply_shared_kernel<float>)", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "apply_blocks_kernel<float> (operator block pass; the partial "
+                     "sums of block-shared nodes are read by the CG update)", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes": algo, "avg_ms": a_ms,
                      "launches_timed": prof["apply32_count"]},

@@ -73,6 +73,13 @@ SolveScalars *solve_scalars(tm_ctx *c) { return reinterpret_cast<SolveScalars *>
 OcState *oc_state(tm_ctx *c) { return reinterpret_cast<OcState *>(c->w.scal + 64); }
 double *scal_at(tm_ctx *c, int i) { return c->w.scal + i; }
 
+// Event record on the context's stream; while a graph is being captured the
+// record becomes a node of the graph (re-recorded at every replay).
+cudaError_t record_event(tm_ctx *ctx, cudaEvent_t e) {
+  if (ctx->capturing) return cudaEventRecordWithFlags(e, ctx->stream, cudaEventRecordExternal);
+  return cudaEventRecord(e, ctx->stream);
+}
+
 // Operator launches with optional CUDA-event timing (tm_profile): each timed
 // application records an event pair on the context's stream; pairs are read
 // back at the next synchronisation point.
@@ -90,13 +97,40 @@ int timed_apply(tm_ctx *ctx, const T *ce, const T *x, T *y, T *part, double *dot
     }
     e0 = ctx->ev_free.back(); ctx->ev_free.pop_back();
     e1 = ctx->ev_free.back(); ctx->ev_free.pop_back();
-    TM_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+    TM_CUDA(ctx, record_event(ctx, e0));
   }
   TM_CUDA(ctx, launch_apply<T>(ctx->dm, ce, x, y, part, dotp, sc, ctx->w.ticket + 5, zero_hanging, done, ctx->stream));
   ctx->launches += 2;
   if (ctx->prof_on) {
-    TM_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
-    ctx->ev_pending.push_back({e0, e1, sizeof(T) == 4 ? 1 : 0});
+    TM_CUDA(ctx, record_event(ctx, e1));
+    ctx->ev_pending.push_back({e0, e1, sizeof(T) == 4 ? 1 : 0, false});
+  }
+  return TM_OK;
+}
+
+// The block pass alone (CG iterations): shared nodes stay in their partials.
+template <typename T>
+int timed_apply_blocks(tm_ctx *ctx, const T *ce, const T *x, T *y, T *part, double *energy_partials,
+                       SolveScalars *sc, const int *done) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ctx->prof_on) {
+    if (ctx->ev_free.size() < 2) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        TM_CUDA(ctx, cudaEventCreate(&e));
+        ctx->ev_free.push_back(e);
+      }
+    }
+    e0 = ctx->ev_free.back(); ctx->ev_free.pop_back();
+    e1 = ctx->ev_free.back(); ctx->ev_free.pop_back();
+    TM_CUDA(ctx, record_event(ctx, e0));
+  }
+  TM_CUDA(ctx, launch_apply_blocks<T>(ctx->dm, ce, x, y, part, energy_partials, sc, ctx->w.ticket + 5, done,
+                                      ctx->stream));
+  ctx->launches += 1;
+  if (ctx->prof_on) {
+    TM_CUDA(ctx, record_event(ctx, e1));
+    ctx->ev_pending.push_back({e0, e1, sizeof(T) == 4 ? 1 : 0, false});
   }
   return TM_OK;
 }
@@ -114,11 +148,24 @@ int drain_profile(tm_ctx *ctx, bool all) {
     // an apply skipped by the device-side done flag is not a launch that did work
     if (pe.kind == 1) { ctx->prof.apply32_ms += ms; ctx->prof.apply32_count++; }
     else { ctx->prof.apply64_ms += ms; ctx->prof.apply64_count++; }
-    ctx->ev_free.push_back(pe.e0);
-    ctx->ev_free.push_back(pe.e1);
+    if (!pe.graph_owned) {
+      ctx->ev_free.push_back(pe.e0);
+      ctx->ev_free.push_back(pe.e1);
+    }
   }
   ctx->ev_pending.swap(keep);
   return TM_OK;
+}
+
+void drop_graphs(tm_ctx *ctx) {
+  for (auto &g : ctx->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto &pe : g.ev) {
+      cudaEventDestroy(pe.e0);
+      cudaEventDestroy(pe.e1);
+    }
+  }
+  ctx->graphs.clear();
 }
 
 int read_scalar(tm_ctx *ctx, const double *dev, double *out) {
@@ -169,7 +216,10 @@ int tm_create(tm_ctx **out, int device, void *cuda_stream) {
   tm_ctx *c = new tm_ctx();
   c->device = device;
   c->stream = (cudaStream_t)cuda_stream;
-  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess) {
     delete c;
     return TM_ECUDA;
   }
@@ -181,6 +231,8 @@ int tm_destroy(tm_ctx *ctx) {
   if (!ctx) return TM_OK;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  cudaStreamSynchronize(ctx->gstream);
+  drop_graphs(ctx);
   release(ctx->dm.owned);
   release(ctx->w.owned);
   for (auto &pe : ctx->ev_pending) {
@@ -188,6 +240,9 @@ int tm_destroy(tm_ctx *ctx) {
     cudaEventDestroy(pe.e1);
   }
   for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   delete ctx;
@@ -206,6 +261,7 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
   TM_CHECK_CTX(ctx);
   if (!d) return fail(ctx, TM_EINVAL, "null mesh descriptor");
   TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  drop_graphs(ctx);
   ctx->has_mesh = false;
   release(ctx->dm.owned);
   release(ctx->w.owned);
@@ -255,6 +311,7 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
   m.max_rec_bytes = h.max_rec_bytes;
   TM_CUDA(ctx, upload(o, B, &m.sh_node, h.sh_node));
   TM_CUDA(ctx, upload(o, B, &m.sh_ptr, h.sh_ptr));
+  TM_CUDA(ctx, upload(o, B, &m.sh_of_node, h.sh_of_node));
   TM_CUDA(ctx, upload(o, B, &m.dg_ptr, h.dg_ptr));
   TM_CUDA(ctx, upload(o, B, &m.dg_elem, h.dg_elem));
   TM_CUDA(ctx, upload(o, B, &m.dg_q, h.dg_q));
@@ -467,13 +524,83 @@ int enqueue_iterations(tm_ctx *ctx, int count, const T *ce, T *part, TX *x, T *r
   Work &w = ctx->w;
   SolveScalars *sc = solve_scalars(ctx);
   const int64_t n = 3 * ctx->dm.Nn;
+  const DeviceMesh &m = ctx->dm;
   for (int k = 0; k < count; ++k) {
-    int rc = timed_apply<T>(ctx, ce, p, q, part, w.red, sc, false, &sc->done);
+    int rc = timed_apply_blocks<T>(ctx, ce, p, q, part, w.red, sc, &sc->done);
     if (rc) return rc;
-    TM_CUDA(ctx, launch_update<TX, T>(x, p, q, r, dinv, n, sc, w.red, w.ticket, ctx->stream));
+    TM_CUDA(ctx, launch_update_nodes<TX, T>(x, p, q, r, dinv, m.Nn, m.sh_of_node, m.sh_ptr, part, sc, w.red,
+                                            w.ticket, ctx->stream));
     TM_CUDA(ctx, launch_pupdate<T>(p, r, dinv, n, sc, ctx->stream));
     ctx->launches += 2;
   }
+  return TM_OK;
+}
+
+// Return event pairs to the pool unless a captured graph owns them.
+void recycle(tm_ctx *ctx, const tm_ctx::Pending &pe) {
+  if (pe.graph_owned) return;
+  ctx->ev_free.push_back(pe.e0);
+  ctx->ev_free.push_back(pe.e1);
+}
+
+// A batch of `count` CG iterations as a CUDA graph on the context's own stream,
+// captured once per (vector set, batch size, profiling) and replayed.
+template <typename TX, typename T>
+int batch_graph(tm_ctx *ctx, int count, const T *ce, T *part, TX *x, T *r, T *p, T *q, const T *dinv,
+                tm_ctx::Graph **out) {
+  const void *key[4] = {(const void *)x, (const void *)r, (const void *)ce, (const void *)part};
+  for (auto &g : ctx->graphs)
+    if (g.count == count && g.prof == ctx->prof_on && std::memcmp(g.key, key, sizeof(key)) == 0) {
+      *out = &g;
+      return TM_OK;
+    }
+  if (ctx->graphs.size() >= 8) {   // bounded cache: drop the oldest
+    TM_CUDA(ctx, cudaStreamSynchronize(ctx->gstream));
+    tm_ctx::Graph &old = ctx->graphs.front();
+    if (old.exec) cudaGraphExecDestroy(old.exec);
+    for (auto &pe : old.ev) {
+      cudaEventDestroy(pe.e0);
+      cudaEventDestroy(pe.e1);
+    }
+    ctx->graphs.pop_front();
+  }
+  if (ctx->prof_on) {   // no event creation while capturing
+    while (ctx->ev_free.size() < 2 * (size_t)count + 2) {
+      cudaEvent_t ev;
+      TM_CUDA(ctx, cudaEventCreate(&ev));
+      ctx->ev_free.push_back(ev);
+    }
+  }
+  tm_ctx::Graph g;
+  std::memcpy(g.key, key, sizeof(key));
+  g.count = count;
+  g.prof = ctx->prof_on;
+  cudaStream_t user = ctx->stream;
+  ctx->stream = ctx->gstream;
+  ctx->capturing = true;
+  const size_t base = ctx->ev_pending.size();
+  cudaError_t e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal);
+  int rc = TM_OK;
+  if (e == cudaSuccess) rc = enqueue_iterations<TX, T>(ctx, count, ce, part, x, r, p, q, dinv);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(ctx->gstream, &graph);
+  ctx->capturing = false;
+  ctx->stream = user;
+  // the pairs recorded while capturing belong to the graph
+  for (size_t i = base; i < ctx->ev_pending.size(); ++i) {
+    g.ev.push_back(ctx->ev_pending[i]);
+    g.ev.back().graph_owned = true;
+  }
+  ctx->ev_pending.resize(base);
+  ctx->launches -= 3 * count;   // counted at replay
+  if (e != cudaSuccess) return fail(ctx, TM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  if (rc) return rc;
+  if (e2 != cudaSuccess) return fail(ctx, TM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e2));
+  e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(ctx, TM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  ctx->graphs.push_back(std::move(g));
+  *out = &ctx->graphs.back();
   return TM_OK;
 }
 
@@ -483,18 +610,26 @@ int run_cg(tm_ctx *ctx, int check_every, int *iters_out, int *nonfinite, const T
   SolveScalars s;
   int rc = read_run(ctx, &s);
   if (rc) return rc;
+  tm_ctx::Graph *g = nullptr;
+  rc = batch_graph<TX, T>(ctx, check_every, ce, part, x, r, p, q, dinv, &g);
+  if (rc) return rc;
   while (!s.done) {
     const int it_before = s.it;
     const size_t base = ctx->ev_pending.size();
-    rc = enqueue_iterations<TX, T>(ctx, check_every, ce, part, x, r, p, q, dinv);
-    if (rc) return rc;
+    // user stream -> own stream -> user stream
+    TM_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
+    TM_CUDA(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev_fork, 0));
+    TM_CUDA(ctx, cudaGraphLaunch(g->exec, ctx->gstream));
+    TM_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->gstream));
+    TM_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+    ctx->launches += 3 * (int64_t)check_every;
+    for (const auto &pe : g->ev) ctx->ev_pending.push_back(pe);
     TM_CUDA(ctx, cudaMemcpyAsync(&s, solve_scalars(ctx), sizeof(s), cudaMemcpyDeviceToHost, ctx->stream));
     TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     // applications enqueued after convergence returned at once: not timed work
     const size_t real = base + (size_t)(s.it - it_before);
     while (ctx->ev_pending.size() > real) {
-      ctx->ev_free.push_back(ctx->ev_pending.back().e0);
-      ctx->ev_free.push_back(ctx->ev_pending.back().e1);
+      recycle(ctx, ctx->ev_pending.back());
       ctx->ev_pending.pop_back();
     }
     rc = drain_profile(ctx, true);

@@ -49,9 +49,14 @@ __device__ __forceinline__ void bwd_stage(T v[8], int bit) {
 }
 
 // X, Y: 24 values, DOF 3*k + c of corner k = i + 2j + 4m.
-// WANT_ENERGY: returns x^T K0 x (Y untouched); otherwise writes Y = coef * K0 X.
-template <typename T, bool WANT_ENERGY>
+// MODE 0: writes Y = coef K0 X.  MODE 1: returns X^T K0 X (Y untouched).
+// MODE 2: both, returning coef X^T K0 X (a sum of per-block quadratic forms of
+// positive semidefinite blocks, free of the cancellation of X . Y).
+constexpr int kOpApply = 0, kOpEnergy = 1, kOpBoth = 2;
+template <typename T, int MODE>
 __device__ __forceinline__ T element_op(const T X[24], T Y[24], T coef, const ModalBlocks<T> &M) {
+  constexpr bool WANT_ENERGY = MODE != kOpApply;
+  constexpr bool WANT_Y = MODE != kOpEnergy;
   T w[3][8];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -84,15 +89,14 @@ __device__ __forceinline__ T element_op(const T X[24], T Y[24], T coef, const Mo
       r1 = M.b[s][1][0] * a0 + M.b[s][1][1] * a1 + M.b[s][1][2] * a2;
       r2 = M.b[s][2][0] * a0 + M.b[s][2][1] * a1 + M.b[s][2][2] * a2;
     }
-    if (WANT_ENERGY) {
-      energy += a0 * r0 + a1 * r1 + a2 * r2;
-    } else {
+    if (WANT_ENERGY) energy += a0 * r0 + a1 * r1 + a2 * r2;
+    if (WANT_Y) {
       z[0][s ^ 1] = r0;
       z[1][s ^ 2] = r1;
       z[2][s ^ 4] = r2;
     }
   }
-  if (WANT_ENERGY) return energy;
+  if (!WANT_Y) return energy;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
 #pragma unroll
@@ -103,5 +107,5 @@ __device__ __forceinline__ T element_op(const T X[24], T Y[24], T coef, const Mo
 #pragma unroll
     for (int k = 0; k < 8; ++k) Y[3 * k + c] = z[c][k];
   }
-  return T(0);
+  return WANT_ENERGY ? coef * energy : T(0);
 }

@@ -46,7 +46,9 @@ struct ApplyParams {
   const T *x;
   T *y;
   T *part;
-  double *dotp;     // per-CTA partials of x . y (nullptr: skip)
+  double *dotp;     // per-CTA partials of x^T A x (nullptr: skip)
+  SolveScalars *sc; // with dotp: the last CTA sets sc->pq and sc->alpha = sc->rz / pq
+  unsigned int *ticket;
   const int *done;  // skip the launch when set (nullptr: never)
   ModalBlocks<T> K;
   int nblk;
@@ -158,7 +160,10 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(T) == 4 ? 4 : 2) apply_b
     }
   }
   __syncthreads();
-  // 2. element operator: gather the 8 corners, results into the slots
+  // 2. element operator: gather the 8 corners, results into the slots; x^T A x is
+  // the sum of the element energies c_e X_e^T K0 X_e (C and the Dirichlet zeros are
+  // already in X_e)
+  double dot = 0.0;
   if (tid < ne) {
     const uint4 cw = lcorner[tid];
     const int code[8] = {(int)(cw.x & 0xFFFF), (int)(cw.x >> 16), (int)(cw.y & 0xFFFF), (int)(cw.y >> 16),
@@ -170,7 +175,8 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(T) == 4 ? 4 : 2) apply_b
       X[3 * k + 1] = R[3 * code[k] + 1];
       X[3 * k + 2] = R[3 * code[k] + 2];
     }
-    element_op<T, false>(X, Y, P.ce[e0 + tid], P.K);
+    if (P.dotp) dot = (double)element_op<T, kOpBoth>(X, Y, P.ce[e0 + tid], P.K);
+    else element_op<T, kOpApply>(X, Y, P.ce[e0 + tid], P.K);
 #pragma unroll
     for (int j = 0; j < 24; ++j) XY[tid * kRow + j] = Y[j];
   }
@@ -188,7 +194,6 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(T) == 4 ? 4 : 2) apply_b
   }
   __syncthreads();
   // 3b/4. regular nodes: own slots + folded hanging sums (C^T), then store
-  double dot = 0.0;
   for (int i = tid; i < nreg; i += kApplyThreads) {
     T s0 = T(0), s1 = T(0), s2 = T(0);
     const int q1 = ip[i + 1];
@@ -211,63 +216,46 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(T) == 4 ? 4 : 2) apply_b
     } else {
       T *dst = P.y + 3 * (size_t)(gw & 0x7FFFFFFFu);
       dst[0] = s0; dst[1] = s1; dst[2] = s2;
-      dot += (double)R[3 * i] * (double)s0 + (double)R[3 * i + 1] * (double)s1 + (double)R[3 * i + 2] * (double)s2;
     }
   }
   if (P.dotp) {
     dot = block_sum<kApplyThreads>(dot);
     if (tid == 0) P.dotp[b] = dot;
+    if (P.sc && last_cta(P.ticket)) {
+      const double pq = sum_partials<kApplyThreads>(P.dotp, gridDim.x);
+      if (tid == 0) {
+        P.sc->pq = pq;
+        P.sc->alpha = P.sc->rz / pq;
+        if (!isfinite(pq) || !isfinite(P.sc->alpha) || pq <= 0.0) {
+          P.sc->nonfinite = 1;
+          P.sc->done = 1;
+        }
+      }
+    }
   }
 }
 
 // Second pass: each shared node sums its contiguous run of partials (one per
 // block touching it, in ascending block order); optionally hanging DOFs of y are
-// zeroed.  With dot partials, the last CTA also finishes p^T A p and sets
-// alpha = rz / pq for CG (when sc is given).
+// zeroed.
 template <typename T>
 __global__ void __launch_bounds__(256) apply_shared_kernel(const int32_t *sh_node, const int32_t *sh_ptr, int64_t nsh,
-                                                           const int32_t *hang_node, int64_t nh,
-                                                           const uint8_t *nflag, const T *part, const T *x,
-                                                           T *y, double *dotp, int nblk_partials,
-                                                           SolveScalars *sc, unsigned int *ticket,
+                                                           const int32_t *hang_node, int64_t nh, const T *part, T *y,
                                                            const int *done) {
   if (done && *(volatile const int *)done) return;
-  double dot = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nsh + nh;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (i < nsh) {
-      const int g = sh_node[i];
-      T s0 = T(0), s1 = T(0), s2 = T(0);
-      for (int j = sh_ptr[i]; j < sh_ptr[i + 1]; ++j) {
-        const T *src = part + 3 * (size_t)j;
-        s0 += src[0]; s1 += src[1]; s2 += src[2];
-      }
-      T *dst = y + 3 * (size_t)g;
-      dst[0] = s0; dst[1] = s1; dst[2] = s2;
-      if (dotp) {
-        const T *xv = x + 3 * (size_t)g;
-        if (!(nflag[g] & 1))
-          dot += (double)xv[0] * (double)s0 + (double)xv[1] * (double)s1 + (double)xv[2] * (double)s2;
-      }
-    } else {
-      T *dst = y + 3 * (size_t)hang_node[i - nsh];
-      dst[0] = dst[1] = dst[2] = T(0);
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < nsh) {
+    const int g = sh_node[i];
+    T s0 = T(0), s1 = T(0), s2 = T(0);
+    for (int j = sh_ptr[i]; j < sh_ptr[i + 1]; ++j) {
+      const T *src = part + 3 * (size_t)j;
+      s0 += src[0]; s1 += src[1]; s2 += src[2];
     }
-  }
-  if (dotp) {
-    dot = block_sum<256>(dot);
-    if (threadIdx.x == 0) dotp[nblk_partials + blockIdx.x] = dot;
-    if (sc && last_cta(ticket)) {
-      const double pq = sum_partials<256>(dotp, nblk_partials + gridDim.x);
-      if (threadIdx.x == 0) {
-        sc->pq = pq;
-        sc->alpha = sc->rz / pq;
-        if (!isfinite(pq) || !isfinite(sc->alpha) || pq <= 0.0) {
-          sc->nonfinite = 1;
-          sc->done = 1;
-        }
-      }
-    }
+    T *dst = y + 3 * (size_t)g;
+    dst[0] = s0; dst[1] = s1; dst[2] = s2;
+  } else if (i < nsh + nh) {
+    T *dst = y + 3 * (size_t)hang_node[i - nsh];
+    dst[0] = dst[1] = dst[2] = T(0);
   }
 }
 
@@ -285,9 +273,8 @@ int shared_grid(int64_t n) {
 }
 
 template <typename T>
-cudaError_t launch_apply(const DeviceMesh &m, const T *ce, const T *x, T *y, T *part, double *dot_partials,
-                         SolveScalars *sc, unsigned int *ticket, bool zero_hanging, const int *done,
-                         cudaStream_t s) {
+cudaError_t launch_apply_blocks(const DeviceMesh &m, const T *ce, const T *x, T *y, T *part, double *energy_partials,
+                                SolveScalars *sc, unsigned int *ticket, const int *done, cudaStream_t s) {
   static size_t configured = 0;
   const int rec_bytes = (m.max_rec_bytes + 15) / 16 * 16;
   const size_t smem = apply_smem_bytes<T>(m.max_local, rec_bytes);
@@ -297,22 +284,32 @@ cudaError_t launch_apply(const DeviceMesh &m, const T *ce, const T *x, T *y, T *
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  const int g = std::max(m.nblk, 1);
   ApplyParams<T> P;
   P.brec = m.brec; P.rec_off = m.rec_off; P.ce = ce; P.x = x; P.y = y; P.part = part;
-  P.dotp = dot_partials; P.done = done; P.nblk = m.nblk;
+  P.dotp = energy_partials; P.sc = sc; P.ticket = ticket; P.done = done; P.nblk = m.nblk;
   for (int i = 0; i < 72; ++i) (&P.K.b[0][0][0])[i] = (T)m.modal[i];
   P.max_local = m.max_local; P.rec_bytes = rec_bytes;
-  if (m.nblk > 0) apply_blocks_kernel<T><<<g, kApplyThreads, smem, s>>>(P);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int64_t items = m.nsh + (zero_hanging ? m.nh : 0);
-  apply_shared_kernel<T><<<item_grid(items), 256, 0, s>>>(m.sh_node, m.sh_ptr, m.nsh, m.hang_node,
-                                                          zero_hanging ? m.nh : 0, m.nflag, part, x, y,
-                                                          dot_partials, m.nblk > 0 ? g : 0, sc, ticket, done);
+  if (m.nblk > 0) apply_blocks_kernel<T><<<m.nblk, kApplyThreads, smem, s>>>(P);
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_apply(const DeviceMesh &m, const T *ce, const T *x, T *y, T *part, double *dot_partials,
+                         SolveScalars *sc, unsigned int *ticket, bool zero_hanging, const int *done,
+                         cudaStream_t s) {
+  cudaError_t e = launch_apply_blocks<T>(m, ce, x, y, part, dot_partials, sc, ticket, done, s);
+  if (e != cudaSuccess) return e;
+  const int64_t items = m.nsh + (zero_hanging ? m.nh : 0);
+  apply_shared_kernel<T><<<item_grid(items), 256, 0, s>>>(m.sh_node, m.sh_ptr, m.nsh, m.hang_node,
+                                                          zero_hanging ? m.nh : 0, part, y, done);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_apply_blocks<double>(const DeviceMesh &, const double *, const double *, double *,
+                                                 double *, double *, SolveScalars *, unsigned int *, const int *,
+                                                 cudaStream_t);
+template cudaError_t launch_apply_blocks<float>(const DeviceMesh &, const float *, const float *, float *, float *,
+                                                double *, SolveScalars *, unsigned int *, const int *, cudaStream_t);
 template cudaError_t launch_apply<double>(const DeviceMesh &, const double *, const double *, double *, double *,
                                           double *, SolveScalars *, unsigned int *, bool, const int *, cudaStream_t);
 template cudaError_t launch_apply<float>(const DeviceMesh &, const float *, const float *, float *, float *,

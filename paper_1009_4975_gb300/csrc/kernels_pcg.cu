@@ -3,7 +3,8 @@
 // reductions finalised on the device, so the iteration needs no host round trip.
 //
 // Iteration (x: solution, z = Dinv r is never stored):
-//   q = A p ; pq = p.q and alpha = rz / pq (fused into the operator's passes)
+//   q = A p ; pq = sum of element energies of p, alpha = rz / pq (in the operator's
+//   block pass; the q of shared nodes is summed from their partials by the update)
 //   x += alpha p ; r -= alpha q ; rz' = r.Dinv r ; rr = r.r          beta = rz' / rz
 //   p = Dinv r + beta p
 // Every kernel returns immediately once the device flag `done` is set, so a
@@ -60,6 +61,68 @@ __global__ void __launch_bounds__(kVecThreads) update_kernel(TX *x, const T *p, 
       } else if (s1 <= sc->stop_rr || sc->it >= sc->max_it) {
         sc->done = 1;
         sc->last_beta_skipped = 1;
+      }
+    }
+  }
+}
+
+// Same update, node by node, for an operator result q that is complete only at
+// nodes owned by one block: the q of a shared node is the sum of its partials
+// (contiguous, ascending block order), read here instead of a second pass.
+template <typename TX, typename T>
+__global__ void __launch_bounds__(kVecThreads) update_nodes_kernel(TX *x, const T *p, const T *q, T *r, const T *dinv,
+                                                                   int64_t Nn, const int32_t *sh_of_node,
+                                                                   const int32_t *sh_ptr, const T *part,
+                                                                   SolveScalars *sc, double *partials,
+                                                                   unsigned int *ticket) {
+  if (sc->done) return;
+  const double alpha = sc->alpha;
+  const T a = (T)alpha;
+  DotAcc<T> arz, arr;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < Nn; n += (int64_t)gridDim.x * blockDim.x) {
+    T qv[3];
+    const int sh = sh_of_node[n];
+    if (sh < 0) {
+      qv[0] = q[3 * n]; qv[1] = q[3 * n + 1]; qv[2] = q[3 * n + 2];
+    } else {
+      qv[0] = qv[1] = qv[2] = T(0);
+      for (int j = sh_ptr[sh]; j < sh_ptr[sh + 1]; ++j) {
+        qv[0] += part[3 * (size_t)j]; qv[1] += part[3 * (size_t)j + 1]; qv[2] += part[3 * (size_t)j + 2];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int64_t i = 3 * n + c;
+      x[i] += (TX)alpha * (TX)p[i];
+      const T ri = r[i] - a * qv[c];
+      r[i] = ri;
+      arz.add_prod(ri, dinv[i] * ri);
+      arr.add_prod(ri, ri);
+    }
+  }
+  double rz = arz.value(), rr = arr.value();
+  block_sum2<kVecThreads>(rz, rr);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = rz;
+    partials[2 * blockIdx.x + 1] = rr;
+  }
+  if (last_cta(ticket)) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += kVecThreads) {
+      s0 += ((volatile double *)partials)[2 * i];
+      s1 += ((volatile double *)partials)[2 * i + 1];
+    }
+    block_sum2<kVecThreads>(s0, s1);
+    if (threadIdx.x == 0) {
+      sc->beta = s0 / sc->rz;
+      sc->rz = s0;
+      sc->rr = s1;
+      sc->it += 1;
+      if (!finite(s0) || !finite(s1)) {
+        sc->nonfinite = 1;
+        sc->done = 1;
+      } else if (s1 <= sc->stop_rr || sc->it >= sc->max_it) {
+        sc->done = 1;
       }
     }
   }
@@ -168,6 +231,22 @@ template cudaError_t launch_update<double, double>(double *, const double *, con
                                                    unsigned int *, cudaStream_t);
 template cudaError_t launch_update<float, float>(float *, const float *, const float *, float *, const float *,
                                                  int64_t, SolveScalars *, double *, unsigned int *, cudaStream_t);
+
+template <typename TX, typename T>
+cudaError_t launch_update_nodes(TX *x, const T *p, const T *q, T *r, const T *dinv, int64_t Nn,
+                                const int32_t *sh_of_node, const int32_t *sh_ptr, const T *part, SolveScalars *sc,
+                                double *partials, unsigned int *ticket, cudaStream_t s) {
+  update_nodes_kernel<TX, T><<<vec_grid(Nn), kVecThreads, 0, s>>>(x, p, q, r, dinv, Nn, sh_of_node, sh_ptr, part, sc,
+                                                                   partials, ticket);
+  return cudaGetLastError();
+}
+template cudaError_t launch_update_nodes<double, double>(double *, const double *, const double *, double *,
+                                                         const double *, int64_t, const int32_t *, const int32_t *,
+                                                         const double *, SolveScalars *, double *, unsigned int *,
+                                                         cudaStream_t);
+template cudaError_t launch_update_nodes<float, float>(float *, const float *, const float *, float *, const float *,
+                                                       int64_t, const int32_t *, const int32_t *, const float *,
+                                                       SolveScalars *, double *, unsigned int *, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_pupdate(T *p, const T *r, const T *dinv, int64_t n, SolveScalars *sc, cudaStream_t s) {

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(kTopThreads) sensitivity_kernel(const int32_t 
       X[3 * k + 1] = src[1];
       X[3 * k + 2] = src[2];
     }
-    const double en = element_op<double, true>(X, nullptr, 1.0, K);
+    const double en = element_op<double, kOpEnergy>(X, nullptr, 1.0, K);
     const double h = ldexp(h0, -leaf[4 * e + 3]);
     const double r = rho[e];
     dc[e] = -penal * pow(r, penal - 1.0) * (E0 - Emin) * h * en;

@@ -487,8 +487,10 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
         m.lslot[m.blk_slot[b] + i] = fill[n]++;
       }
     m.sh_ptr.push_back(0);
+    m.sh_of_node.assign(Nn, -1);
     for (int64_t n = 0; n < Nn; ++n)
       if (cnt[n + 1] > 0) {
+        m.sh_of_node[n] = (int32_t)m.sh_node.size();
         m.sh_node.push_back((int32_t)n);
         m.sh_ptr.push_back(start[n + 1]);
       }

@@ -19,6 +19,10 @@ int vec_grid(int64_t n);
 template <typename TX, typename T>
 cudaError_t launch_update(TX *x, const T *p, const T *q, T *r, const T *dinv, int64_t n, SolveScalars *sc,
                           double *partials, unsigned int *ticket, cudaStream_t s);
+template <typename TX, typename T>
+cudaError_t launch_update_nodes(TX *x, const T *p, const T *q, T *r, const T *dinv, int64_t Nn,
+                                const int32_t *sh_of_node, const int32_t *sh_ptr, const T *part, SolveScalars *sc,
+                                double *partials, unsigned int *ticket, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pupdate(T *p, const T *r, const T *dinv, int64_t n, SolveScalars *sc, cudaStream_t s);
 template <typename T>

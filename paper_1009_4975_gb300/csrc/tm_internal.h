@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <deque>
 #include <string>
 #include <vector>
 
@@ -64,6 +65,7 @@ struct HostMesh {
   // second pass over shared nodes
   std::vector<int32_t> sh_node;       // shared node ids
   std::vector<int32_t> sh_ptr;        // CSR: partials of shared node i are [sh_ptr[i], sh_ptr[i+1])
+  std::vector<int32_t> sh_of_node;    // node -> shared-node index or -1
   // Jacobi diagonal: node-centric CSR of (element, coefficient-triple index)
   std::vector<int32_t> dg_ptr;        // Nn+1
   std::vector<int32_t> dg_elem;
@@ -113,6 +115,7 @@ struct DeviceMesh {
   int32_t *rec_off = nullptr;
   int32_t max_rec_bytes = 0;
   int32_t *sh_node = nullptr, *sh_ptr = nullptr;
+  int32_t *sh_of_node = nullptr;      // node -> shared-node index, -1 when one block owns it
   int32_t *dg_ptr = nullptr, *dg_elem = nullptr;
   uint16_t *dg_q = nullptr;
   double *dg_tab = nullptr;
@@ -156,18 +159,32 @@ struct tm_ctx {
   tm_profile_data prof = tm_profile_data();
   struct Pending {
     cudaEvent_t e0, e1;
-    int kind;  // 1: FP32 operator, 0: FP64 operator
+    int kind;          // 1: FP32 operator, 0: FP64 operator
+    bool graph_owned;  // recorded by a captured graph (kept with it)
   };
   std::vector<Pending> ev_pending;
   std::vector<cudaEvent_t> ev_free;
+  // CG batches captured as CUDA graphs, replayed on the context's own stream
+  struct Graph {
+    const void *key[4] = {};
+    int count = 0;
+    bool prof = false;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<Pending> ev;
+  };
+  std::deque<Graph> graphs;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool capturing = false;
 };
 
 namespace amr {
 // device-side launchers of the operator file; each returns the launch's cudaError_t
 cudaError_t launch_coeff(const DeviceMesh &m, const Work &w, const double *rho, cudaStream_t s);
 struct SolveScalars;
-// y = C^T K C x.  With dot_partials: also x . y; with sc: alpha = sc->rz / (x . y)
-// computed by the last CTA of the second pass (ticket: its counter).
+// y = C^T K C x.  With dot_partials: also x^T A x (element energies); with sc:
+// alpha = sc->rz / (x^T A x) computed by the last CTA of the block pass (ticket:
+// its counter).
 template <typename T>
 cudaError_t launch_apply(const DeviceMesh &m, const T *ce, const T *x, T *y, T *part, double *dot_partials,
                          SolveScalars *sc, unsigned int *ticket, bool zero_hanging, const int *done,
@@ -176,6 +193,11 @@ cudaError_t launch_diag(const DeviceMesh &m, const double *ce, double *d, double
                         cudaStream_t s);
 cudaError_t launch_expand(const DeviceMesh &m, const double *u, double *uf, cudaStream_t s);
 int shared_grid(int64_t n);
+// The block pass alone: y is complete at nodes owned by one block; shared nodes'
+// contributions are left in `part` (CSR order, see DeviceMesh::sh_ptr).
+template <typename T>
+cudaError_t launch_apply_blocks(const DeviceMesh &m, const T *ce, const T *x, T *y, T *part, double *energy_partials,
+                                SolveScalars *sc, unsigned int *ticket, const int *done, cudaStream_t s);
 
 // Static scratch of the no-allocation operator entry point (kernels_apply.cu).
 constexpr int64_t kStaticElems = int64_t(1) << 21;   // coefficients: meshes up to 2,097,152 elements
