@@ -169,7 +169,8 @@ def run_gpu(args):
     rmin = w.r_min
 
     def step(rho_in, rho_out, prec=P.TM_PREC_MIXED):
-        st = P.tm_pcg_solve(ctx, rho_in, f, u, rtol=1e-8, max_iter=200000, precision=prec, check_every=64)
+        st = P.tm_pcg_solve(ctx, rho_in, f, u, rtol=1e-8, max_iter=200000, precision=prec, check_every=64,
+                            graphs=not args.no_graphs)
         P.tm_expand(ctx, u, uf)
         comp = P.tm_sensitivity(ctx, rho_in, uf, dc)
         P.tm_filter(ctx, rho_in, dc, rmin, 0, dch)
@@ -296,6 +297,29 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_apply(args):
+    """Profiling workload for ncu: upload the benchmark mesh and run K FP32 operator applications."""
+    import torch
+    import paper_1009_4975_gb300 as P
+    from paper_1009_4975_gb300 import build
+    import workloads as W
+    build.build()
+    w = W.config2()
+    d = w.dom
+    ctx = P.tm_create(0, stream=torch.cuda.current_stream())
+    info = P.tm_mesh_upload(ctx, d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, w.dirichlet_faces, w.E0, w.Emin, w.nu,
+                            w.penal)
+    perm = P.tm_mesh_tables(ctx)["perm"]
+    rho = torch.as_tensor(w.rho[perm], device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    x = torch.randn(3 * info["Nn"], dtype=torch.float32, device="cuda", generator=gen)
+    y = torch.zeros_like(x)
+    for _ in range(args.profile_apply):
+        P.tm_apply_K_f32(ctx, rho, x, y)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_apply": args.profile_apply, "elements": info["Ne"]}), flush=True)
+
+
 def _sample_workload(w=None):
     """Bounded sample of the benchmark mesh: its leaves inside the first two base-cell layers at
     the clamped face, as a mesh of its own (domain 2 x 24 x 24 base cells, same levels)."""
@@ -359,8 +383,14 @@ def main():
     ap.add_argument("--fp64-iters", type=int, default=400, help="FP64 PCG iterations for its throughput figure")
     ap.add_argument("--cpu-iters", type=int, default=600, help="oracle PCG iterations of the CPU baseline")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="plain kernel launches instead of CUDA-graph batches (for launch-list profiling)")
+    ap.add_argument("--profile-apply", type=int, default=0,
+                    help="profiling workload: K FP32 operator applications on the benchmark mesh, no timing")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_apply > 0:
+        run_profile_apply(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -94,6 +94,9 @@ typedef struct {
   int32_t precision;          /* TM_PREC_FP64 or TM_PREC_MIXED                    */
   double inner_rtol;          /* mixed: residual reduction of one FP32 sweep      */
   int32_t check_every;        /* iterations between host convergence checks       */
+  int32_t no_graphs;          /* 0: each batch of check_every CG iterations is a   */
+                              /* CUDA graph replayed on a library stream; 1: plain */
+                              /* launches on the context's stream                   */
 } tm_solve_opts;
 
 typedef struct {

@@ -605,25 +605,32 @@ int batch_graph(tm_ctx *ctx, int count, const T *ce, T *part, TX *x, T *r, T *p,
 }
 
 template <typename TX, typename T>
-int run_cg(tm_ctx *ctx, int check_every, int *iters_out, int *nonfinite, const T *ce, T *part, TX *x, T *r, T *p,
-           T *q, const T *dinv) {
+int run_cg(tm_ctx *ctx, int check_every, bool graphs, int *iters_out, int *nonfinite, const T *ce, T *part, TX *x,
+           T *r, T *p, T *q, const T *dinv) {
   SolveScalars s;
   int rc = read_run(ctx, &s);
   if (rc) return rc;
   tm_ctx::Graph *g = nullptr;
-  rc = batch_graph<TX, T>(ctx, check_every, ce, part, x, r, p, q, dinv, &g);
-  if (rc) return rc;
+  if (graphs) {
+    rc = batch_graph<TX, T>(ctx, check_every, ce, part, x, r, p, q, dinv, &g);
+    if (rc) return rc;
+  }
   while (!s.done) {
     const int it_before = s.it;
     const size_t base = ctx->ev_pending.size();
-    // user stream -> own stream -> user stream
-    TM_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
-    TM_CUDA(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev_fork, 0));
-    TM_CUDA(ctx, cudaGraphLaunch(g->exec, ctx->gstream));
-    TM_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->gstream));
-    TM_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
-    ctx->launches += 3 * (int64_t)check_every;
-    for (const auto &pe : g->ev) ctx->ev_pending.push_back(pe);
+    if (g) {
+      // user stream -> own stream -> user stream
+      TM_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
+      TM_CUDA(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev_fork, 0));
+      TM_CUDA(ctx, cudaGraphLaunch(g->exec, ctx->gstream));
+      TM_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->gstream));
+      TM_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+      ctx->launches += 3 * (int64_t)check_every;
+      for (const auto &pe : g->ev) ctx->ev_pending.push_back(pe);
+    } else {
+      rc = enqueue_iterations<TX, T>(ctx, check_every, ce, part, x, r, p, q, dinv);
+      if (rc) return rc;
+    }
     TM_CUDA(ctx, cudaMemcpyAsync(&s, solve_scalars(ctx), sizeof(s), cudaMemcpyDeviceToHost, ctx->stream));
     TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     // applications enqueued after convergence returned at once: not timed work
@@ -657,6 +664,7 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
   cudaStream_t st = ctx->stream;
   const int64_t n = 3 * m.Nn;
   const int check = opts->check_every > 0 ? opts->check_every : 32;
+  const bool graphs = opts->no_graphs == 0;
   tm_solve_stats out;
   std::memset(&out, 0, sizeof(out));
 
@@ -690,7 +698,7 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
       TM_CUDA(ctx, launch_start<double>(f_dev, w.q, 1.0, w.r, w.p, w.dinv, n, solve_scalars(ctx), w.red, w.ticket + 2, st));
       ctx->launches += 1;
       int it = 0, nf = 0;
-      rc = run_cg<double, double>(ctx, check, &it, &nf, w.ce64, w.part64, u_dev, w.r, w.p, w.q, w.dinv);
+      rc = run_cg<double, double>(ctx, check, graphs, &it, &nf, w.ce64, w.part64, u_dev, w.r, w.p, w.q, w.dinv);
       if (rc) return rc;
       out.iterations += it;
       out.fp64_applies += it;
@@ -740,7 +748,8 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
                                        w.ticket + 2, st));
       ctx->launches += 1;
       int it = 0, nf = 0;
-      rc = run_cg<float, float>(ctx, check, &it, &nf, w.ce32, w.part32, w.x32, w.r32, w.p32, w.q32, w.dinv32);
+      rc = run_cg<float, float>(ctx, check, graphs, &it, &nf, w.ce32, w.part32, w.x32, w.r32, w.p32, w.q32,
+                                w.dinv32);
       if (rc) return rc;
       out.iterations += it;
       out.fp32_applies += it;

@@ -43,7 +43,7 @@ class tm_mesh_info(C.Structure):
 
 class tm_solve_opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
-                ("inner_rtol", C.c_double), ("check_every", C.c_int32)]
+                ("inner_rtol", C.c_double), ("check_every", C.c_int32), ("no_graphs", C.c_int32)]
 
 
 class tm_solve_stats(C.Structure):
@@ -263,9 +263,9 @@ def tm_jacobi_diag(ctx: Ctx, rho, d):
 
 
 def tm_pcg_solve(ctx: Ctx, rho, f, u, rtol=1e-8, max_iter=100000, precision=TM_PREC_FP64, inner_rtol=1e-3,
-                 check_every=64, raise_on_error=True) -> dict:
+                 check_every=64, raise_on_error=True, graphs=True) -> dict:
     import torch
-    o = tm_solve_opts(rtol, max_iter, precision, inner_rtol, check_every)
+    o = tm_solve_opts(rtol, max_iter, precision, inner_rtol, check_every, 0 if graphs else 1)
     s = tm_solve_stats()
     rc = load_library().tm_pcg_solve(ctx.handle, _elem(ctx, rho, "rho"), _vec(ctx, f, torch.float64, "f"),
                                      _vec(ctx, u, torch.float64, "u"), C.byref(o), C.byref(s))
