@@ -132,6 +132,20 @@ def _dist():
     return ws, rank, local
 
 
+def aggregate(total_ms: float, iters: float, device):
+    """Max of the timed milliseconds and sum of the CG iterations over all ranks (identity for one
+    process).  Replicas exchange nothing else."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return total_ms, iters
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    n = torch.tensor([iters], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -213,15 +227,7 @@ def run_gpu(args):
     prof = P.tm_profile_read(ctx)
     P.tm_profile(ctx, False)
     total_ms = float(sum(step_ms))
-    if ws > 1:
-        t = torch.tensor([total_ms, float(iters)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        tsum = t.clone()
-        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
-        total_ms_job, iters_job = float(tmax[0]), float(tsum[1])
-    else:
-        total_ms_job, iters_job = total_ms, float(iters)
+    total_ms_job, iters_job = aggregate(total_ms, float(iters), dev)
     value = nfree * iters_job / (total_ms_job * 1e-3) / 1e9
 
     # ---- end to end: host (pinned) inputs copied in and results copied out each step

@@ -168,3 +168,52 @@ def to_full_layout(mesh: Mesh, v_free: np.ndarray) -> np.ndarray:
 
 def from_full_layout(mesh: Mesh, v_full: np.ndarray) -> np.ndarray:
     return np.asarray(v_full).reshape(-1, 3)[free_nodes(mesh)].ravel()
+
+
+def operator_rows(mesh: Mesh, rho, x_full, nodes, E0=1.0, Emin=1e-9, nu=0.3, penal=3.0, absolute=False):
+    """(C^T K(rho) C x) at the given (free) nodes, element by element, for meshes too large to
+    assemble: x_full is an A-space vector (3 Nn, constrained entries ignored).  With `absolute`
+    every factor is replaced by its absolute value, giving the rounding scale (|A| |x|)."""
+    K0 = reference_stiffness(nu)
+    if absolute:
+        K0 = np.abs(K0)
+    x = np.asarray(x_full, np.float64).reshape(-1, 3)
+    if absolute:
+        x = np.abs(x)
+    ce = young(rho, E0, Emin, penal) * mesh.h
+    hang = mesh.hanging
+    # node -> (element, corner) incidences, and master -> hanging nodes
+    order = np.argsort(mesh.conn.ravel(), kind="stable")
+    flat = mesh.conn.ravel()[order]
+    starts = np.searchsorted(flat, np.arange(mesh.Nn + 1))
+    of_master = {}
+    for h, ms in hang.items():
+        for mm, w in ms:
+            of_master.setdefault(mm, []).append((h, float(w)))
+
+    def corner_value(n):
+        if mesh.dirichlet[n]:
+            return np.zeros(3)
+        if n in hang:
+            v = np.zeros(3)
+            for mm, w in hang[n]:
+                if not mesh.dirichlet[mm]:
+                    v += float(w) * x[mm]
+            return v
+        return x[n]
+
+    def element_result(e):
+        X = np.concatenate([corner_value(n) for n in mesh.conn[e]])
+        return (ce[e] * (K0 @ X)).reshape(8, 3)
+
+    out = np.zeros((len(nodes), 3))
+    for i, t in enumerate(nodes):
+        t = int(t)
+        acc = np.zeros(3)
+        terms = [(t, 1.0)] + of_master.get(t, [])
+        for n, w in terms:
+            for pos in order[starts[n]:starts[n + 1]]:
+                e, k = divmod(int(pos), 8)
+                acc += w * element_result(e)[k]
+        out[i] = acc
+    return out

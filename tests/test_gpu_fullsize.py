@@ -1,0 +1,146 @@
+"""Parity at the benchmark's full size (base 48x24x24, three levels, ~2M elements), in the launch
+configuration the bench times.  The oracle cannot assemble this system, so outputs are checked on
+samples it computes one by one (operator rows, element sensitivities, filter values) and through
+properties that hold at any size (integer tables bit for bit, residual of the solve measured with
+the independently validated FP64 operator, OC volume closure)."""
+import numpy as np
+import pytest
+
+from tests.gpu_common import U32, U64, ctx, tm
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def full():
+    import torch
+    import workloads as W
+    from oracle import mesh as M
+    w = W.config2()
+    d = w.dom
+    info = tm().tm_mesh_upload(ctx(), d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, w.dirichlet_faces, w.E0, w.Emin, w.nu,
+                               w.penal)
+    m = M.build_mesh(d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, dirichlet_faces=w.dirichlet_faces)
+    rho = w.rho[m.perm].copy()
+    dev = torch.device("cuda:0")
+    return {"w": w, "m": m, "rho": rho, "info": info, "dev": dev,
+            "rho_d": torch.as_tensor(rho, device=dev)}
+
+
+def test_fullsize_tables_bit_exact(full):
+    m = full["m"]
+    t = tm().tm_mesh_tables(ctx())
+    assert np.array_equal(t["perm"], m.perm)
+    assert np.array_equal(t["node_xyz"], m.nodes)
+    assert np.array_equal(t["conn"], m.conn)
+    hn = m.hanging_ids()
+    assert np.array_equal(t["hang_node"], hn)
+    hm = np.full((hn.size, 4), -1, np.int64)
+    for i, h in enumerate(hn):
+        ms = [j for j, _ in m.hanging[h]]
+        hm[i, :len(ms)] = ms
+    assert np.array_equal(t["hang_master"], hm)
+
+
+def _sample_free_nodes(m, n, seed):
+    from oracle import fem as F
+    fn = F.free_nodes(m)
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(fn.size, size=n, replace=False)
+    # include hanging-node masters explicitly: they exercise C^T
+    masters = sorted({mm for ms in m.hanging.values() for mm, _ in ms} & set(fn.tolist()))
+    extra = rng.choice(len(masters), size=n // 4, replace=False)
+    return np.unique(np.concatenate([fn[pick], np.asarray(masters)[extra]]))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_fullsize_operator_rows(full, prec):
+    import torch
+    from oracle import fem as F
+    m, w = full["m"], full["w"]
+    rng = np.random.default_rng(31)
+    x = rng.standard_normal(3 * m.Nn)
+    if prec == "f32":
+        x = x.astype(np.float32).astype(np.float64)
+        xd = torch.as_tensor(x, dtype=torch.float32, device=full["dev"])
+        yd = torch.zeros_like(xd)
+        tm().tm_apply_K_f32(ctx(), full["rho_d"], xd, yd)
+        u = U32
+    else:
+        xd = torch.as_tensor(x, device=full["dev"])
+        yd = torch.zeros_like(xd)
+        tm().tm_apply_K(ctx(), full["rho_d"], xd, yd)
+        u = U64
+    y = yd.double().cpu().numpy().reshape(-1, 3)
+    nodes = _sample_free_nodes(m, 192, 5)
+    ref = F.operator_rows(m, full["rho"], x, nodes, w.E0, w.Emin, w.nu, w.penal)
+    scale = F.operator_rows(m, full["rho"], x, nodes, w.E0, w.Emin, w.nu, w.penal, absolute=True)
+    assert np.all(np.abs(y[nodes] - ref) <= 256 * u * scale)
+
+
+def test_fullsize_mixed_solve_residual(full):
+    """The bench's solve (mixed precision, rtol 1e-8): its residual measured with the FP64
+    operator (validated row by row above) and FP64 norms."""
+    import torch
+    w = full["w"]
+    f = torch.zeros(3 * full["m"].Nn, dtype=torch.float64, device=full["dev"])
+    tm().tm_build_rhs(ctx(), w.load_nodes, w.load_comp, w.load_val, f)
+    u = torch.zeros_like(f)
+    st = tm().tm_pcg_solve(ctx(), full["rho_d"], f, u, rtol=1e-8, max_iter=200000, precision=1, check_every=64)
+    q = torch.zeros_like(u)
+    tm().tm_apply_K(ctx(), full["rho_d"], u, q)
+    rel = float(torch.linalg.norm(f - q) / torch.linalg.norm(f))
+    assert st["status"] == 0
+    assert rel <= 1e-8
+    full["u"] = u
+
+
+def test_fullsize_sensitivity_filter_oc_samples(full):
+    import torch
+    from scipy.spatial import cKDTree
+    from oracle import fem as F
+    from oracle import topopt as T
+    m, w = full["m"], full["w"]
+    u = full.get("u")
+    if u is None:
+        pytest.skip("needs the solve of the previous test")
+    uf = torch.zeros_like(u)
+    tm().tm_expand(ctx(), u, uf)
+    ufn = uf.cpu().numpy()
+    dc = torch.zeros_like(full["rho_d"])
+    comp = tm().tm_sensitivity(ctx(), full["rho_d"], uf, dc)
+    dcn = dc.cpu().numpy()
+    rng = np.random.default_rng(8)
+    sample = rng.choice(m.Ne, size=2000, replace=False)
+    K0 = F.reference_stiffness(w.nu)
+    ue = ufn[F.element_dofs(m)[sample]]
+    en = np.einsum("ei,ij,ej->e", ue, K0, ue)
+    mag = np.einsum("ei,ij,ej->e", np.abs(ue), np.abs(K0), np.abs(ue))
+    rho = full["rho"]
+    pref = w.penal * rho[sample] ** (w.penal - 1) * (w.E0 - w.Emin) * m.h[sample]
+    assert np.all(np.abs(dcn[sample] + pref * en) <= 256 * U64 * pref * mag)
+    # compliance = f^T u
+    f = torch.zeros_like(u)
+    tm().tm_build_rhs(ctx(), w.load_nodes, w.load_comp, w.load_val, f)
+    assert comp == pytest.approx(float(torch.dot(f, u)), rel=1e-6)
+    # filter Eq. 5 on sampled elements, neighbours found by the oracle's kd-tree
+    out = torch.zeros_like(dc)
+    tm().tm_filter(ctx(), full["rho_d"], dc, w.r_min, 0, out)
+    outn = out.cpu().numpy()
+    c = m.centres
+    tree = cKDTree(c)
+    V = m.volume
+    for e in sample[:300]:
+        nb = np.array(tree.query_ball_point(c[e], w.r_min))
+        dist = np.linalg.norm(c[nb] - c[e], axis=1)
+        keep = dist < w.r_min
+        nb, dist = nb[keep], dist[keep]
+        wgt = (w.r_min - dist) * V[nb]
+        ref = np.sum(wgt * rho[nb] * dcn[nb]) / (rho[e] * np.sum(wgt))
+        assert outn[e] == pytest.approx(ref, rel=1e-12, abs=1e-300)
+    # OC at full size: volume closure, bounds, move limit
+    new = torch.zeros_like(dc)
+    tm().tm_oc_update(ctx(), full["rho_d"], out, 0.2, 0.2, 0.5, 1e-3, new)
+    nn = new.cpu().numpy()
+    assert abs(np.sum(nn * V) - 0.2 * V.sum()) <= 1e-10 * V.sum()
+    assert nn.min() >= 1e-3 and nn.max() <= 1.0 and np.all(np.abs(nn - rho) <= 0.2 + 1e-15)

@@ -227,3 +227,20 @@ def test_eq8_unit_diagonal_form_gives_the_same_displacement():
     assert np.abs(uhat[constrained]).max() == 0.0
     u9 = Qfull @ uhat
     assert np.abs(u9 - uf).max() <= 1e-9 * np.abs(uf).max()
+
+
+def test_operator_rows_match_assembled_operator():
+    """The element-by-element row evaluation used for meshes too large to assemble."""
+    w = W.config1b()
+    m = _mesh(w)
+    rho = w.rho[m.perm]
+    A, f, C = F.reduced_system(m, rho, w.load_nodes, w.load_comp, w.load_val)
+    x = np.random.default_rng(0).standard_normal(3 * m.Nn)
+    fn = F.free_nodes(m)
+    y = (A @ F.from_full_layout(m, x)).reshape(-1, 3)
+    rows = F.operator_rows(m, rho, x, fn[::5])
+    assert np.abs(rows - y[::5]).max() <= 1e-14 * np.abs(y).max()
+    absrows = F.operator_rows(m, rho, x, fn[::5], absolute=True)
+    yabs = (abs(A) @ np.abs(F.from_full_layout(m, x))).reshape(-1, 3)
+    assert np.all(absrows >= np.abs(rows) - 1e-15)
+    assert np.all(absrows >= yabs[::5] * (1 - 1e-13))   # |C^T||K||C||x| bounds |A||x|
