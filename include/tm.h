@@ -153,6 +153,11 @@ int tm_tables_build(const tm_mesh_desc *d, tm_tables **out, tm_mesh_info *info, 
 int tm_tables_copy(const tm_tables *t, int64_t *perm, int32_t *node_xyz, int32_t *conn, int32_t *hang_node,
                    int32_t *hang_master, uint8_t *node_flags);
 void tm_tables_free(tm_tables *t);
+/* Host-only form of tm_amr_adapt on built tables (marks and rho on the host, in
+ * the tables' element order); same rules, outputs and errors. */
+int tm_tables_adapt(const tm_tables *t, const int8_t *mark, const double *rho, int64_t capacity,
+                    int32_t *leaves_out, double *rho_out, int64_t *n_out);
+
 
 /* f_dev (A-space) = C^T f_full where f_full holds the given nodal point loads
  * (Eq. 7 right-hand side).  node_xyz: host, 3 per load, must be mesh nodes
@@ -221,6 +226,45 @@ int tm_filter(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double rm
  * *change_out (host, may be NULL) receives max |rho_new - rho|. */
 int tm_oc_update(tm_ctx *ctx, const double *rho_dev, const double *dc_dev, double volfrac, double move,
                  double eta, double rho_min, double *rho_new_dev, double *change_out);
+
+/* Dynamic adaptation, step 1 (Sec. 4): mark_dev (device, Ne int8, element order
+ * of tm_mesh_tables) receives +1 (refine), 0 (keep) or -1 (derefine).
+ * An element is solid when rho_e >= rho_solid; it is marked +1 when it is solid
+ * or the centre of a solid element lies at a distance below r_amr from its
+ * centre, else -1; +1 at the finest level and -1 at level 0 become 0.  Then the
+ * two sweeps of Sec. 4: a -1 survives only when all 8 siblings are leaves
+ * marked -1, and only when every leaf touching the parent box ends, after its
+ * own refinement, at most one level finer than the parent (coarsenings of
+ * neighbours are not counted).  r_amr is limited to 4 finest cells (TM_EINVAL
+ * beyond), like the filter radius.  rho_dev: device, Ne doubles. */
+int tm_amr_mark(tm_ctx *ctx, const double *rho_dev, double rho_solid, double r_amr, int8_t *mark_dev);
+
+/* Dynamic adaptation, step 2 (Sec. 4, with the balancing of Sec. 6): the leaves
+ * of the adapted mesh from marks (device, Ne int8) and densities (device, Ne
+ * doubles).  Elements marked +1 split into 8 children that inherit rho; a
+ * family of 8 siblings all marked -1 merges into its parent, whose rho is the
+ * mean of the 8 (summed in sibling order, x fastest); then leaves are refined
+ * (children inherit rho) until touching leaves differ by at most one level.
+ * Output on the host, in Morton order: leaves_out[4*capacity] as (ix, iy, iz,
+ * level) like tm_mesh_desc, rho_out[capacity]; *n_out receives the leaf count
+ * even when it exceeds capacity (then TM_EINVAL and nothing is written).  Runs
+ * on the host after copying the marks and densities back (synchronises the
+ * stream).  TM_EINVAL for +1 at the finest level, -1 at level 0, or a -1 family
+ * that is not 8 sibling leaves all marked -1. */
+int tm_amr_adapt(tm_ctx *ctx, const int8_t *mark_dev, const double *rho_dev, int64_t capacity,
+                 int32_t *leaves_out, double *rho_out, int64_t *n_out);
+
+/* Design difference of Eq. 10 between the uploaded mesh with rho_dev (device,
+ * Ne doubles) and another design on the same box and maximum level
+ * (leaves_other: host, 4*n_other int32 as in tm_mesh_desc, any order;
+ * rho_other: host, n_other doubles): *d_out (host) = sum_c |rho1_c - rho2_c| /
+ * sum_c rho1_c over the cells c of the finest grid, each cell taking the
+ * density of the leaf covering it (all cells have the same volume).  Allocates
+ * device memory for the other design and a cell map (4 bytes per finest cell)
+ * for the duration of the call and synchronises the stream.  TM_EINVAL when the
+ * other leaves do not tile the box exactly once. */
+int tm_design_difference(tm_ctx *ctx, const double *rho_dev, int64_t n_other, const int32_t *leaves_other,
+                         const double *rho_other, double *d_out);
 
 /* Instrumentation (no counterpart in the paper): tm_profile(ctx, 1) resets the
  * counters and starts timing every operator application with a CUDA-event

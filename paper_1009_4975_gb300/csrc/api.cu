@@ -335,6 +335,7 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
   TM_CUDA(ctx, alloc(wo, WB, &w.scal, (size_t)kScalDoubles));
   TM_CUDA(ctx, alloc(wo, WB, &w.ticket, (size_t)16));
   TM_CUDA(ctx, alloc(wo, WB, &w.status, (size_t)16));
+  TM_CUDA(ctx, alloc(wo, WB, &w.mark_tmp, (size_t)m.Ne));
   TM_CUDA(ctx, alloc(wo, WB, &w.r, nv));
   TM_CUDA(ctx, alloc(wo, WB, &w.p, nv));
   TM_CUDA(ctx, alloc(wo, WB, &w.q, nv));
@@ -470,6 +471,92 @@ int tm_expand(tm_ctx *ctx, const double *u_dev, double *u_full_dev) {
   if (!u_dev || !u_full_dev) return fail(ctx, TM_EINVAL, "null pointer");
   TM_CUDA(ctx, launch_expand(ctx->dm, u_dev, u_full_dev, ctx->stream));
   ctx->launches += ctx->dm.nh > 0 ? 2 : 1;
+  return TM_OK;
+}
+
+int tm_amr_mark(tm_ctx *ctx, const double *rho_dev, double rho_solid, double r_amr, int8_t *mark_dev) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!rho_dev || !mark_dev) return fail(ctx, TM_EINVAL, "null pointer");
+  if (!(r_amr >= 0) || r_amr > 4.0 * ctx->dm.hmin) return fail(ctx, TM_EINVAL, "r_amr must be in [0, 4 h_min]");
+  TM_CUDA(ctx, launch_amr_mark(ctx->dm, rho_dev, rho_solid, r_amr, ctx->w.mark_tmp, mark_dev, ctx->stream));
+  ctx->launches += 3;
+  return TM_OK;
+}
+
+int tm_amr_adapt(tm_ctx *ctx, const int8_t *mark_dev, const double *rho_dev, int64_t capacity, int32_t *leaves_out,
+                 double *rho_out, int64_t *n_out) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!mark_dev || !rho_dev || !n_out) return fail(ctx, TM_EINVAL, "null pointer");
+  const int64_t Ne = ctx->dm.Ne;
+  std::vector<int8_t> mk(Ne);
+  std::vector<double> r(Ne);
+  TM_CUDA(ctx, cudaMemcpyAsync(mk.data(), mark_dev, Ne, cudaMemcpyDeviceToHost, ctx->stream));
+  TM_CUDA(ctx, cudaMemcpyAsync(r.data(), rho_dev, Ne * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  std::vector<int32_t> lv;
+  std::vector<double> rn;
+  std::string msg = adapt_leaves(ctx->host, mk.data(), r.data(), lv, rn);
+  if (!msg.empty()) return fail(ctx, TM_EINVAL, msg);
+  *n_out = (int64_t)rn.size();
+  if ((int64_t)rn.size() > capacity || !leaves_out || !rho_out)
+    return fail(ctx, TM_EINVAL, "capacity " + std::to_string(capacity) + " < " + std::to_string(rn.size()) + " leaves");
+  std::memcpy(leaves_out, lv.data(), lv.size() * sizeof(int32_t));
+  std::memcpy(rho_out, rn.data(), rn.size() * sizeof(double));
+  return TM_OK;
+}
+
+int tm_design_difference(tm_ctx *ctx, const double *rho_dev, int64_t n_other, const int32_t *leaves_other,
+                         const double *rho_other, double *d_out) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!rho_dev || !leaves_other || !rho_other || !d_out || n_other < 1) return fail(ctx, TM_EINVAL, "bad arguments");
+  const HostMesh &h = ctx->host;
+  {
+    // the other design must tile the same box with leaves of levels 0..L, each cell once
+    const int64_t ext[3] = {(int64_t)h.nx << h.L, (int64_t)h.ny << h.L, (int64_t)h.nz << h.L};
+    std::vector<uint8_t> seen((size_t)(ext[0] * ext[1] * ext[2]), 0);
+    int64_t covered = 0;
+    for (int64_t i = 0; i < n_other; ++i) {
+      const int32_t *l = leaves_other + 4 * i;
+      if (l[3] < 0 || l[3] > h.L) return fail(ctx, TM_EINVAL, "other design: leaf level out of range");
+      const int64_t s = (int64_t)1 << (h.L - l[3]);
+      for (int a = 0; a < 3; ++a)
+        if (l[a] < 0 || l[a] + s > ext[a] || l[a] % s) return fail(ctx, TM_EINVAL, "other design: misplaced leaf");
+      for (int64_t z = l[2]; z < l[2] + s; ++z)
+        for (int64_t y = l[1]; y < l[1] + s; ++y)
+          for (int64_t x = l[0]; x < l[0] + s; ++x) {
+            uint8_t &c = seen[(size_t)((z * ext[1] + y) * ext[0] + x)];
+            if (c) return fail(ctx, TM_EINVAL, "other design: overlapping leaves");
+            c = 1;
+          }
+      covered += s * s * s;
+    }
+    if (covered != (int64_t)seen.size()) return fail(ctx, TM_EINVAL, "other design does not cover the box");
+  }
+  const int64_t ncell = (int64_t)ctx->dm.fx * ctx->dm.fy * ctx->dm.fz;
+  int32_t *dl = nullptr, *map2 = nullptr;
+  double *dr = nullptr;
+  cudaError_t e = cudaMalloc(&dl, n_other * 4 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&dr, n_other * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&map2, ncell * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(map2, 0xFF, ncell * sizeof(int32_t), ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dl, leaves_other, n_other * 4 * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dr, rho_other, n_other * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = launch_design_difference(ctx->dm, rho_dev, dl, n_other, dr, map2, ctx->w.red, ctx->w.ticket + 6, scal_at(ctx, 90),
+                                 ctx->stream);
+  double out[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, scal_at(ctx, 90), 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(dl);
+  cudaFree(dr);
+  cudaFree(map2);
+  TM_CUDA(ctx, e);
+  ctx->launches += 2;
+  *d_out = out[0] / out[1];
   return TM_OK;
 }
 

@@ -681,3 +681,125 @@ int tm_tables_copy(const tm_tables *t, int64_t *perm, int32_t *node_xyz, int32_t
 void tm_tables_free(tm_tables *t) { delete t; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- adaptation (paper Sec. 4)
+namespace amr {
+
+// New leaf set from final marks (+1 refine, 0 keep, -1 derefine; canonical order):
+// refined leaves split into 8 children that inherit rho; a family of 8 siblings
+// marked -1 (consecutive in Morton order) merges into its parent with the mean
+// rho; then leaves are refined until every two touching leaves differ by at most
+// one level (children inherit rho).
+std::string adapt_leaves(const HostMesh &m, const int8_t *mark, const double *rho, std::vector<int32_t> &leaves,
+                         std::vector<double> &rho_out) {
+  const int L = m.L;
+  const int64_t fx = (int64_t)m.nx << L, fy = (int64_t)m.ny << L, fz = (int64_t)m.nz << L;
+  leaves.clear();
+  rho_out.clear();
+  for (int64_t e = 0; e < m.Ne; ++e) {
+    const int32_t *l = &m.leaf[4 * e];
+    const int32_t s = 1 << (L - l[3]);
+    if (mark[e] == 1) {
+      if (l[3] >= L) return "refinement mark on a finest-level element";
+      const int32_t h = s / 2;
+      for (int k = 0; k < 8; ++k) {
+        leaves.insert(leaves.end(), {l[0] + h * (k & 1), l[1] + h * ((k >> 1) & 1), l[2] + h * ((k >> 2) & 1), l[3] + 1});
+        rho_out.push_back(rho[e]);
+      }
+    } else if (mark[e] == -1) {
+      if (l[3] == 0) return "derefinement mark on a level-0 element";
+      const int32_t ps = 2 * s;
+      const int k0 = (l[0] % ps ? 1 : 0) + (l[1] % ps ? 2 : 0) + (l[2] % ps ? 4 : 0);
+      if (k0) {   // merged with the family's first sibling, which must carry the same mark
+        const int32_t *f = e >= k0 ? &m.leaf[4 * (e - k0)] : nullptr;
+        if (!f || f[3] != l[3] || f[0] != l[0] - s * (k0 & 1) || f[1] != l[1] - s * ((k0 >> 1) & 1) ||
+            f[2] != l[2] - s * ((k0 >> 2) & 1) || mark[e - k0] != -1)
+          return "family marked for derefinement is not 8 sibling leaves";
+        continue;
+      }
+      if (e + 8 > m.Ne) return "incomplete family marked for derefinement";
+      double sum = 0.0;
+      for (int k = 0; k < 8; ++k) {
+        const int32_t *q = &m.leaf[4 * (e + k)];
+        if (mark[e + k] != -1 || q[3] != l[3] || q[0] != l[0] + s * (k & 1) || q[1] != l[1] + s * ((k >> 1) & 1) ||
+            q[2] != l[2] + s * ((k >> 2) & 1))
+          return "family marked for derefinement is not 8 sibling leaves";
+        sum += rho[e + k];
+      }
+      leaves.insert(leaves.end(), {l[0], l[1], l[2], l[3] - 1});
+      rho_out.push_back(sum / 8.0);
+    } else {
+      leaves.insert(leaves.end(), {l[0], l[1], l[2], l[3]});
+      rho_out.push_back(rho[e]);
+    }
+  }
+  // 2:1 balance by refinement
+  std::vector<uint8_t> lv((size_t)(fx * fy * fz));
+  for (int pass = 0; pass < 64; ++pass) {
+    const int64_t n = (int64_t)rho_out.size();
+    for (int64_t i = 0; i < n; ++i) {
+      const int32_t *l = &leaves[4 * i];
+      const int32_t s = 1 << (L - l[3]);
+      for (int z = 0; z < s; ++z)
+        for (int y = 0; y < s; ++y)
+          std::memset(&lv[((size_t)(l[2] + z) * fy + (l[1] + y)) * fx + l[0]], l[3], s);
+    }
+    std::vector<char> need(n, 0);
+    bool any = false;
+    for (int64_t i = 0; i < n; ++i) {
+      const int32_t *l = &leaves[4 * i];
+      const int32_t s = 1 << (L - l[3]);
+      int mx = 0;
+      for (int64_t z = std::max<int64_t>(l[2] - 1, 0); z < std::min<int64_t>(l[2] + s + 1, fz); ++z)
+        for (int64_t y = std::max<int64_t>(l[1] - 1, 0); y < std::min<int64_t>(l[1] + s + 1, fy); ++y)
+          for (int64_t x = std::max<int64_t>(l[0] - 1, 0); x < std::min<int64_t>(l[0] + s + 1, fx); ++x) {
+            const bool inside = x >= l[0] && x < l[0] + s && y >= l[1] && y < l[1] + s && z >= l[2] && z < l[2] + s;
+            if (!inside) mx = std::max<int>(mx, lv[((size_t)z * fy + y) * fx + x]);
+          }
+      if (mx > l[3] + 1) {
+        need[i] = 1;
+        any = true;
+      }
+    }
+    if (!any) return "";
+    std::vector<int32_t> nl;
+    std::vector<double> nr;
+    nl.reserve(leaves.size());
+    nr.reserve(rho_out.size());
+    for (int64_t i = 0; i < n; ++i) {
+      const int32_t *l = &leaves[4 * i];
+      if (!need[i]) {
+        nl.insert(nl.end(), l, l + 4);
+        nr.push_back(rho_out[i]);
+        continue;
+      }
+      const int32_t h = (1 << (L - l[3])) / 2;
+      for (int k = 0; k < 8; ++k) {
+        nl.insert(nl.end(), {l[0] + h * (k & 1), l[1] + h * ((k >> 1) & 1), l[2] + h * ((k >> 2) & 1), l[3] + 1});
+        nr.push_back(rho_out[i]);
+      }
+    }
+    leaves.swap(nl);
+    rho_out.swap(nr);
+  }
+  return "2:1 balancing did not settle";
+}
+
+}  // namespace amr
+
+extern "C" {
+
+int tm_tables_adapt(const tm_tables *t, const int8_t *mark, const double *rho, int64_t capacity,
+                    int32_t *leaves_out, double *rho_out, int64_t *n_out) {
+  if (!t || !mark || !rho || !n_out) return TM_EINVAL;
+  std::vector<int32_t> lv;
+  std::vector<double> r;
+  if (!amr::adapt_leaves(t->m, mark, rho, lv, r).empty()) return TM_EINVAL;
+  *n_out = (int64_t)r.size();
+  if ((int64_t)r.size() > capacity || !leaves_out || !rho_out) return TM_EINVAL;
+  std::memcpy(leaves_out, lv.data(), lv.size() * sizeof(int32_t));
+  std::memcpy(rho_out, r.data(), r.size() * sizeof(double));
+  return TM_OK;
+}
+
+}  // extern "C"

@@ -79,6 +79,8 @@ struct HostMesh {
 
 // Returns "" on success or an error message.
 std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m);
+std::string adapt_leaves(const HostMesh &m, const int8_t *mark, const double *rho, std::vector<int32_t> &leaves,
+                         std::vector<double> &rho_out);
 void reference_stiffness(double nu, double *K0 /* 576 */);
 uint64_t morton3(uint32_t x, uint32_t y, uint32_t z);
 
@@ -134,6 +136,7 @@ struct Work {
   double *scal = nullptr;      // device scalars
   unsigned int *ticket = nullptr;  // last-block counters
   int *status = nullptr;       // device status word
+  int8_t *mark_tmp = nullptr;  // Ne, intermediate adaptation marks
   // solver vectors (3 * Nn)
   double *r = nullptr, *p = nullptr, *q = nullptr, *dinv = nullptr, *d = nullptr;
   float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *dinv32 = nullptr, *x32 = nullptr;
@@ -205,4 +208,10 @@ constexpr int64_t kStaticSlots = int64_t(1) << 21;   // shared-node partials: up
 constexpr int kStaticMaxDevices = 64;
 cudaError_t static_scratch(int device, float **ce, float **part);
 cudaError_t launch_coeff_f32(const DeviceMesh &m, const double *rho, float *ce32, cudaStream_t s);
+// adaptation (kernels_amr.cu)
+cudaError_t launch_amr_mark(const DeviceMesh &m, const double *rho, double rho_solid, double r_amr, int8_t *tmp,
+                            int8_t *mark, cudaStream_t s);
+cudaError_t launch_design_difference(const DeviceMesh &m, const double *rho1, const int32_t *leaves2, int64_t n2,
+                                     const double *rho2, int32_t *map2, double *partials, unsigned int *ticket,
+                                     double *out, cudaStream_t s);
 }  // namespace amr

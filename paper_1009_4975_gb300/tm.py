@@ -58,7 +58,8 @@ class tm_profile_data(C.Structure):
 
 EXPORTS = ["tm_create", "tm_destroy", "tm_set_stream", "tm_last_error", "tm_mesh_upload", "tm_mesh_tables",
            "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_apply_K_f32_static", "tm_jacobi_diag", "tm_pcg_solve", "tm_expand",
-           "tm_sensitivity", "tm_filter", "tm_oc_update", "tm_profile", "tm_profile_read"]
+           "tm_sensitivity", "tm_filter", "tm_oc_update", "tm_amr_mark", "tm_amr_adapt", "tm_design_difference",
+           "tm_tables_adapt", "tm_profile", "tm_profile_read"]
 
 _lib = None
 
@@ -88,6 +89,10 @@ def load_library(path: str = LIB_PATH):
         "tm_sensitivity": [vp, vp, vp, vp, C.POINTER(dbl)],
         "tm_filter": [vp, vp, vp, dbl, C.c_int, vp],
         "tm_oc_update": [vp, vp, vp, dbl, dbl, dbl, dbl, vp, C.POINTER(dbl)],
+        "tm_amr_mark": [vp, vp, dbl, dbl, vp],
+        "tm_amr_adapt": [vp, vp, vp, i64, vp, vp, C.POINTER(i64)],
+        "tm_design_difference": [vp, vp, i64, vp, vp, C.POINTER(dbl)],
+        "tm_tables_adapt": [vp, vp, vp, i64, vp, vp, C.POINTER(i64)],
         "tm_profile": [vp, C.c_int],
         "tm_profile_read": [vp, C.POINTER(tm_profile_data)],
     }
@@ -301,6 +306,75 @@ def tm_oc_update(ctx: Ctx, rho, dc, volfrac, move, eta, rho_min, rho_new) -> flo
     ctx.check(load_library().tm_oc_update(ctx.handle, _elem(ctx, rho, "rho"), _elem(ctx, dc, "dc"), volfrac, move,
                                           eta, rho_min, _elem(ctx, rho_new, "rho_new"), C.byref(ch)))
     return ch.value
+
+
+def tm_amr_mark(ctx: Ctx, rho, rho_solid: float, r_amr: float, mark):
+    """Adaptation marks (+1 / 0 / -1, int8 CUDA tensor of Ne) after both sweeps; see include/tm.h."""
+    import torch
+    ctx.check(load_library().tm_amr_mark(ctx.handle, _elem(ctx, rho, "rho"), rho_solid, r_amr,
+                                         _ptr(mark, torch.int8, ctx.info["Ne"], "mark")))
+
+
+def _adapt_call(fn, ne, handle, mark_p, rho_p, raise_err):
+    cap = 8 * ne + 64
+    for _ in range(2):
+        lv = np.empty((cap, 4), np.int32)
+        r = np.empty(cap, np.float64)
+        n = C.c_int64(0)
+        rc = fn(handle, mark_p, rho_p, cap, C.c_void_p(lv.ctypes.data), C.c_void_p(r.ctypes.data), C.byref(n))
+        if rc == TM_OK:
+            return lv[:n.value].copy(), r[:n.value].copy()
+        if n.value <= cap:
+            raise_err(rc)
+        cap = n.value
+    raise_err(rc)
+
+
+def tm_amr_adapt(ctx: Ctx, mark, rho):
+    """(leaves int32 (n, 4), rho float64 (n,)) of the adapted mesh, on the host."""
+    import torch
+    ne = ctx.info["Ne"]
+    return _adapt_call(load_library().tm_amr_adapt, ne, ctx.handle, _ptr(mark, torch.int8, ne, "mark"),
+                       _elem(ctx, rho, "rho"), ctx.check)
+
+
+def tm_design_difference(ctx: Ctx, rho, leaves_other, rho_other) -> float:
+    """Eq. 10 between the uploaded design and another one given on the host."""
+    lv = np.ascontiguousarray(np.asarray(leaves_other, np.int32).reshape(-1, 4))
+    ro = np.ascontiguousarray(np.asarray(rho_other, np.float64).ravel())
+    if ro.size != lv.shape[0]:
+        raise ValueError("rho_other must have one value per leaf")
+    d = C.c_double()
+    ctx.check(load_library().tm_design_difference(ctx.handle, _elem(ctx, rho, "rho"), lv.shape[0],
+                                                  C.c_void_p(lv.ctypes.data), C.c_void_p(ro.ctypes.data),
+                                                  C.byref(d)))
+    return d.value
+
+
+def tm_tables_adapt(nx, ny, nz, max_level, h0, leaves, mark, rho):
+    """Host-only adaptation (tm_tables_adapt): marks and rho in the tables' (Morton) element order."""
+    lib = load_library()
+    lv = np.ascontiguousarray(np.asarray(leaves, np.int32).reshape(-1, 4))
+    d = tm_mesh_desc(nx, ny, nz, max_level, h0, lv.shape[0], lv.ctypes.data_as(C.POINTER(C.c_int32)), 1, 1.0,
+                     1e-9, 0.3, 3.0)
+    info = tm_mesh_info()
+    h = C.c_void_p()
+    err = C.create_string_buffer(512)
+    rc = lib.tm_tables_build(C.byref(d), C.byref(h), C.byref(info), err, 512)
+    if rc != TM_OK:
+        raise TmError(rc, err.value.decode())
+    try:
+        mk = np.ascontiguousarray(np.asarray(mark, np.int8).ravel())
+        r = np.ascontiguousarray(np.asarray(rho, np.float64).ravel())
+        if mk.size != info.Ne or r.size != info.Ne:
+            raise ValueError("mark and rho must have Ne entries")
+
+        def raise_err(code):
+            raise TmError(code, "tm_tables_adapt rejected the marks")
+        return _adapt_call(lib.tm_tables_adapt, info.Ne, h, C.c_void_p(mk.ctypes.data), C.c_void_p(r.ctypes.data),
+                           raise_err)
+    finally:
+        lib.tm_tables_free(h)
 
 
 def tm_profile(ctx: Ctx, enable: bool = True):

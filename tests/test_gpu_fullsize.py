@@ -144,3 +144,46 @@ def test_fullsize_sensitivity_filter_oc_samples(full):
     nn = new.cpu().numpy()
     assert abs(np.sum(nn * V) - 0.2 * V.sum()) <= 1e-10 * V.sum()
     assert nn.min() >= 1e-3 and nn.max() <= 1.0 and np.all(np.abs(nn - rho) <= 0.2 + 1e-15)
+
+
+def test_fullsize_amr_marks_sampled_and_adapted_mesh_valid(full):
+    """The ~2M-element mesh with a moved design: every GPU mark on a sample of elements is
+    re-derived one by one from the oracle's predicates; the adapted mesh tiles the box, is
+    2:1 balanced and keeps the integral of rho; D against the oracle on the finest grid."""
+    import torch
+    import workloads as W
+    from oracle import amr as A
+    from oracle import mesh as M
+    w, m = full["w"], full["m"]
+    d = w.dom
+    phi = W.truss_sdf(m.centres, 11, r0=0.06)
+    rho = np.clip(0.5 - phi / (2.0 * d.h_min), 1e-3, 1.0)
+    r_amr = 2.0 * d.h_min
+    rho_d = torch.as_tensor(rho, device="cuda:0")
+    mk = torch.empty(m.Ne, dtype=torch.int8, device="cuda:0")
+    tm().tm_amr_mark(ctx(), rho_d, 0.5, r_amr, mk)
+    got = mk.cpu().numpy()
+    raw = A.mark(m, rho, 0.5, r_amr)
+    assert (got == 1).sum() > 0 and (got == -1).sum() > 0
+    index = A.leaf_index(m)
+    owner = M.leaf_owner_map(d.nx, d.ny, d.nz, d.L, m.leaves)
+    rng = np.random.default_rng(5)
+    sample = np.unique(np.concatenate([rng.choice(m.Ne, 3000, replace=False),
+                                       rng.choice(np.nonzero(raw == -1)[0], 3000, replace=False)]))
+    for e in sample:
+        want = int(raw[e])
+        if want == -1 and not (A.family_marked(m, index, raw, int(e)) and A.parent_compatible(m, owner, raw, int(e))):
+            want = 0
+        assert got[e] == want, (int(e), int(got[e]), want)
+    # every +1 and 0 agrees with the unswept marks everywhere; sweeps only turn -1 into 0
+    assert np.array_equal(got == 1, raw == 1)
+    assert not ((got == -1) & (raw != -1)).any()
+    gl, gr = tm().tm_amr_adapt(ctx(), mk, rho_d)
+    M.check_leaves(d.nx, d.ny, d.nz, d.L, gl)
+    M.check_balance(d.nx, d.ny, d.nz, d.L, gl)
+    v1 = (1 << (d.L - m.leaves[:, 3])).astype(np.float64) ** 3
+    v2 = (1 << (d.L - gl[:, 3])).astype(np.float64) ** 3
+    assert np.sum(gr * v2) == pytest.approx(np.sum(rho * v1), rel=1e-12)
+    got_d = tm().tm_design_difference(ctx(), rho_d, gl, gr)
+    want_d = A.design_difference(d.nx, d.ny, d.nz, d.L, m.leaves, rho, gl, gr)
+    assert got_d == pytest.approx(want_d, rel=1e-11, abs=1e-15)
