@@ -274,6 +274,7 @@ def run_gpu(args):
 
     if rank != 0:
         return
+    adapt = adaptation_timing(P, ctx, cur, d, Ne, dev)
     peak, peak_kind = _peaks()
     a_ms = prof["apply32_ms"] / max(prof["apply32_count"], 1)
     algo = ALGO_BYTES_PER_ELEM_F32 * Ne
@@ -294,6 +295,7 @@ def run_gpu(args):
         "compliance": comps,
         "mesh_upload_s": mesh_s,
         "fp64_pcg": fp64,
+        "adaptation": adapt,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "roofline": {"bound": "hbm", "kernel": "apply_blocks_kernel<float> (operator block pass; the partial "
@@ -307,6 +309,35 @@ def run_gpu(args):
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
+
+
+def adaptation_timing(P, ctx, rho, d, Ne, dev):
+    """Adaptation step on the benchmark mesh after the timed region (not part of a step): marks
+    and both sweeps on the device (CUDA events), the new leaf set on the host, and Eq. 10 between
+    the two designs."""
+    import torch
+    r_amr = 2.0 * d.h0 / (1 << d.L)
+    mk = torch.empty(Ne, dtype=torch.int8, device=dev)
+    P.tm_amr_mark(ctx, rho, 0.5, r_amr, mk)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    reps = 5
+    for _ in range(reps):
+        P.tm_amr_mark(ctx, rho, 0.5, r_amr, mk)
+    e1.record()
+    torch.cuda.synchronize()
+    mark_ms = e0.elapsed_time(e1) / reps
+    counts = torch.bincount((mk.to(torch.int64) + 1), minlength=3).tolist()
+    t0 = time.perf_counter()
+    leaves, rho2 = P.tm_amr_adapt(ctx, mk, rho)
+    adapt_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    dd = P.tm_design_difference(ctx, rho, leaves, rho2)
+    dd_s = time.perf_counter() - t0
+    return {"rho_solid": 0.5, "r_amr": r_amr, "marks": {"derefine": counts[0], "keep": counts[1],
+            "refine": counts[2]}, "mark_and_sweeps_ms": mark_ms, "adapt_host_s": adapt_s,
+            "new_elements": int(leaves.shape[0]), "design_difference": dd, "design_difference_s": dd_s}
 
 
 def run_profile_apply(args):

@@ -5,11 +5,13 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 Readings (the paper states the rules in words only):
 
 * Marking (Sec. 4, step 1): element e is *solid* when rho_e >= rho_s.  It is marked
-  for refinement (+1) when it is solid or some solid element lies within distance
-  r_AMR (distance between element centres, as for the filter); otherwise it is void
-  with no solid element within r_AMR and is marked for derefinement (-1).  An
+  for refinement (+1) when it is solid or some solid element lies at a distance
+  below r_AMR (distance between element centres, as for the filter); otherwise it
+  is void with no solid element that close and is marked for derefinement (-1).  An
   element at the finest level cannot be refined (0), one at level 0 cannot be
-  derefined (0).
+  derefined (0).  The distance test is exact: centres in half finest-cell units are
+  integers, and dist < r is taken as d2 < (2 r / unit)^2 with d2 their integer
+  squared distance (centres exactly r apart are common, e.g. r = 2 finest cells).
 * Sweep 1: a -1 mark survives only if all 8 siblings (the children of the same
   parent) are leaves marked -1.
 * Sweep 2: a -1 mark survives only if the coarsened parent (level l-1) would differ
@@ -33,36 +35,51 @@ from scipy.spatial import cKDTree
 from .mesh import Mesh, leaf_owner_map
 
 
-def mark(mesh: Mesh, rho, rho_solid: float, r_amr: float) -> np.ndarray:
-    rho = np.asarray(rho, np.float64)
-    solid = rho >= rho_solid
-    c = mesh.centres
-    near = np.zeros(mesh.Ne, bool)
-    if solid.any():
-        tree = cKDTree(c[solid])
-        d, _ = tree.query(c, k=1)
-        near = d < r_amr
-    m = np.where(solid | near, 1, -1).astype(np.int8)
+def _half_cell_centres(mesh: Mesh) -> np.ndarray:
+    """Element centres in units of half a finest cell: exact integers 2 * anchor + size."""
+    return 2 * mesh.leaves[:, :3].astype(np.int64) + mesh.size[:, None]
+
+
+def _threshold(mesh: Mesh, r_amr: float) -> float:
+    """(2 r / unit)^2: 'distance below r' is 'squared half-cell distance below this'."""
+    t = 2.0 * r_amr / (mesh.h0 / (1 << mesh.L))
+    return t * t
+
+
+def _finish(mesh: Mesh, refine) -> np.ndarray:
+    m = np.where(refine, 1, -1).astype(np.int8)
     lvl = mesh.leaves[:, 3]
     m[(m == 1) & (lvl >= mesh.L)] = 0
     m[(m == -1) & (lvl == 0)] = 0
     return m
 
 
+def mark(mesh: Mesh, rho, rho_solid: float, r_amr: float) -> np.ndarray:
+    rho = np.asarray(rho, np.float64)
+    solid = rho >= rho_solid
+    c2 = _half_cell_centres(mesh)
+    near = np.zeros(mesh.Ne, bool)
+    if solid.any():
+        # nearest solid centre (exact: integer coordinates), then the exact squared distance
+        tree = cKDTree(c2[solid].astype(np.float64))
+        _, j = tree.query(c2.astype(np.float64), k=1)
+        diff = c2 - c2[solid][j]
+        near = (diff * diff).sum(axis=1).astype(np.float64) < _threshold(mesh, r_amr)
+    return _finish(mesh, solid | near)
+
+
 def mark_bruteforce(mesh: Mesh, rho, rho_solid: float, r_amr: float) -> np.ndarray:
-    c = mesh.centres
-    out = np.zeros(mesh.Ne, np.int8)
+    c2 = _half_cell_centres(mesh)
+    thr = _threshold(mesh, r_amr)
+    refine = np.zeros(mesh.Ne, bool)
     for e in range(mesh.Ne):
-        refine = rho[e] >= rho_solid
+        refine[e] = rho[e] >= rho_solid
         for d in range(mesh.Ne):
-            if rho[d] >= rho_solid and np.sqrt(np.sum((c[e] - c[d]) ** 2)) < r_amr:
-                refine = True
-        lvl = mesh.leaves[e, 3]
-        if refine:
-            out[e] = 1 if lvl < mesh.L else 0
-        else:
-            out[e] = -1 if lvl > 0 else 0
-    return out
+            if rho[d] >= rho_solid:
+                dd = [int(c2[e, a] - c2[d, a]) for a in range(3)]
+                if float(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]) < thr:
+                    refine[e] = True
+    return _finish(mesh, refine)
 
 
 def _parent(leaf, L):

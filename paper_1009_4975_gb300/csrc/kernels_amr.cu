@@ -4,8 +4,8 @@
 //
 // Marks: +1 refine, 0 keep, -1 derefine.
 //  * mark: element e is solid when rho_e >= rho_s; it is marked +1 when it is
-//    solid or the centre of some solid element lies within r_AMR of its centre,
-//    else -1.  Finest-level elements cannot refine and level-0 elements cannot
+//    solid or the centre of some solid element lies at a distance below r_AMR from
+//    its centre (compared exactly, see amr_mark_kernel), else -1.  Finest-level elements cannot refine and level-0 elements cannot
 //    derefine (0).  Solid neighbours are found through the finest-cell map over
 //    the box [c - r_AMR, c + r_AMR], stopping at the first one.
 //  * sibling sweep: a -1 survives only when all 8 children of its parent are
@@ -28,23 +28,26 @@ __device__ __forceinline__ int cell_owner(const int32_t *cellmap, int fx, int fy
   return cellmap[((size_t)z * fy + y) * fx + x];
 }
 
+// Distances are compared exactly: centres in half finest-cell units are integers
+// (2 * anchor + size), so the squared distance d2 is an exact integer, and "distance
+// below r_AMR" is d2 < thr with thr = (2 r_AMR / unit)^2 (computed once in FP64).
 __global__ void __launch_bounds__(kAmrThreads) amr_mark_kernel(const int32_t *leaf, const int32_t *cellmap, int fx,
-                                                               int fy, int fz, int L, double unit, const double *rho,
-                                                               double rho_solid, double r_amr, int64_t Ne,
+                                                               int fy, int fz, int L, double ru, double thr,
+                                                               const double *rho, double rho_solid, int64_t Ne,
                                                                int8_t *mark) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < Ne; e += (int64_t)gridDim.x * blockDim.x) {
     const int *le = leaf + 4 * e;
     const int se = 1 << (L - le[3]);
     bool refine = rho[e] >= rho_solid;
     if (!refine) {
-      const double c[3] = {le[0] + 0.5 * se, le[1] + 0.5 * se, le[2] + 0.5 * se};
-      const double ru = r_amr / unit;
+      const int c2[3] = {2 * le[0] + se, 2 * le[1] + se, 2 * le[2] + se};
       const int ext[3] = {fx, fy, fz};
       int lo[3], hi[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        lo[a] = (int)floor(c[a] - ru);
-        hi[a] = (int)ceil(c[a] + ru) - 1;
+        // cells that can hold the centre of an element closer than r_AMR, one cell of margin
+        lo[a] = (int)floor(0.5 * c2[a] - ru) - 1;
+        hi[a] = (int)ceil(0.5 * c2[a] + ru);
         if (lo[a] < 0) lo[a] = 0;
         if (hi[a] > ext[a] - 1) hi[a] = ext[a] - 1;
       }
@@ -55,9 +58,8 @@ __global__ void __launch_bounds__(kAmrThreads) amr_mark_kernel(const int32_t *le
             if (!(rho[d] >= rho_solid)) continue;
             const int *ld = leaf + 4 * d;
             const int sd = 1 << (L - ld[3]);
-            const double dx = (ld[0] + 0.5 * sd - c[0]) * unit, dy = (ld[1] + 0.5 * sd - c[1]) * unit,
-                         dz = (ld[2] + 0.5 * sd - c[2]) * unit;
-            if (sqrt(dx * dx + dy * dy + dz * dz) < r_amr) refine = true;
+            const long long dx = 2 * ld[0] + sd - c2[0], dy = 2 * ld[1] + sd - c2[1], dz = 2 * ld[2] + sd - c2[2];
+            if ((double)(dx * dx + dy * dy + dz * dz) < thr) refine = true;
           }
     }
     int8_t m = refine ? 1 : -1;
@@ -125,8 +127,9 @@ int amr_grid(int64_t n) {
 cudaError_t launch_amr_mark(const DeviceMesh &m, const double *rho, double rho_solid, double r_amr, int8_t *tmp,
                             int8_t *mark, cudaStream_t s) {
   const int g = amr_grid(m.Ne);
-  amr_mark_kernel<<<g, kAmrThreads, 0, s>>>(m.leaf, m.cellmap, m.fx, m.fy, m.fz, m.L, m.hmin, rho, rho_solid, r_amr,
-                                            m.Ne, mark);
+  const double t = 2.0 * r_amr / m.hmin;
+  amr_mark_kernel<<<g, kAmrThreads, 0, s>>>(m.leaf, m.cellmap, m.fx, m.fy, m.fz, m.L, r_amr / m.hmin, t * t, rho,
+                                            rho_solid, m.Ne, mark);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   amr_sweep_siblings_kernel<<<g, kAmrThreads, 0, s>>>(m.leaf, m.cellmap, m.fx, m.fy, m.L, mark, m.Ne, tmp);

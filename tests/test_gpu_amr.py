@@ -22,7 +22,8 @@ def _upload(w):
                                w.penal)
 
 
-@pytest.mark.parametrize("seed,r_cells,rho_s", [(1, 1.6, 0.5), (2, 1.3, 0.5), (4, 3.7, 0.3), (1, 0.0, 0.5)])
+@pytest.mark.parametrize("seed,r_cells,rho_s", [(1, 1.6, 0.5), (2, 1.3, 0.5), (4, 3.7, 0.3), (1, 0.0, 0.5),
+                                               (2, 2.0, 0.5), (4, 1.0, 0.5), (1, 4.0, 0.5)])
 def test_marks_and_adapted_mesh_bit_exact(seed, r_cells, rho_s):
     import torch
     w = W.config1b(seed)

@@ -42,6 +42,10 @@ def test_hand_case_refine_and_balance():
             assert v == 0
         else:
             assert v == (1 if a in want_plus else -1), (a, v)
+    # centres exactly r apart are not below r: at r = 0.5 only the solid child refines
+    tie = _by_anchor(m, A.mark(m, rho, 0.5, 0.5))
+    assert [v for (a, lvl), v in tie.items() if lvl == 1].count(1) == 1
+    assert tie[((0, 0, 0), 1)] == 1 and tie[((2, 0, 0), 1)] == -1
     fin = A.final_marks(m, rho, 0.5, 0.6)
     for (a, lvl), v in _by_anchor(m, fin).items():
         assert v == (1 if lvl == 1 and a in want_plus else 0)
@@ -120,7 +124,7 @@ def _moved_design(w, m, seed):
     return np.clip(0.5 - phi / (2.0 * w.dom.h_min), 1e-3, 1.0)
 
 
-@pytest.mark.parametrize("seed,r_cells", [(1, 1.3), (3, 2.2), (5, 3.7)])
+@pytest.mark.parametrize("seed,r_cells", [(1, 1.3), (3, 2.0), (5, 3.7), (2, 1.0)])
 def test_mark_matches_bruteforce(seed, r_cells):
     w = W.config1b(seed)
     m = _mesh(w.dom, w.leaves)
