@@ -274,6 +274,7 @@ def run_gpu(args):
 
     if rank != 0:
         return
+    precision = precision_report(P, ctx, rho_first, f, u_first, u64)
     adapt = adaptation_timing(P, ctx, cur, d, Ne, dev)
     peak, peak_kind = _peaks()
     a_ms = prof["apply32_ms"] / max(prof["apply32_count"], 1)
@@ -295,6 +296,7 @@ def run_gpu(args):
         "compliance": comps,
         "mesh_upload_s": mesh_s,
         "fp64_pcg": fp64,
+        "precision": precision,
         "adaptation": adapt,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
@@ -309,6 +311,40 @@ def run_gpu(args):
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
+
+
+def precision_report(P, ctx, rho, f, u0, u64):
+    """Errors of the mixed and FP64 solvers at the bench tolerance (1e-8) on the first timed
+    system, against a solve of the same system to 1e-12 (FP64 residual): energy-norm error of u
+    (FP64 operator), relative compliance error, sensitivity error relative to max |dc|."""
+    import torch
+    ref = u0.clone()
+    st_ref = P.tm_pcg_solve(ctx, rho, f, ref, rtol=1e-12, max_iter=400000, precision=P.TM_PREC_MIXED,
+                            raise_on_error=False)
+    um = u0.clone()
+    P.tm_pcg_solve(ctx, rho, f, um, rtol=1e-8, max_iter=200000, precision=P.TM_PREC_MIXED)
+    uf = torch.zeros_like(f)
+    dc = torch.zeros_like(rho)
+
+    def fields(u):
+        P.tm_expand(ctx, u, uf)
+        c = P.tm_sensitivity(ctx, rho, uf, dc)
+        return c, dc.clone()
+
+    c_ref, dc_ref = fields(ref)
+    au = torch.zeros_like(f)
+    P.tm_apply_K(ctx, rho, ref, au)
+    e_ref = float(torch.dot(ref, au))
+    out = {"reference": "mixed solve of the same system to rel. residual 1e-12",
+           "reference_rel_residual": st_ref["rel_residual"]}
+    for name, u in (("mixed_1e-8", um), ("fp64_1e-8", u64)):
+        c, dcu = fields(u)
+        e = u - ref
+        P.tm_apply_K(ctx, rho, e, au)
+        out[name] = {"u_energy_rel_err": abs(float(torch.dot(e, au))) ** 0.5 / e_ref ** 0.5 if e_ref > 0 else None,
+                     "compliance_rel_err": abs(c - c_ref) / abs(c_ref),
+                     "dc_err_rel_max": float((dcu - dc_ref).abs().max() / dc_ref.abs().max())}
+    return out
 
 
 def adaptation_timing(P, ctx, rho, d, Ne, dev):

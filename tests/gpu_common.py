@@ -43,6 +43,13 @@ class Case:
         self.fn = F.free_nodes(self.m)
         self.dev = torch.device("cuda:0")
 
+    def direct(self):
+        """The oracle's direct solution of the reduced system, computed once per case."""
+        if getattr(self, "_ud", None) is None:
+            from oracle import solve as S
+            self._ud = S.direct(self.A, self.f)
+        return self._ud
+
     def upload(self):
         w, d = self.w, self.w.dom
         info = tm().tm_mesh_upload(ctx(), d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, w.dirichlet_faces, w.E0, w.Emin,

@@ -3,8 +3,8 @@
 Tolerances (stated per test) follow from the arithmetic:
 * integer tables: bit-exact;
 * operator: the library evaluates each entry of A x in a different order than the
-  oracle's assembled CSR (sum factorisation over Gauss points, colour order,
-  slot sums), so entry i may differ by a small multiple of the unit roundoff u
+  oracle's assembled CSR (symmetry-adapted element product, per-node slot sums,
+  partial sums of block-shared nodes), so entry i may differ by a small multiple of the unit roundoff u
   times (|A| |x|)_i, the standard bound for a reordered sum of products; the
   multiple 256 covers the ~60 operations on any path through the element
   kernel and the <= 16 contributions per node;
@@ -140,8 +140,7 @@ def test_pcg_residual_in_oracle_operator(up, precision):
 def test_pcg_solution_and_compliance_against_direct(up, precision):
     """Tight solve (1e-12): u within 1e-8 of the oracle's direct solution in the energy
     norm, and compliance within 1e-8."""
-    from oracle import solve as S
-    ud = S.direct(up.A, up.f)
+    ud = up.direct()
     u, st = _solve(up, precision, 1e-12)
     e = u - ud
     energy_err = np.sqrt(abs(e @ (up.A @ e))) / np.sqrt(ud @ (up.A @ ud))
@@ -153,8 +152,7 @@ def test_pcg_solution_and_compliance_against_direct(up, precision):
 def test_sensitivity_and_compliance(up):
     import torch
     from oracle import topopt as T
-    from oracle import solve as S
-    ud = S.direct(up.A, up.f)
+    ud = up.direct()
     uf = up.C @ ud
     w = up.w
     ref = T.sensitivity(up.m, up.rho, uf, w.E0, w.Emin, w.nu, w.penal)

@@ -1,0 +1,74 @@
+"""Accuracy of the solver precisions along an optimisation run (design snapshots after 0, 30
+and 60 OC iterations), against the oracle's direct solution of each snapshot's system.
+
+Both solvers stop at ||f - A u|| / ||f|| <= 1e-8.  Measured against the direct solution:
+the energy-norm error of u, the relative error of the compliance c = f^T u and the error of
+the sensitivities dc relative to max |dc|.  FP64 Jacobi-PCG at this tolerance shows errors of
+about 1e-9 (u, dc) and 1e-12 (c) on these meshes; the bounds below are 100x to 1000x that, and
+the mixed solver (FP32 operator and vectors inside FP64 refinement) must meet the same bounds
+as the FP64 solver."""
+import numpy as np
+import pytest
+
+from tests.gpu_common import case, ctx, tm
+
+pytestmark = pytest.mark.gpu
+
+SNAPSHOTS = (0, 30, 60)
+
+
+def _errors(c, rho, u_free, dc_gpu, comp_gpu):
+    from oracle import fem as F
+    from oracle import solve as S
+    from oracle import topopt as T
+    w = c.w
+    A, f, C = F.reduced_system(c.m, rho, w.load_nodes, w.load_comp, w.load_val, w.E0, w.Emin, w.nu, w.penal)
+    us = S.direct(A, f)
+    e = u_free - us
+    eu = float(np.sqrt(abs(e @ (A @ e)) / (us @ (A @ us))))
+    cs = float(f @ us)
+    ec = abs(comp_gpu - cs) / cs
+    dcs = T.sensitivity(c.m, rho, C @ us, w.E0, w.Emin, w.nu, w.penal)
+    edc = float(np.abs(dc_gpu - dcs).max() / np.abs(dcs).max())
+    return eu, ec, edc
+
+
+def test_precisions_along_an_optimisation_run():
+    import torch
+    P = tm()
+    c = case("config1b")
+    c.upload()
+    w = c.w
+    n3 = 3 * c.m.Nn
+    f = torch.zeros(n3, dtype=torch.float64, device=c.dev)
+    P.tm_build_rhs(ctx(), w.load_nodes, w.load_comp, w.load_val, f)
+    rho = c.t(c.rho)
+    u = torch.zeros_like(f)
+    uf = torch.zeros_like(f)
+    dc = torch.zeros_like(rho)
+    dch = torch.zeros_like(rho)
+    new = torch.zeros_like(rho)
+    report = []
+    for it in range(SNAPSHOTS[-1] + 1):
+        if it in SNAPSHOTS:
+            rho_h = rho.cpu().numpy()
+            for prec in (P.TM_PREC_FP64, P.TM_PREC_MIXED):
+                us = torch.zeros_like(f)
+                st = P.tm_pcg_solve(ctx(), rho, f, us, rtol=1e-8, max_iter=200000, precision=prec)
+                assert st["status"] == 0
+                P.tm_expand(ctx(), us, uf)
+                comp = P.tm_sensitivity(ctx(), rho, uf, dc)
+                eu, ec, edc = _errors(c, rho_h, c.free(us.cpu().numpy()), dc.cpu().numpy(), comp)
+                report.append((it, prec, st["iterations"], eu, ec, edc))
+                assert eu <= 1e-6 and ec <= 1e-9 and edc <= 1e-6, report[-1]
+        # one optimisation step (mixed solve, warm start)
+        P.tm_pcg_solve(ctx(), rho, f, u, rtol=1e-8, max_iter=200000, precision=P.TM_PREC_MIXED)
+        P.tm_expand(ctx(), u, uf)
+        P.tm_sensitivity(ctx(), rho, uf, dc)
+        P.tm_filter(ctx(), rho, dc, w.r_min, 0, dch)
+        P.tm_oc_update(ctx(), rho, dch, 0.3, 0.2, 0.5, w.rho_min, new)
+        rho, new = new, rho
+    for r in report:
+        print("snapshot %2d precision %d: %5d iterations, energy err %.2e, c err %.2e, dc err %.2e" % r)
+    # the design moved: the last snapshot is a different system from the first
+    assert float((rho - c.t(c.rho)).abs().max()) > 0.1
