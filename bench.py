@@ -275,6 +275,7 @@ def run_gpu(args):
     if rank != 0:
         return
     precision = precision_report(P, ctx, rho_first, f, u_first, u64)
+    batch = batch_report(P, W) if args.batch else None
     adapt = adaptation_timing(P, ctx, cur, d, Ne, dev)
     peak, peak_kind = _peaks()
     a_ms = prof["apply32_ms"] / max(prof["apply32_count"], 1)
@@ -297,6 +298,7 @@ def run_gpu(args):
         "mesh_upload_s": mesh_s,
         "fp64_pcg": fp64,
         "precision": precision,
+        "batch": batch,
         "adaptation": adapt,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
@@ -345,6 +347,55 @@ def precision_report(P, ctx, rho, f, u0, u64):
                      "compliance_rel_err": abs(c - c_ref) / abs(c_ref),
                      "dc_err_rel_max": float((dcu - dc_ref).abs().max() / dc_ref.abs().max())}
     return out
+
+
+def batch_report(P, W):
+    """Sixteen independent designs of 50k-500k leaves (two-level truss cantilevers, seeds
+    100-115), mixed solves from zero to 1e-8: one after another on one stream each, then all
+    at once through tm_pcg_solve_batch.  Throughput = sum of unknowns x iterations / wall time."""
+    import torch
+    works = W.batch_designs()
+    items = []
+    for w in works:
+        d = w.dom
+        s = torch.cuda.Stream()
+        c = P.tm_create(torch.cuda.current_device(), stream=s)
+        info = P.tm_mesh_upload(c, d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, w.dirichlet_faces, w.E0, w.Emin, w.nu,
+                                w.penal)
+        perm = P.tm_mesh_tables(c)["perm"]
+        rho = torch.as_tensor(w.rho[perm], device="cuda")
+        f = torch.zeros(3 * info["Nn"], dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(s):
+            P.tm_build_rhs(c, w.load_nodes, w.load_comp, w.load_val, f)
+        items.append((c, rho, f, info["n_free"]))
+    torch.cuda.synchronize()
+
+    def run(batched):
+        us = [torch.zeros_like(f) for _, _, f, _ in items]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if batched:
+            sts = P.tm_pcg_solve_batch([it[0] for it in items], [it[1] for it in items], [it[2] for it in items], us,
+                                       rtol=1e-8, max_iter=200000, precision=P.TM_PREC_MIXED)
+        else:
+            sts = [P.tm_pcg_solve(c, rho, f, u, rtol=1e-8, max_iter=200000, precision=P.TM_PREC_MIXED)
+                   for (c, rho, f, _), u in zip(items, us)]
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        work = sum(n * st["iterations"] for (_, _, _, n), st in zip(items, sts))
+        return wall, work, [st["iterations"] for st in sts]
+
+    run(True)   # warm-up: graphs captured, kernels loaded
+    seq_s, seq_work, seq_it = run(False)
+    bat_s, bat_work, bat_it = run(True)
+    for c, _, _, _ in items:
+        P.tm_destroy(c)
+    return {"designs": len(works), "elements": [int(len(w.leaves)) for w in works],
+            "unknowns_total": int(sum(it[3] for it in items)), "iterations": bat_it,
+            "same_iterations_as_sequential": bat_it == seq_it,
+            "sequential_s": seq_s, "batched_s": bat_s,
+            "sequential_gdof_iter_per_s": seq_work / seq_s / 1e9, "batched_gdof_iter_per_s": bat_work / bat_s / 1e9,
+            "speedup": seq_s / bat_s}
 
 
 def adaptation_timing(P, ctx, rho, d, Ne, dev):
@@ -463,6 +514,8 @@ def main():
                     help="iteration cap of the FP64 PCG comparison solve (same system as the first timed step)")
     ap.add_argument("--cpu-iters", type=int, default=600, help="oracle PCG iterations of the CPU baseline")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-batch", dest="batch", action="store_false",
+                    help="skip the batched-solve report (16 independent designs)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="plain kernel launches instead of CUDA-graph batches (for launch-list profiling)")
     ap.add_argument("--profile-apply", type=int, default=0,

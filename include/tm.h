@@ -203,6 +203,18 @@ int tm_jacobi_diag(tm_ctx *ctx, const double *rho_dev, double *d_dev);
 int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double *u_dev,
                  const tm_solve_opts *opts, tm_solve_stats *stats);
 
+/* Several independent solves at once (one design and load case per context, each
+ * context with its own mesh): solve i is tm_pcg_solve(ctxs[i], rho_dev[i], f_dev[i],
+ * u_dev[i], opts, &stats[i]) and gives the same result bit for bit; the solves run
+ * concurrently, one host thread per context, so that small meshes (which leave most
+ * of the GPU idle alone) share it.  The contexts must be distinct (TM_EINVAL
+ * otherwise); for the solves to overlap on the GPU each context needs its own
+ * non-default stream.  stats (n entries) and status (n entries, each solve's
+ * return code) may be NULL.  Returns TM_OK when every solve did, else the first
+ * non-OK code; each context's tm_last_error describes its own failure. */
+int tm_pcg_solve_batch(int n, tm_ctx *const *ctxs, const double *const *rho_dev, const double *const *f_dev,
+                       double *const *u_dev, const tm_solve_opts *opts, tm_solve_stats *stats, int *status);
+
 /* u_full = C u (Eq. 9): hanging DOFs interpolated, Dirichlet DOFs 0. */
 int tm_expand(tm_ctx *ctx, const double *u_dev, double *u_full_dev);
 

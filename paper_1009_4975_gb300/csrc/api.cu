@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pcg.cuh"
@@ -463,6 +464,32 @@ int tm_jacobi_diag(tm_ctx *ctx, const double *rho_dev, double *d_dev) {
   TM_CUDA(ctx, launch_diag(ctx->dm, ctx->w.ce64, d_dev, nullptr, nullptr, ctx->stream));
   ctx->launches += 2;
   return TM_OK;
+}
+
+int tm_pcg_solve_batch(int n, tm_ctx *const *ctxs, const double *const *rho_dev, const double *const *f_dev,
+                       double *const *u_dev, const tm_solve_opts *opts, tm_solve_stats *stats, int *status) {
+  if (n < 1 || !ctxs || !rho_dev || !f_dev || !u_dev || !opts) return TM_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return TM_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(ctxs[i], TM_EINVAL, "a context appears twice in one batch");
+  }
+  // one host thread per context: each drives its own solve on its own streams, so the
+  // solves' kernels, graph replays and convergence checks interleave on the GPU
+  std::vector<int> rc(n, TM_OK);
+  std::vector<std::thread> th;
+  th.reserve(n);
+  for (int i = 0; i < n; ++i)
+    th.emplace_back([&, i] {
+      rc[i] = tm_pcg_solve(ctxs[i], rho_dev[i], f_dev[i], u_dev[i], opts, stats ? &stats[i] : nullptr);
+    });
+  for (auto &t : th) t.join();
+  int first = TM_OK;
+  for (int i = 0; i < n; ++i) {
+    if (status) status[i] = rc[i];
+    if (first == TM_OK && rc[i] != TM_OK) first = rc[i];
+  }
+  return first;
 }
 
 int tm_expand(tm_ctx *ctx, const double *u_dev, double *u_full_dev) {

@@ -57,7 +57,7 @@ class tm_profile_data(C.Structure):
 
 
 EXPORTS = ["tm_create", "tm_destroy", "tm_set_stream", "tm_last_error", "tm_mesh_upload", "tm_mesh_tables",
-           "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_apply_K_f32_static", "tm_jacobi_diag", "tm_pcg_solve", "tm_expand",
+           "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_apply_K_f32_static", "tm_jacobi_diag", "tm_pcg_solve", "tm_pcg_solve_batch", "tm_expand",
            "tm_sensitivity", "tm_filter", "tm_oc_update", "tm_amr_mark", "tm_amr_adapt", "tm_design_difference",
            "tm_tables_adapt", "tm_profile", "tm_profile_read"]
 
@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH):
         "tm_apply_K_f32_static": [vp, vp, vp, vp],
         "tm_jacobi_diag": [vp, vp, vp],
         "tm_pcg_solve": [vp, vp, vp, vp, C.POINTER(tm_solve_opts), C.POINTER(tm_solve_stats)],
+        "tm_pcg_solve_batch": [C.c_int, vp, vp, vp, vp, C.POINTER(tm_solve_opts), vp, vp],
         "tm_expand": [vp, vp, vp],
         "tm_sensitivity": [vp, vp, vp, vp, C.POINTER(dbl)],
         "tm_filter": [vp, vp, vp, dbl, C.c_int, vp],
@@ -279,6 +280,32 @@ def tm_pcg_solve(ctx: Ctx, rho, f, u, rtol=1e-8, max_iter=100000, precision=TM_P
     if raise_on_error and rc != TM_OK:
         ctx.check(rc)
     return stats
+
+
+def tm_pcg_solve_batch(ctxs, rhos, fs, us, rtol=1e-8, max_iter=100000, precision=TM_PREC_FP64, inner_rtol=1e-3,
+                       check_every=64, raise_on_error=True, graphs=True) -> list:
+    """Independent solves on distinct contexts, run concurrently (include/tm.h)."""
+    import torch
+    n = len(ctxs)
+    if not (len(rhos) == len(fs) == len(us) == n) or n == 0:
+        raise ValueError("one rho, f and u per context")
+    hs = (C.c_void_p * n)(*[c.handle for c in ctxs])
+    rp = (C.c_void_p * n)(*[_elem(c, r, "rho").value for c, r in zip(ctxs, rhos)])
+    fp = (C.c_void_p * n)(*[_vec(c, f, torch.float64, "f").value for c, f in zip(ctxs, fs)])
+    up = (C.c_void_p * n)(*[_vec(c, u, torch.float64, "u").value for c, u in zip(ctxs, us)])
+    o = tm_solve_opts(rtol, max_iter, precision, inner_rtol, check_every, 0 if graphs else 1)
+    st = (tm_solve_stats * n)()
+    status = (C.c_int * n)()
+    rc = load_library().tm_pcg_solve_batch(n, hs, rp, fp, up, C.byref(o), st, status)
+    out = []
+    for i in range(n):
+        d = {k: getattr(st[i], k) for k, _ in tm_solve_stats._fields_}
+        d["status"] = status[i]
+        out.append(d)
+    if raise_on_error and rc != TM_OK:
+        bad = next((i for i in range(n) if status[i] != TM_OK), 0)
+        ctxs[bad].check(status[bad] if status[bad] != TM_OK else rc)
+    return out
 
 
 def tm_expand(ctx: Ctx, u, u_full):

@@ -37,7 +37,7 @@ from scipy import ndimage
 __all__ = [
     "Domain", "Workload", "uniform_leaves", "refine", "balance", "level_map",
     "smoothed_field", "random_field_mesh", "truss_mesh", "config1", "config1b",
-    "config2", "small_truss", "load_at",
+    "config2", "small_truss", "load_at", "batch_designs",
 ]
 
 
@@ -283,3 +283,12 @@ def small_truss(seed: int = 2, base=(12, 6, 6), L: int = 2, r0: float = 0.06) ->
     """The config-2 recipe on a coarser base: sizes the oracle's direct solver handles in seconds."""
     nx, ny, nz = base
     return truss_mesh(f"cantilever_{nx}x{ny}x{nz}_L{L}_truss", Domain(nx, ny, nz, L, 2.0 / nx), seed, r0=r0)
+
+
+def batch_designs(n: int = 16, seed0: int = 100):
+    """Independent designs for batched solves: the truss recipe with two levels on bases of
+    2k x k x k cells, k stepping from 9 to 26 across the batch (about 50k to 500k leaves),
+    seeds seed0, seed0 + 1, ..."""
+    ks = np.linspace(9, 26, n).round().astype(int)
+    return [truss_mesh(f"cantilever_{2 * k}x{k}x{k}_L2_truss_s{seed0 + i}", Domain(2 * k, k, k, 2, 1.0 / k),
+                       seed0 + i, r0=0.045) for i, k in enumerate(ks)]
