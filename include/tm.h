@@ -92,7 +92,8 @@ typedef struct {
   double rtol;                /* stop when ||f - A u||_2 <= rtol ||f||_2          */
   int32_t max_iter;           /* CG iterations (all sweeps together)              */
   int32_t precision;          /* TM_PREC_FP64 or TM_PREC_MIXED                    */
-  double inner_rtol;          /* mixed: residual reduction of one FP32 sweep      */
+  double inner_rtol;          /* mixed: FP32 residual reduction between two FP64
+                                 residual replacements (<= 0: 0.1)                */
   int32_t check_every;        /* iterations between host convergence checks       */
   int32_t no_graphs;          /* 0: each batch of check_every CG iterations is a   */
                               /* CUDA graph replayed on a library stream; 1: plain */
@@ -101,7 +102,7 @@ typedef struct {
 
 typedef struct {
   int32_t iterations;         /* CG iterations performed (sum over sweeps)        */
-  int32_t sweeps;             /* refinement sweeps (1 for FP64)                   */
+  int32_t sweeps;             /* mixed: FP64 residual replacements; FP64: 1        */
   double rel_residual;        /* final ||f - A u|| / ||f|| evaluated in FP64      */
   double seconds;             /* device time of the solve (CUDA events)           */
   int32_t fp64_applies;       /* FP64 operator applications                       */
@@ -196,10 +197,14 @@ int tm_jacobi_diag(tm_ctx *ctx, const double *rho_dev, double *d_dev);
 
 /* Solve C^T K(rho) C u = f by Jacobi-preconditioned CG (equivalent to CG on the
  * diagonally rescaled system of Sec. 5), warm-started from u_dev (Sec. 5).
- * TM_PREC_FP64: every step in FP64.  TM_PREC_MIXED: FP64 residual and update
- * around FP32-operator CG sweeps whose dot products accumulate in FP64.
- * Returns TM_ENOTCONVERGED (u holds the last iterate) when max_iter is reached,
- * TM_ENONFINITE on NaN/Inf. `stats` may be NULL. */
+ * TM_PREC_FP64: every step in FP64.  TM_PREC_MIXED: CG with the FP32 operator and
+ * FP32 vectors (dot products accumulated in FP64) and reliable updates: whenever the
+ * FP32 residual has dropped by inner_rtol, the FP32 correction is added to u in FP64
+ * and the residual is replaced by the FP64 true residual f - A u, keeping the search
+ * direction (made orthogonal to the new residual); convergence is always judged on the
+ * FP64 true residual.  Returns TM_ENOTCONVERGED (u holds the last iterate) when
+ * max_iter is reached, TM_ENONFINITE on NaN/Inf. `stats` may be NULL; stats->sweeps
+ * counts the FP64 residual replacements. */
 int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double *u_dev,
                  const tm_solve_opts *opts, tm_solve_stats *stats);
 

@@ -834,12 +834,18 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
     out.rel_residual = rel;
     if (rel > opts->rtol) status = TM_ENOTCONVERGED;
   } else {
-    // FP64 iterative refinement around FP32-operator CG sweeps.
-    const double inner = opts->inner_rtol > 0 ? opts->inner_rtol : 1e-3;
+    // FP32-operator CG with reliable updates: the FP32 run continues until its residual
+    // has dropped by inner_rtol from the largest value since the last update; then the
+    // FP32 correction is added to u in FP64, the residual is replaced by the FP64 true
+    // residual f - A u (rescaled to unit norm), and CG continues with the kept search
+    // direction, made orthogonal to the new residual (no restart).
+    const double delta = opts->inner_rtol > 0 ? opts->inner_rtol : 0.1;
     int left = opts->max_iter;
-    double rel = 0;
+    double rel = 0, scale_old = 0;
+    bool first = true;
     TM_CUDA(ctx, cudaMemsetAsync(w.q32, 0, n * sizeof(float), st));
-    for (int sweep = 0; sweep < 64; ++sweep) {
+    TM_CUDA(ctx, cudaMemsetAsync(w.x32, 0, n * sizeof(float), st));
+    for (int sweep = 0; sweep < 4096; ++sweep) {
       rc = timed_apply<double>(ctx, w.ce64, u_dev, w.q, w.part64, nullptr, nullptr, true, nullptr);
       if (rc) return rc;
       out.fp64_applies++;
@@ -853,14 +859,21 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
       if (rel <= opts->rtol || left <= 0) break;
       out.sweeps++;
       const double scale = 1.0 / std::sqrt(rr);
-      // stop the sweep at the inner reduction, or a little past the outer target
+      // stop a little past the outer target
       const double abs_stop = 0.25 * opts->rtol * opts->rtol * ff / rr;
-      rc = init_run(ctx, inner * inner, abs_stop, left);
-      if (rc) return rc;
-      TM_CUDA(ctx, cudaMemsetAsync(w.x32, 0, n * sizeof(float), st));
-      TM_CUDA(ctx, launch_start<float>(w.r, nullptr, scale, w.r32, w.p32, w.dinv32, n, solve_scalars(ctx), w.red,
-                                       w.ticket + 2, st));
+      if (first) {
+        rc = init_run(ctx, delta * delta, abs_stop, left);
+        if (rc) return rc;
+        TM_CUDA(ctx, launch_start<float>(w.r, nullptr, scale, w.r32, w.p32, w.dinv32, n, solve_scalars(ctx), w.red,
+                                         w.ticket + 2, st));
+        first = false;
+      } else {
+        TM_CUDA(ctx, launch_replace(w.r, scale, scale / scale_old, w.r32, w.p32, w.dinv32, n, abs_stop, left,
+                                    solve_scalars(ctx), w.red, w.ticket + 2, st));
+        ctx->launches += 1;
+      }
       ctx->launches += 1;
+      scale_old = scale;
       int it = 0, nf = 0;
       rc = run_cg<float, float>(ctx, check, graphs, &it, &nf, w.ce32, w.part32, w.x32, w.r32, w.p32, w.q32,
                                 w.dinv32);
@@ -868,7 +881,7 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
       out.iterations += it;
       out.fp32_applies += it;
       left -= it;
-      if (nf) return fail(ctx, TM_ENONFINITE, "non-finite value in the FP32 sweep");
+      if (nf) return fail(ctx, TM_ENONFINITE, "non-finite value in the FP32 iteration");
       TM_CUDA(ctx, launch_correct(u_dev, w.x32, 1.0 / scale, n, st));
       ctx->launches += 1;
     }

@@ -10,23 +10,24 @@
 // lists (the (element, corner) slots it collects, plus fold entries naming the
 // hanging nodes it is a master of).
 //
-// The kernel is persistent: each CTA walks blocks b, b + G, b + 2G, ... and
-// pipelines them with cp.async -- the record of block t+2 and the node values
-// of block t+1 are in flight while block t computes:
+// One CTA per block.  The block's record is staged into shared memory with
+// cp.async, then the node values it names (zero-filled for Dirichlet nodes):
 //   1. hanging nodes take the (bi)linear interpolation of their masters (C);
-//   2. one thread per element gathers its 8 corners and computes c_e K0 X_e
-//      (sum factorisation, element.cuh) into a per-element slot buffer;
+//   2. one thread per element gathers its 8 corners and computes c_e K0 X_e in
+//      the symmetry-adapted basis (element.cuh) into a per-element slot buffer;
 //   3. hanging nodes sum their slots; regular nodes sum their slots plus
 //      w * (sum) of every hanging node they are a master of (C^T) -- a fixed
 //      summation order, no atomics, bitwise reproducible;
 //   4. nodes touched only by this block are stored to y; nodes shared with
-//      other blocks are stored to their partial slots, which a second kernel
-//      sums in ascending block order.  Hanging DOFs of y are set to 0.
-// Dirichlet nodes read as 0 (zero-filled copies) and are written as 0.  The dot
-// product x . y can be accumulated on the fly (CG's p^T A p).
+//      other blocks are stored to their partial slots (node-major), which the CG
+//      update or a second kernel sums in ascending block order.  Hanging DOFs of
+//      y are set to 0.
+// The element energies c_e X_e^T K0 X_e can be accumulated on the fly: their
+// sum is CG's p^T A p.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "element.cuh"
 #include "pcg.cuh"
@@ -36,7 +37,7 @@
 namespace amr {
 
 constexpr int kApplyThreads = kBlockElems;  // one thread per element of a block
-constexpr int kRow = 25;                    // padded per-element row of the slot buffer
+constexpr int kRow = kSlotRow;              // padded per-element row of the slot buffer
 
 template <typename T>
 struct ApplyParams {
@@ -56,7 +57,6 @@ struct ApplyParams {
   int rec_bytes;    // record buffer size (largest record, multiple of 16)
 };
 
-__device__ __forceinline__ int slot_of(int p) { return (p >> 3) * kRow + 3 * (p & 7); }
 
 // Shared memory: XY (per-element slots) | R (3 values per local node) | record.
 template <typename T>
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(T) == 4 ? 4 : 2) apply_b
     T s0 = T(0), s1 = T(0), s2 = T(0);
     const int q1 = ip[nreg + j + 1];
     for (int q = ip[nreg + j]; q < q1; ++q) {
-      const T *d = XY + slot_of(iv[q]);
+      const T *d = XY + iv[q];
       s0 += d[0]; s1 += d[1]; s2 += d[2];
     }
     T *r = R + 3 * (nreg + j);
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(T) == 4 ? 4 : 2) apply_b
     for (int q = ip[i]; q < q1; ++q) {
       const int p = iv[q];
       if (!(p & kFoldBit)) {
-        const T *d = XY + slot_of(p);
+        const T *d = XY + p;
         s0 += d[0]; s1 += d[1]; s2 += d[2];
       } else {
         const T w = (p & kQuarterBit) ? T(0.25) : T(0.5);
@@ -275,14 +275,23 @@ int shared_grid(int64_t n) {
 template <typename T>
 cudaError_t launch_apply_blocks(const DeviceMesh &m, const T *ce, const T *x, T *y, T *part, double *energy_partials,
                                 SolveScalars *sc, unsigned int *ticket, const int *done, cudaStream_t s) {
-  static size_t configured = 0;
+  // the dynamic shared-memory opt-in, raised per device as larger meshes come (contexts
+  // may call from several host threads)
+  static std::mutex mu;
+  static size_t configured[kStaticMaxDevices] = {};
   const int rec_bytes = (m.max_rec_bytes + 15) / 16 * 16;
   const size_t smem = apply_smem_bytes<T>(m.max_local, rec_bytes);
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(apply_blocks_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    configured = smem;
+    if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem > configured[dev]) {
+      e = cudaFuncSetAttribute(apply_blocks_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      configured[dev] = smem;
+    }
   }
   ApplyParams<T> P;
   P.brec = m.brec; P.rec_off = m.rec_off; P.ce = ce; P.x = x; P.y = y; P.part = part;

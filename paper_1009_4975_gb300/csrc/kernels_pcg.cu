@@ -52,13 +52,15 @@ __global__ void __launch_bounds__(kVecThreads) update_kernel(TX *x, const T *p, 
     block_sum2<kVecThreads>(s0, s1);
     if (threadIdx.x == 0) {
       sc->beta = s0 / sc->rz;
+      sc->rz_prev = sc->rz;
       sc->rz = s0;
       sc->rr = s1;
       sc->it += 1;
+      if (s1 > sc->rrmax) sc->rrmax = s1;
       if (!finite(s0) || !finite(s1)) {
         sc->nonfinite = 1;
         sc->done = 1;
-      } else if (s1 <= sc->stop_rr || sc->it >= sc->max_it) {
+      } else if (s1 <= fmax(sc->stop_ratio2 * sc->rrmax, sc->stop_abs_rr) || sc->it >= sc->max_it) {
         sc->done = 1;
         sc->last_beta_skipped = 1;
       }
@@ -115,13 +117,15 @@ __global__ void __launch_bounds__(kVecThreads) update_nodes_kernel(TX *x, const 
     block_sum2<kVecThreads>(s0, s1);
     if (threadIdx.x == 0) {
       sc->beta = s0 / sc->rz;
+      sc->rz_prev = sc->rz;
       sc->rz = s0;
       sc->rr = s1;
       sc->it += 1;
+      if (s1 > sc->rrmax) sc->rrmax = s1;
       if (!finite(s0) || !finite(s1)) {
         sc->nonfinite = 1;
         sc->done = 1;
-      } else if (s1 <= sc->stop_rr || sc->it >= sc->max_it) {
+      } else if (s1 <= fmax(sc->stop_ratio2 * sc->rrmax, sc->stop_abs_rr) || sc->it >= sc->max_it) {
         sc->done = 1;
       }
     }
@@ -168,6 +172,7 @@ __global__ void __launch_bounds__(kVecThreads) start_kernel(const double *f, con
       sc->rz = s0;
       sc->rr = s1;
       sc->rr0 = s1;
+      sc->rrmax = s1;
       sc->it = 0;
       sc->nonfinite = 0;
       sc->last_beta_skipped = 0;
@@ -205,6 +210,74 @@ __global__ void correct_kernel(double *u, float *d, double s, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     u[i] += s * (double)d[i];
     d[i] = 0.0f;
+  }
+}
+
+// Residual replacement, pass 1: r = scale * r64, p *= c; rz = r.Dinv r, rp = r.p,
+// rr = r.r.  The last CTA sets beta = rz / (rz_prev c^2) (the previous iteration's
+// rz in the new units) and gamma = rp / rz, and restarts the run's counters.
+__global__ void __launch_bounds__(kVecThreads) replace_dots_kernel(const double *r64, double scale, double c, float *r,
+                                                                   float *p, const float *dinv, int64_t n,
+                                                                   double stop_abs_rr, int max_it, SolveScalars *sc,
+                                                                   double *partials, unsigned int *ticket) {
+  DotAcc<float> arz, arp, arr;
+  const float cf = (float)c;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float ri = (float)(scale * r64[i]);
+    const float pi = p[i] * cf;
+    r[i] = ri;
+    p[i] = pi;
+    arz.add_prod(ri, dinv[i] * ri);
+    arp.add_prod(ri, pi);
+    arr.add_prod(ri, ri);
+  }
+  double rz = arz.value(), rp = arp.value(), rr = arr.value();
+  block_sum2<kVecThreads>(rz, rp);
+  rr = block_sum<kVecThreads>(rr);
+  if (threadIdx.x == 0) {
+    partials[3 * blockIdx.x] = rz;
+    partials[3 * blockIdx.x + 1] = rp;
+    partials[3 * blockIdx.x + 2] = rr;
+  }
+  if (last_cta(ticket)) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += kVecThreads) {
+      s0 += ((volatile double *)partials)[3 * i];
+      s1 += ((volatile double *)partials)[3 * i + 1];
+      s2 += ((volatile double *)partials)[3 * i + 2];
+    }
+    block_sum2<kVecThreads>(s0, s1);
+    s2 = block_sum<kVecThreads>(s2);
+    if (threadIdx.x == 0) {
+      const double prev = sc->rz_prev * c * c;
+      sc->beta = s0 / prev;
+      sc->rp = s1 / s0;        // gamma
+      sc->rz = s0;
+      sc->rr = s2;
+      sc->rr0 = s2;
+      sc->rrmax = s2;
+      sc->it = 0;
+      sc->max_it = max_it;
+      sc->stop_abs_rr = stop_abs_rr;
+      sc->nonfinite = 0;
+      sc->last_beta_skipped = 0;
+      sc->done = (s2 <= stop_abs_rr || s2 == 0.0) ? 1 : 0;
+      if (!finite(s0) || !finite(s1) || !finite(s2) || !finite(sc->beta) || s0 <= 0.0) {
+        sc->nonfinite = 1;
+        sc->done = 1;
+      }
+    }
+  }
+}
+
+// Pass 2: p = z + beta (p - gamma z) with z = Dinv r.
+__global__ void __launch_bounds__(kVecThreads) replace_p_kernel(const float *r, float *p, const float *dinv, int64_t n,
+                                                                const SolveScalars *sc) {
+  if (sc->done) return;
+  const float beta = (float)sc->beta, gamma = (float)sc->rp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float zi = dinv[i] * r[i];
+    p[i] = zi + beta * (p[i] - gamma * zi);
   }
 }
 
@@ -273,6 +346,17 @@ template cudaError_t launch_start<float>(const double *, const double *, double,
 cudaError_t launch_residual64(const double *f, const double *q, double *r, int64_t n, double *out, double *partials,
                               unsigned int *ticket, cudaStream_t s) {
   residual64_kernel<<<vec_grid(n), kVecThreads, 0, s>>>(f, q, r, n, out, partials, ticket);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_replace(const double *r64, double scale, double c, float *r, float *p, const float *dinv,
+                           int64_t n, double stop_abs_rr, int max_it, SolveScalars *sc, double *partials,
+                           unsigned int *ticket, cudaStream_t s) {
+  replace_dots_kernel<<<vec_grid(n), kVecThreads, 0, s>>>(r64, scale, c, r, p, dinv, n, stop_abs_rr, max_it, sc,
+                                                          partials, ticket);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  replace_p_kernel<<<vec_grid(n), kVecThreads, 0, s>>>(r, p, dinv, n, sc);
   return cudaGetLastError();
 }
 

@@ -40,6 +40,8 @@ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
 }
 
 // LSD radix sort of keys, returning the permutation (stable).
+static_assert(kBlockElems * kSlotRow < kQuarterBit, "inverse-list slot offsets must stay below the fold bits");
+
 static std::vector<int64_t> radix_order(const std::vector<uint64_t> &key) {
   const size_t n = key.size();
   uint64_t mx = 0;
@@ -442,7 +444,8 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
       for (int k = 0; k < 8; ++k) m.lcorner[8 * e + k] = (uint16_t)local_of[m.conn[8 * e + k]];
     std::vector<std::vector<uint16_t>> lists(nloc);
     for (int64_t e = e0; e < e1; ++e)
-      for (int k = 0; k < 8; ++k) lists[local_of[m.conn[8 * e + k]]].push_back((uint16_t)(8 * (e - e0) + k));
+      for (int k = 0; k < 8; ++k)   // the slot's offset in the block's per-element result buffer
+        lists[local_of[m.conn[8 * e + k]]].push_back((uint16_t)((e - e0) * kSlotRow + 3 * k));
     for (size_t j = 0; j < used_h.size(); ++j) {
       const int32_t h = used_h[j];
       const bool quarter = m.hang_master[4 * h + 2] >= 0;

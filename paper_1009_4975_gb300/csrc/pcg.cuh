@@ -8,10 +8,13 @@ namespace amr {
 struct SolveScalars {
   double rz, pq, alpha, beta;
   double rr, rr0;          // current / initial ||r||^2 of this CG run
-  double stop_ratio2;      // stop when rr <= max(stop_ratio2 * rr0, stop_abs_rr)
+  double stop_ratio2;      // stop when rr <= max(stop_ratio2 * rrmax, stop_abs_rr)
   double stop_abs_rr;
   double stop_rr;
-  double scratch[7];
+  double rrmax;            // largest ||r||^2 since the run (or the last residual replacement) began
+  double rz_prev;          // rz of the previous iteration (the one p was built from)
+  double rp;               // r^T p after a residual replacement
+  double scratch[4];
   int it, max_it, done, nonfinite, last_beta_skipped, pad[3];
 };
 
@@ -31,6 +34,12 @@ cudaError_t launch_start(const double *f, const double *q, double scale, T *r, T
 cudaError_t launch_residual64(const double *f, const double *q, double *r, int64_t n, double *out,
                               double *partials, unsigned int *ticket, cudaStream_t s);
 cudaError_t launch_correct(double *u, float *d, double scale, int64_t n, cudaStream_t s);
+// Residual replacement of the mixed solver: r = scale * r64 (the FP64 true residual),
+// p *= c (the previous run's units to the new ones), then p made orthogonal to r
+// within span{Dinv r} and p = Dinv r + beta p; CG then continues with the kept direction.
+cudaError_t launch_replace(const double *r64, double scale, double c, float *r, float *p, const float *dinv,
+                           int64_t n, double stop_abs_rr, int max_it, SolveScalars *sc, double *partials,
+                           unsigned int *ticket, cudaStream_t s);
 cudaError_t launch_mask(const uint8_t *nflag, double *u, int64_t Nn, cudaStream_t s);
 
 }  // namespace amr

@@ -18,6 +18,7 @@ namespace amr {
 // touch directly or through a hanging corner's masters.
 constexpr int kBlockElems = 256;     // elements per block (ragged last block)
 constexpr int kMaxLocal = 1024;      // local nodes per block
+constexpr int kSlotRow = 25;         // per-element row of the operator's result buffer (24 + 1 pad)
 constexpr int kFoldBit = 0x8000;     // inverse-list entry names a hanging node to fold in
 constexpr int kQuarterBit = 0x4000;  // ... whose weight is 1/4 (else 1/2)
 
@@ -42,9 +43,10 @@ struct HostMesh {
   // operator blocks (consecutive canonical elements).  Local node ids of a
   // block: regular nodes first (shared ones, then interior), then the hanging
   // nodes its elements use.  The inverse list of a local node names the
-  // (element, corner) slots it fills -- entry e_local * 8 + k -- and, for a
-  // regular node, the hanging nodes it is a master of -- entry kFoldBit |
-  // (kQuarterBit if the hanging node has 4 masters) | hanging index.
+  // (element, corner) slots it fills -- entry e_local * kSlotRow + 3 k, the slot's
+  // offset in the per-element result buffer (< 0x4000) -- and, for a regular node,
+  // the hanging nodes it is a master of -- entry kFoldBit | (kQuarterBit if the
+  // hanging node has 4 masters) | hanging index.
   int32_t nblk = 0, max_local = 0;
   std::vector<int32_t> blk_elem;      // nblk+1: element ranges
   std::vector<int32_t> blk_node;      // nblk+1: regular local node ranges in lnode

@@ -268,7 +268,7 @@ def tm_jacobi_diag(ctx: Ctx, rho, d):
     ctx.check(load_library().tm_jacobi_diag(ctx.handle, _elem(ctx, rho, "rho"), _vec(ctx, d, torch.float64, "d")))
 
 
-def tm_pcg_solve(ctx: Ctx, rho, f, u, rtol=1e-8, max_iter=100000, precision=TM_PREC_FP64, inner_rtol=1e-3,
+def tm_pcg_solve(ctx: Ctx, rho, f, u, rtol=1e-8, max_iter=100000, precision=TM_PREC_FP64, inner_rtol=0.1,
                  check_every=64, raise_on_error=True, graphs=True) -> dict:
     import torch
     o = tm_solve_opts(rtol, max_iter, precision, inner_rtol, check_every, 0 if graphs else 1)
@@ -282,7 +282,7 @@ def tm_pcg_solve(ctx: Ctx, rho, f, u, rtol=1e-8, max_iter=100000, precision=TM_P
     return stats
 
 
-def tm_pcg_solve_batch(ctxs, rhos, fs, us, rtol=1e-8, max_iter=100000, precision=TM_PREC_FP64, inner_rtol=1e-3,
+def tm_pcg_solve_batch(ctxs, rhos, fs, us, rtol=1e-8, max_iter=100000, precision=TM_PREC_FP64, inner_rtol=0.1,
                        check_every=64, raise_on_error=True, graphs=True) -> list:
     """Independent solves on distinct contexts, run concurrently (include/tm.h)."""
     import torch
