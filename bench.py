@@ -463,39 +463,51 @@ def _sample_workload(w=None):
     return W.Workload(w.name + "_first2layers", dom, w.leaves[keep], w.rho[keep], ln, lc, lv)
 
 
-def cpu_baseline(args, full=None):
+def _cpu_sample(full=None):
+    """The oracle's reduced system on the bounded sample of the benchmark workload."""
     from oracle import fem as F
     from oracle import mesh as M
-    from oracle import solve as S
     w = _sample_workload(full)
     d = w.dom
     m = M.build_mesh(d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, dirichlet_faces=w.dirichlet_faces)
     A, f, C = F.reduced_system(m, w.rho[m.perm], w.load_nodes, w.load_comp, w.load_val, w.E0, w.Emin, w.nu,
                                w.penal)
+    return m, A, f
+
+
+def _cpu_run(args, m, A, f):
+    from oracle import solve as S
     n = A.shape[0]
-    iters = args.cpu_iters
-    u, it, rr, sec = S.jacobi_pcg(A, f, rtol=1e-30, max_iter=iters)
-    value = n * it / sec / 1e9
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+    u, it, rr, sec = S.jacobi_pcg(A, f, rtol=1e-30, max_iter=args.cpu_iters)
+    return {"value": n * it / sec / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{it} Jacobi-PCG iterations (scipy CSR SpMV, FP64) on the benchmark mesh's leaves in "
                       f"the first 2 base-cell layers at the clamped face: {m.Ne} elements, {n} unknowns",
             "seconds": sec}
 
 
+def cpu_baseline(args, full=None):
+    return _cpu_run(args, *_cpu_sample(full))
+
+
 def run_reference(args):
+    """The oracle as it stands, on the host cores: W untimed and K timed runs of its Jacobi-PCG on
+    the bounded sample (each run a fixed number of iterations)."""
     ws, rank, local = _dist()
     if rank != 0:
         return
+    sample = _cpu_sample()
+    for _ in range(args.warmup):
+        _cpu_run(args, *sample)
     t0 = time.perf_counter()
     vals = []
     cb = None
     for _ in range(max(args.steps, 1)):
-        cb = cpu_baseline(args)
+        cb = _cpu_run(args, *sample)
         vals.append(cb["value"])
     wall = time.perf_counter() - t0
     value = sum(vals) / len(vals)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": 0, "ms_per_step": 1e3 * wall / max(args.steps, 1), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded octree truss cantilever)",
             "impl": "reference", "config": {"workload": "cantilever_48x24x24_L3_truss (bounded sample)"},
             "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": value,
