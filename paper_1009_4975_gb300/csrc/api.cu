@@ -310,6 +310,7 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
   }
   TM_CUDA(ctx, upload(o, B, &m.rec_off, h.rec_off));
   m.max_rec_bytes = h.max_rec_bytes;
+  TM_CUDA(ctx, apply_residency(m, &m.resident_cta32, &m.resident_cta64));
   TM_CUDA(ctx, upload(o, B, &m.sh_node, h.sh_node));
   TM_CUDA(ctx, upload(o, B, &m.sh_ptr, h.sh_ptr));
   TM_CUDA(ctx, upload(o, B, &m.sh_of_node, h.sh_of_node));

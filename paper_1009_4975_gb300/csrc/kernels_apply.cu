@@ -55,6 +55,7 @@ struct ApplyParams {
   int nblk;
   int max_local;    // local nodes of the largest block
   int rec_bytes;    // record buffer size (largest record, multiple of 16)
+  int ahead;        // CTAs resident on the GPU: block b prefetches the record of b + ahead into L2
 };
 
 
@@ -129,6 +130,12 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(T) == 4 ? 4 : 2) apply_b
   const int b = blockIdx.x;
   // record, then the node values it names: every copy of a stage in flight at once
   issue_record(P.brec, P.rec_off, b, P.nblk, rec);
+  // the record of the block that starts about one resident wave later, into L2 (one bulk
+  // prefetch; records are 16-byte aligned multiples of 16 bytes)
+  if (tid == 0 && P.ahead > 0 && b + P.ahead < P.nblk) {
+    const int r0 = P.rec_off[b + P.ahead], nr = P.rec_off[b + P.ahead + 1] - r0;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(P.brec + r0), "r"(16 * nr) : "memory");
+  }
   cp_async_wait<0>();
   __syncthreads();
   issue_values<T>(rec, P.x, R, true);
@@ -293,11 +300,12 @@ cudaError_t launch_apply_blocks(const DeviceMesh &m, const T *ce, const T *x, T 
       configured[dev] = smem;
     }
   }
+  const int ahead = sizeof(T) == 4 ? m.resident_cta32 : m.resident_cta64;
   ApplyParams<T> P;
   P.brec = m.brec; P.rec_off = m.rec_off; P.ce = ce; P.x = x; P.y = y; P.part = part;
   P.dotp = energy_partials; P.sc = sc; P.ticket = ticket; P.done = done; P.nblk = m.nblk;
   for (int i = 0; i < 72; ++i) (&P.K.b[0][0][0])[i] = (T)m.modal[i];
-  P.max_local = m.max_local; P.rec_bytes = rec_bytes;
+  P.max_local = m.max_local; P.rec_bytes = rec_bytes; P.ahead = ahead;
   if (m.nblk > 0) apply_blocks_kernel<T><<<m.nblk, kApplyThreads, smem, s>>>(P);
   return cudaGetLastError();
 }
@@ -312,6 +320,27 @@ cudaError_t launch_apply(const DeviceMesh &m, const T *ce, const T *x, T *y, T *
   apply_shared_kernel<T><<<item_grid(items), 256, 0, s>>>(m.sh_node, m.sh_ptr, m.nsh, m.hang_node,
                                                           zero_hanging ? m.nh : 0, part, y, done);
   return cudaGetLastError();
+}
+
+// CTAs of the block pass resident on the whole GPU for this mesh's shared-memory size, in FP32
+// and FP64 (queried once per mesh, outside any stream capture).
+cudaError_t apply_residency(const DeviceMesh &m, int *resident32, int *resident64) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int rec_bytes = (m.max_rec_bytes + 15) / 16 * 16;
+  const size_t s32 = apply_smem_bytes<float>(m.max_local, rec_bytes), s64 = apply_smem_bytes<double>(m.max_local, rec_bytes);
+  e = cudaFuncSetAttribute(apply_blocks_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(apply_blocks_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64);
+  int b32 = 0, b64 = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, apply_blocks_kernel<float>, kApplyThreads, s32);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, apply_blocks_kernel<double>, kApplyThreads, s64);
+  if (e != cudaSuccess) return e;
+  *resident32 = b32 * sms;
+  *resident64 = b64 * sms;
+  return cudaSuccess;
 }
 
 template cudaError_t launch_apply_blocks<double>(const DeviceMesh &, const double *, const double *, double *,

@@ -118,6 +118,7 @@ struct DeviceMesh {
   uint4 *brec = nullptr;
   int32_t *rec_off = nullptr;
   int32_t max_rec_bytes = 0;
+  int32_t resident_cta32 = 0, resident_cta64 = 0;  // block-pass CTAs resident on the GPU (record prefetch distance)
   int32_t *sh_node = nullptr, *sh_ptr = nullptr;
   int32_t *sh_of_node = nullptr;      // node -> shared-node index, -1 when one block owns it
   int32_t *dg_ptr = nullptr, *dg_elem = nullptr;
@@ -210,6 +211,7 @@ constexpr int64_t kStaticSlots = int64_t(1) << 21;   // shared-node partials: up
 constexpr int kStaticMaxDevices = 64;
 cudaError_t static_scratch(int device, float **ce, float **part);
 cudaError_t launch_coeff_f32(const DeviceMesh &m, const double *rho, float *ce32, cudaStream_t s);
+cudaError_t apply_residency(const DeviceMesh &m, int *resident32, int *resident64);
 // adaptation (kernels_amr.cu)
 cudaError_t launch_amr_mark(const DeviceMesh &m, const double *rho, double rho_solid, double r_amr, int8_t *tmp,
                             int8_t *mark, cudaStream_t s);
