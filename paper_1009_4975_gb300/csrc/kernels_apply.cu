@@ -279,27 +279,32 @@ int shared_grid(int64_t n) {
   return (int)g;
 }
 
+// The block pass's dynamic shared-memory opt-in on the current device: only ever raised
+// (meshes of several contexts share the kernel; contexts may call from several threads).
+template <typename T>
+cudaError_t ensure_apply_smem(size_t smem) {
+  static std::mutex mu;
+  static size_t configured[kStaticMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (smem > configured[dev]) {
+    e = cudaFuncSetAttribute(apply_blocks_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured[dev] = smem;
+  }
+  return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t launch_apply_blocks(const DeviceMesh &m, const T *ce, const T *x, T *y, T *part, double *energy_partials,
                                 SolveScalars *sc, unsigned int *ticket, const int *done, cudaStream_t s) {
-  // the dynamic shared-memory opt-in, raised per device as larger meshes come (contexts
-  // may call from several host threads)
-  static std::mutex mu;
-  static size_t configured[kStaticMaxDevices] = {};
   const int rec_bytes = (m.max_rec_bytes + 15) / 16 * 16;
   const size_t smem = apply_smem_bytes<T>(m.max_local, rec_bytes);
-  {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(mu);
-    if (smem > configured[dev]) {
-      e = cudaFuncSetAttribute(apply_blocks_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      configured[dev] = smem;
-    }
-  }
+  cudaError_t e = ensure_apply_smem<T>(smem);
+  if (e != cudaSuccess) return e;
   const int ahead = sizeof(T) == 4 ? m.resident_cta32 : m.resident_cta64;
   ApplyParams<T> P;
   P.brec = m.brec; P.rec_off = m.rec_off; P.ce = ce; P.x = x; P.y = y; P.part = part;
@@ -331,9 +336,8 @@ cudaError_t apply_residency(const DeviceMesh &m, int *resident32, int *resident6
   if (e != cudaSuccess) return e;
   const int rec_bytes = (m.max_rec_bytes + 15) / 16 * 16;
   const size_t s32 = apply_smem_bytes<float>(m.max_local, rec_bytes), s64 = apply_smem_bytes<double>(m.max_local, rec_bytes);
-  e = cudaFuncSetAttribute(apply_blocks_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(apply_blocks_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64);
+  e = ensure_apply_smem<float>(s32);
+  if (e == cudaSuccess) e = ensure_apply_smem<double>(s64);
   int b32 = 0, b64 = 0;
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, apply_blocks_kernel<float>, kApplyThreads, s32);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, apply_blocks_kernel<double>, kApplyThreads, s64);
