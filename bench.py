@@ -3,8 +3,8 @@ cantilever mesh (base 48x24x24, three refinement levels along a seeded truss, ~2
 ~5.4M unknowns), through the C ABI of libtm.
 
 One step = one optimisation iteration on the fixed mesh: Jacobi-PCG solve of C^T K(rho) C u = f to
-a relative residual of 1e-8 (FP32 operator inside FP64 iterative refinement, warm-started from the
-previous u), expansion u_full = C u, compliance sensitivities, the volume-weighted filter of Eq. 5
+a relative residual of 1e-8 (FP32 CG with reliable updates: FP64 true-residual replacement after
+every 10x reduction, warm-started from the previous u), expansion u_full = C u, compliance sensitivities, the volume-weighted filter of Eq. 5
 and the OC update.  Metric: GDOF*iter/s = unknowns * CG iterations / solve-step seconds.
 
 Arms:

@@ -56,7 +56,7 @@ extern "C" {
 #define TM_ESTATE 7          /* call out of order (e.g. no mesh uploaded)         */
 
 #define TM_PREC_FP64 0       /* every step in FP64                                */
-#define TM_PREC_MIXED 1      /* FP32 operator inside FP64 iterative refinement    */
+#define TM_PREC_MIXED 1      /* FP32 CG with FP64 reliable updates                */
 #define TM_PREC_FP32 1
 
 typedef struct tm_ctx tm_ctx;
@@ -90,7 +90,7 @@ typedef struct {
 
 typedef struct {
   double rtol;                /* stop when ||f - A u||_2 <= rtol ||f||_2          */
-  int32_t max_iter;           /* CG iterations (all sweeps together)              */
+  int32_t max_iter;           /* CG iterations in all                             */
   int32_t precision;          /* TM_PREC_FP64 or TM_PREC_MIXED                    */
   double inner_rtol;          /* mixed: FP32 residual reduction between two FP64
                                  residual replacements (<= 0: 0.1)                */
@@ -101,7 +101,7 @@ typedef struct {
 } tm_solve_opts;
 
 typedef struct {
-  int32_t iterations;         /* CG iterations performed (sum over sweeps)        */
+  int32_t iterations;         /* CG iterations performed                          */
   int32_t sweeps;             /* mixed: FP64 residual replacements; FP64: 1        */
   double rel_residual;        /* final ||f - A u|| / ||f|| evaluated in FP64      */
   double seconds;             /* device time of the solve (CUDA events)           */

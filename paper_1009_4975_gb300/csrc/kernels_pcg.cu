@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kVecThreads) start_kernel(const double *f, con
   }
 }
 
-// r64 = f - q; rr = r.r (FP64) for the outer residual of iterative refinement.
+// r64 = f - q; rr = r.r (FP64): the true residual of the mixed solver's reliable updates.
 __global__ void __launch_bounds__(kVecThreads) residual64_kernel(const double *f, const double *q, double *r,
                                                                  int64_t n, double *out, double *partials,
                                                                  unsigned int *ticket) {
