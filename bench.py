@@ -286,7 +286,7 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 operator, f64 refinement/reductions",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (operator and CG vectors; f64 true residuals, solution and reductions)",
         "data": "synthetic (seeded octree truss cantilever)",
         "config": {"workload": w.name, "elements": Ne, "nodes": Nn, "unknowns": nfree,
                    "hanging_nodes": info["n_hanging"], "solver": "mixed: FP32-operator Jacobi-PCG with reliable updates "
