@@ -154,6 +154,19 @@ int tm_tables_build(const tm_mesh_desc *d, tm_tables **out, tm_mesh_info *info, 
 int tm_tables_copy(const tm_tables *t, int64_t *perm, int32_t *node_xyz, int32_t *conn, int32_t *hang_node,
                    int32_t *hang_master, uint8_t *node_flags);
 void tm_tables_free(tm_tables *t);
+/* Host-only export of the operator's block tables, for checking them without a GPU:
+ * rec_off[n_blocks + 1] (record ranges in 16-byte units), brec[*rec_bytes] (the
+ * per-block records the operator kernel stages: a header of 12 int32 -- first
+ * element, elements, regular and shared local nodes, hanging local nodes, inverse
+ * entries, byte offsets of the lslot, hent, iptr, inv, lcorner and lnode sections --
+ * then those sections), modal[72] (the element matrix of the unit cube in the
+ * symmetry-adapted basis: 8 blocks of 3 x 3, row-major, block s couples the modes
+ * s^1, s^2, s^4 of components 0, 1, 2), sh_node[n_shared] and sh_ptr[n_shared + 1]
+ * (block-shared nodes and the ranges of their partials).  Any pointer may be NULL;
+ * call with brec NULL to learn *rec_bytes first. */
+int tm_tables_operator(const tm_tables *t, int32_t *rec_off, uint8_t *brec, double *modal, int32_t *sh_node,
+                       int32_t *sh_ptr, int64_t *rec_bytes);
+
 /* Host-only form of tm_amr_adapt on built tables (marks and rho on the host, in
  * the tables' element order); same rules, outputs and errors. */
 int tm_tables_adapt(const tm_tables *t, const int8_t *mark, const double *rho, int64_t capacity,

@@ -681,6 +681,19 @@ int tm_tables_copy(const tm_tables *t, int64_t *perm, int32_t *node_xyz, int32_t
   return TM_OK;
 }
 
+int tm_tables_operator(const tm_tables *t, int32_t *rec_off, uint8_t *brec, double *modal, int32_t *sh_node,
+                       int32_t *sh_ptr, int64_t *rec_bytes) {
+  if (!t) return TM_EINVAL;
+  const amr::HostMesh &h = t->m;
+  if (rec_bytes) *rec_bytes = (int64_t)h.brec.size();
+  if (rec_off) std::memcpy(rec_off, h.rec_off.data(), h.rec_off.size() * sizeof(int32_t));
+  if (brec) std::memcpy(brec, h.brec.data(), h.brec.size());
+  if (modal) std::memcpy(modal, h.modal.data(), 72 * sizeof(double));
+  if (sh_node) std::memcpy(sh_node, h.sh_node.data(), h.sh_node.size() * sizeof(int32_t));
+  if (sh_ptr) std::memcpy(sh_ptr, h.sh_ptr.data(), h.sh_ptr.size() * sizeof(int32_t));
+  return TM_OK;
+}
+
 void tm_tables_free(tm_tables *t) { delete t; }
 
 }  // extern "C"

@@ -59,7 +59,7 @@ class tm_profile_data(C.Structure):
 EXPORTS = ["tm_create", "tm_destroy", "tm_set_stream", "tm_last_error", "tm_mesh_upload", "tm_mesh_tables",
            "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_apply_K_f32_static", "tm_jacobi_diag", "tm_pcg_solve", "tm_pcg_solve_batch", "tm_expand",
            "tm_sensitivity", "tm_filter", "tm_oc_update", "tm_amr_mark", "tm_amr_adapt", "tm_design_difference",
-           "tm_tables_adapt", "tm_profile", "tm_profile_read"]
+           "tm_tables_adapt", "tm_tables_operator", "tm_profile", "tm_profile_read"]
 
 _lib = None
 
@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH):
         "tm_amr_adapt": [vp, vp, vp, i64, vp, vp, C.POINTER(i64)],
         "tm_design_difference": [vp, vp, i64, vp, vp, C.POINTER(dbl)],
         "tm_tables_adapt": [vp, vp, vp, i64, vp, vp, C.POINTER(i64)],
+        "tm_tables_operator": [vp, vp, vp, vp, vp, vp, C.POINTER(i64)],
         "tm_profile": [vp, C.c_int],
         "tm_profile_read": [vp, C.POINTER(tm_profile_data)],
     }
@@ -400,6 +401,35 @@ def tm_tables_adapt(nx, ny, nz, max_level, h0, leaves, mark, rho):
             raise TmError(code, "tm_tables_adapt rejected the marks")
         return _adapt_call(lib.tm_tables_adapt, info.Ne, h, C.c_void_p(mk.ctypes.data), C.c_void_p(r.ctypes.data),
                            raise_err)
+    finally:
+        lib.tm_tables_free(h)
+
+
+def tm_tables_operator(nx, ny, nz, max_level, h0, leaves, dirichlet_faces=1):
+    """Host-only export of the operator's block tables (tm_tables_operator): dict with info,
+    rec_off, brec (uint8), modal (8, 3, 3), sh_node, sh_ptr."""
+    lib = load_library()
+    lv = np.ascontiguousarray(np.asarray(leaves, np.int32).reshape(-1, 4))
+    d = tm_mesh_desc(nx, ny, nz, max_level, h0, lv.shape[0], lv.ctypes.data_as(C.POINTER(C.c_int32)),
+                     dirichlet_faces, 1.0, 1e-9, 0.3, 3.0)
+    info = tm_mesh_info()
+    h = C.c_void_p()
+    err = C.create_string_buffer(512)
+    rc = lib.tm_tables_build(C.byref(d), C.byref(h), C.byref(info), err, 512)
+    if rc != TM_OK:
+        raise TmError(rc, err.value.decode())
+    try:
+        nb = C.c_int64(0)
+        lib.tm_tables_operator(h, None, None, None, None, None, C.byref(nb))
+        out = {"info": {k: getattr(info, k) for k, _ in tm_mesh_info._fields_},
+               "rec_off": np.zeros(info.n_blocks + 1, np.int32), "brec": np.zeros(nb.value, np.uint8),
+               "modal": np.zeros((8, 3, 3)), "sh_node": np.zeros(info.n_shared, np.int32),
+               "sh_ptr": np.zeros(info.n_shared + 1, np.int32)}
+        rc = lib.tm_tables_operator(h, *[C.c_void_p(out[k].ctypes.data) for k in
+                                         ("rec_off", "brec", "modal", "sh_node", "sh_ptr")], C.byref(nb))
+        if rc != TM_OK:
+            raise TmError(rc, "tm_tables_operator failed")
+        return out
     finally:
         lib.tm_tables_free(h)
 
