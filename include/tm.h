@@ -187,6 +187,14 @@ int tm_apply_K(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double *
  * of TM_PREC_MIXED). */
 int tm_apply_K_f32(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float *y_dev);
 
+/* The FP32 operator on nrhs vectors at once (1 <= nrhs <= 4; several load cases of one
+ * design): y_dev[r] = C^T K(rho) C x_dev[r] (Eq. 6-9), x_dev and y_dev each nrhs
+ * consecutive A-space vectors of 3 * Nn floats (device).  Each y_dev[r] is the result
+ * of tm_apply_K_f32 on x_dev[r] bit for bit; the operator tables are staged once per
+ * block for all vectors.  Its partial-sum scratch (4 * 3 floats per block-shared node
+ * partial) is allocated on the first call for the uploaded mesh. */
+int tm_apply_K_f32_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const float *x_dev, float *y_dev);
+
 /* The FP32 operator of tm_apply_K_f32 for callers that cannot allocate device
  * memory at call time -- code running while a CUDA stream is being captured into
  * a graph, callers under a strict memory budget, or hosts that forbid

@@ -439,6 +439,19 @@ int tm_apply_K_f32(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float
   return drain_profile(ctx, false);
 }
 
+int tm_apply_K_f32_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const float *x_dev, float *y_dev) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!rho_dev || !x_dev || !y_dev) return fail(ctx, TM_EINVAL, "null pointer");
+  if (nrhs < 1 || nrhs > kMaxRhs) return fail(ctx, TM_EINVAL, "nrhs must be in [1, " + std::to_string(kMaxRhs) + "]");
+  Work &w = ctx->w;
+  if (!w.part_multi) TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.part_multi, (size_t)kMaxRhs * 3 * ctx->dm.nslot));
+  TM_CUDA(ctx, launch_coeff_f32(ctx->dm, rho_dev, w.ce32, ctx->stream));
+  TM_CUDA(ctx, launch_apply_multi(ctx->dm, nrhs, w.ce32, x_dev, y_dev, w.part_multi, ctx->stream));
+  ctx->launches += 3;
+  return TM_OK;
+}
+
 int tm_apply_K_f32_static(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float *y_dev) {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);

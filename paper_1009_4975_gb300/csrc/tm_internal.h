@@ -140,6 +140,7 @@ struct Work {
   unsigned int *ticket = nullptr;  // last-block counters
   int *status = nullptr;       // device status word
   int8_t *mark_tmp = nullptr;  // Ne, intermediate adaptation marks
+  float *part_multi = nullptr; // kMaxRhs * 3 * nslot, partials of the multi-vector operator (on first use)
   // solver vectors (3 * Nn)
   double *r = nullptr, *p = nullptr, *q = nullptr, *dinv = nullptr, *d = nullptr;
   float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *dinv32 = nullptr, *x32 = nullptr;
@@ -212,6 +213,11 @@ constexpr int kStaticMaxDevices = 64;
 cudaError_t static_scratch(int device, float **ce, float **part);
 cudaError_t launch_coeff_f32(const DeviceMesh &m, const double *rho, float *ce32, cudaStream_t s);
 cudaError_t apply_residency(const DeviceMesh &m, int *resident32, int *resident64);
+// several vectors at once (kernels_multi.cu)
+constexpr int kMaxRhs = 4;
+size_t apply_multi_smem_bytes(const DeviceMesh &m, int nr);
+cudaError_t launch_apply_multi(const DeviceMesh &m, int nr, const float *ce, const float *x, float *y, float *part,
+                               cudaStream_t s);
 // adaptation (kernels_amr.cu)
 cudaError_t launch_amr_mark(const DeviceMesh &m, const double *rho, double rho_solid, double r_amr, int8_t *tmp,
                             int8_t *mark, cudaStream_t s);

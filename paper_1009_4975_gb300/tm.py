@@ -57,7 +57,7 @@ class tm_profile_data(C.Structure):
 
 
 EXPORTS = ["tm_create", "tm_destroy", "tm_set_stream", "tm_last_error", "tm_mesh_upload", "tm_mesh_tables",
-           "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_apply_K_f32_static", "tm_jacobi_diag", "tm_pcg_solve", "tm_pcg_solve_batch", "tm_expand",
+           "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_apply_K_f32_static", "tm_apply_K_f32_multi", "tm_jacobi_diag", "tm_pcg_solve", "tm_pcg_solve_batch", "tm_expand",
            "tm_sensitivity", "tm_filter", "tm_oc_update", "tm_amr_mark", "tm_amr_adapt", "tm_design_difference",
            "tm_tables_adapt", "tm_tables_operator", "tm_profile", "tm_profile_read"]
 
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH):
         "tm_apply_K": [vp, vp, vp, vp],
         "tm_apply_K_f32": [vp, vp, vp, vp],
         "tm_apply_K_f32_static": [vp, vp, vp, vp],
+        "tm_apply_K_f32_multi": [vp, C.c_int, vp, vp, vp],
         "tm_jacobi_diag": [vp, vp, vp],
         "tm_pcg_solve": [vp, vp, vp, vp, C.POINTER(tm_solve_opts), C.POINTER(tm_solve_stats)],
         "tm_pcg_solve_batch": [C.c_int, vp, vp, vp, vp, C.POINTER(tm_solve_opts), vp, vp],
@@ -262,6 +263,15 @@ def tm_apply_K_f32_static(ctx: Ctx, rho, x, y):
     ctx.check(load_library().tm_apply_K_f32_static(ctx.handle, _elem(ctx, rho, "rho"),
                                                    _vec(ctx, x, torch.float32, "x"),
                                                    _vec(ctx, y, torch.float32, "y")))
+
+
+def tm_apply_K_f32_multi(ctx: Ctx, rho, x, y):
+    """FP32 operator on the rows of x (nrhs, 3 Nn) at once; see include/tm.h."""
+    import torch
+    if x.dim() != 2 or x.shape != y.shape or x.shape[1] != 3 * ctx.info["Nn"]:
+        raise ValueError("x and y must be (nrhs, 3 Nn)")
+    ctx.check(load_library().tm_apply_K_f32_multi(ctx.handle, x.shape[0], _elem(ctx, rho, "rho"),
+                                                  _ptr(x, torch.float32, None, "x"), _ptr(y, torch.float32, None, "y")))
 
 
 def tm_jacobi_diag(ctx: Ctx, rho, d):
