@@ -241,6 +241,17 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
 int tm_pcg_solve_batch(int n, tm_ctx *const *ctxs, const double *const *rho_dev, const double *const *f_dev,
                        double *const *u_dev, const tm_solve_opts *opts, tm_solve_stats *stats, int *status);
 
+/* Several load cases of one design at once (1 <= nrhs <= 4; TM_PREC_MIXED only):
+ * f_dev and u_dev hold nrhs consecutive A-space vectors (device), u_dev the warm starts
+ * on entry.  The load cases iterate in lockstep; each has its own CG scalars and
+ * reliable updates, and gets the same u and iteration count as tm_pcg_solve with the
+ * same options, bit for bit.  They share one operator pass per iteration
+ * (tm_apply_K_f32_multi).  Plain kernel launches, no CUDA graphs.  stats: nrhs entries
+ * (may be NULL); their seconds field is the time of the whole call.  Work buffers for 4
+ * load cases are allocated on the first call for the uploaded mesh. */
+int tm_pcg_solve_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const double *f_dev, double *u_dev,
+                       const tm_solve_opts *opts, tm_solve_stats *stats);
+
 /* u_full = C u (Eq. 9): hanging DOFs interpolated, Dirichlet DOFs 0. */
 int tm_expand(tm_ctx *ctx, const double *u_dev, double *u_full_dev);
 

@@ -447,7 +447,8 @@ int tm_apply_K_f32_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const flo
   Work &w = ctx->w;
   if (!w.part_multi) TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.part_multi, (size_t)kMaxRhs * 3 * ctx->dm.nslot));
   TM_CUDA(ctx, launch_coeff_f32(ctx->dm, rho_dev, w.ce32, ctx->stream));
-  TM_CUDA(ctx, launch_apply_multi(ctx->dm, nrhs, w.ce32, x_dev, y_dev, w.part_multi, ctx->stream));
+  TM_CUDA(ctx, launch_apply_multi(ctx->dm, nrhs, w.ce32, x_dev, y_dev, w.part_multi, nullptr, nullptr, nullptr,
+                                  ctx->stream));
   ctx->launches += 3;
   return TM_OK;
 }
@@ -910,6 +911,168 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
   rc = drain_profile(ctx, false);
   if (rc) return rc;
   if (stats) *stats = out;
+  if (status == TM_ENOTCONVERGED) return fail(ctx, status, "max_iter reached before rtol");
+  return status;
+}
+
+int tm_pcg_solve_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const double *f_dev, double *u_dev,
+                       const tm_solve_opts *opts, tm_solve_stats *stats) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!rho_dev || !f_dev || !u_dev || !opts) return fail(ctx, TM_EINVAL, "null pointer");
+  if (nrhs < 1 || nrhs > kMaxRhs) return fail(ctx, TM_EINVAL, "nrhs must be in [1, " + std::to_string(kMaxRhs) + "]");
+  if (opts->precision != TM_PREC_MIXED) return fail(ctx, TM_EINVAL, "multi-load solves are TM_PREC_MIXED only");
+  if (!(opts->rtol > 0) || opts->max_iter < 1) return fail(ctx, TM_EINVAL, "need rtol > 0 and max_iter >= 1");
+  const DeviceMesh &m = ctx->dm;
+  Work &w = ctx->w;
+  cudaStream_t st = ctx->stream;
+  const int64_t n = 3 * m.Nn;
+  const int check = opts->check_every > 0 ? opts->check_every : 32;
+  const double delta = opts->inner_rtol > 0 ? opts->inner_rtol : 0.1;
+  if (!w.mvec) {
+    TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.mvec, (size_t)kMaxRhs * 4 * n));
+    TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.mr64, (size_t)kMaxRhs * n));
+    TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.msc, (size_t)kMaxRhs));
+    TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.mdotp, (size_t)kMaxRhs * std::max(m.nblk, 1)));
+  }
+  if (!w.part_multi) TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.part_multi, (size_t)kMaxRhs * 3 * m.nslot));
+  // kind-major: the p (q) vectors of the load cases are consecutive, as the operator reads them
+  auto vec = [&](int r, int k) { return w.mvec + ((size_t)k * kMaxRhs + r) * n; };   // k: 0 x, 1 r, 2 p, 3 q
+  auto scal = [&](int r) { return w.msc + r; };
+  std::vector<tm_solve_stats> out(nrhs);
+  std::memset(out.data(), 0, nrhs * sizeof(tm_solve_stats));
+  TM_CUDA(ctx, cudaEventRecord(ctx->ev0, st));
+  TM_CUDA(ctx, launch_coeff(m, w, rho_dev, st));
+  TM_CUDA(ctx, launch_diag(m, w.ce64, nullptr, w.dinv, w.dinv32, st));
+  ctx->launches += 2;
+  double *rr_dev = scal_at(ctx, 81), *ff_dev = scal_at(ctx, 82);
+  std::vector<double> ff(nrhs), scale_old(nrhs, 0.0), rel(nrhs, 0.0);
+  std::vector<int> left(nrhs, opts->max_iter), active(nrhs, 1), first(nrhs, 1);
+  int rc;
+  // FP64 true residual of load case r into mr64[r]; returns ||r||^2 in *rr
+  auto residual = [&](int r, double *rr) -> int {
+    int rc2 = timed_apply<double>(ctx, w.ce64, u_dev + (size_t)r * n, w.q, w.part64, nullptr, nullptr, true, nullptr);
+    if (rc2) return rc2;
+    out[r].fp64_applies++;
+    TM_CUDA(ctx, launch_residual64(f_dev + (size_t)r * n, w.q, w.mr64 + (size_t)r * n, n, rr_dev, w.red,
+                                   w.ticket + 1, st));
+    ctx->launches += 1;
+    return read_scalar(ctx, rr_dev, rr);
+  };
+  // start or continue load case r's CG run from its FP64 residual (reliable update)
+  auto segment = [&](int r, double rr) -> int {
+    const double scale = 1.0 / std::sqrt(rr);
+    const double abs_stop = 0.25 * opts->rtol * opts->rtol * ff[r] / rr;
+    out[r].sweeps++;
+    if (first[r]) {
+      SolveScalars sc0;
+      std::memset(&sc0, 0, sizeof(sc0));
+      sc0.stop_ratio2 = delta * delta;
+      sc0.stop_abs_rr = abs_stop;
+      sc0.max_it = left[r];
+      TM_CUDA(ctx, cudaMemcpyAsync(scal(r), &sc0, sizeof(sc0), cudaMemcpyHostToDevice, st));
+      TM_CUDA(ctx, cudaMemsetAsync(vec(r, 0), 0, n * sizeof(float), st));
+      TM_CUDA(ctx, launch_start<float>(w.mr64 + (size_t)r * n, nullptr, scale, vec(r, 1), vec(r, 2), w.dinv32, n,
+                                       scal(r), w.red, w.ticket + 2, st));
+      TM_CUDA(ctx, cudaStreamSynchronize(st));   // sc0 lives on the host stack
+      first[r] = 0;
+    } else {
+      TM_CUDA(ctx, launch_replace(w.mr64 + (size_t)r * n, scale, scale / scale_old[r], vec(r, 1), vec(r, 2), w.dinv32,
+                                  n, abs_stop, left[r], scal(r), w.red, w.ticket + 2, st));
+      ctx->launches += 1;
+    }
+    ctx->launches += 1;
+    scale_old[r] = scale;
+    return TM_OK;
+  };
+  for (int r = 0; r < nrhs; ++r) {
+    TM_CUDA(ctx, launch_residual64(f_dev + (size_t)r * n, nullptr, nullptr, n, ff_dev, w.red, w.ticket + 1, st));
+    ctx->launches += 1;
+    rc = read_scalar(ctx, ff_dev, &ff[r]);
+    if (rc) return rc;
+    if (!std::isfinite(ff[r])) return fail(ctx, TM_ENONFINITE, "non-finite load vector");
+    if (ff[r] == 0.0) {
+      TM_CUDA(ctx, cudaMemsetAsync(u_dev + (size_t)r * n, 0, n * sizeof(double), st));
+      active[r] = 0;
+      continue;
+    }
+    double rr = 0;
+    rc = residual(r, &rr);
+    if (rc) return rc;
+    if (!std::isfinite(rr)) return fail(ctx, TM_ENONFINITE, "non-finite residual");
+    rel[r] = std::sqrt(rr / ff[r]);
+    if (rel[r] <= opts->rtol) {
+      active[r] = 0;
+      continue;
+    }
+    rc = segment(r, rr);
+    if (rc) return rc;
+  }
+  // inactive load cases are marked done so that the kernels skip them
+  for (int r = 0; r < nrhs; ++r)
+    if (!active[r]) {
+      const int one = 1;
+      TM_CUDA(ctx, cudaMemcpyAsync(&scal(r)->done, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+      TM_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+  std::vector<SolveScalars> hs(nrhs);
+  auto any_active = [&] {
+    for (int r = 0; r < nrhs; ++r)
+      if (active[r]) return true;
+    return false;
+  };
+  while (any_active()) {
+    for (int k = 0; k < check; ++k) {
+      TM_CUDA(ctx, launch_apply_multi(m, nrhs, w.ce32, vec(0, 2), vec(0, 3), w.part_multi, w.mdotp, scal(0),
+                                      w.ticket + 7, st));
+      ctx->launches += 1;
+      for (int r = 0; r < nrhs; ++r) {
+        if (!active[r]) continue;
+        TM_CUDA(ctx, launch_update_nodes<float, float>(vec(r, 0), vec(r, 2), vec(r, 3), vec(r, 1), w.dinv32, m.Nn,
+                                                       m.sh_of_node, m.sh_ptr, w.part_multi + (size_t)r * 3 * m.nslot,
+                                                       scal(r), w.red, w.ticket, st));
+        TM_CUDA(ctx, launch_pupdate<float>(vec(r, 2), vec(r, 1), w.dinv32, n, scal(r), st));
+        ctx->launches += 2;
+      }
+    }
+    for (int r = 0; r < nrhs; ++r)
+      TM_CUDA(ctx, cudaMemcpyAsync(&hs[r], scal(r), sizeof(SolveScalars), cudaMemcpyDeviceToHost, st));
+    TM_CUDA(ctx, cudaStreamSynchronize(st));
+    for (int r = 0; r < nrhs; ++r) {
+      if (!active[r] || !hs[r].done) continue;
+      // the run of load case r reached its replacement point (or its limit)
+      out[r].iterations += hs[r].it;
+      out[r].fp32_applies += hs[r].it;
+      left[r] -= hs[r].it;
+      if (hs[r].nonfinite) return fail(ctx, TM_ENONFINITE, "non-finite value in the FP32 iteration");
+      TM_CUDA(ctx, launch_correct(u_dev + (size_t)r * n, vec(r, 0), 1.0 / scale_old[r], n, st));
+      ctx->launches += 1;
+      double rr = 0;
+      rc = residual(r, &rr);
+      if (rc) return rc;
+      if (!std::isfinite(rr)) return fail(ctx, TM_ENONFINITE, "non-finite residual");
+      rel[r] = std::sqrt(rr / ff[r]);
+      if (rel[r] <= opts->rtol || left[r] <= 0) {
+        active[r] = 0;       // its scalars keep done set: the kernels skip it
+        continue;
+      }
+      rc = segment(r, rr);
+      if (rc) return rc;
+    }
+  }
+  TM_CUDA(ctx, cudaEventRecord(ctx->ev1, st));
+  TM_CUDA(ctx, cudaEventSynchronize(ctx->ev1));
+  float ms = 0;
+  TM_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+  rc = drain_profile(ctx, false);
+  if (rc) return rc;
+  int status = TM_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    out[r].rel_residual = rel[r];
+    out[r].seconds = ms * 1e-3;
+    if (rel[r] > opts->rtol) status = TM_ENOTCONVERGED;
+  }
+  if (stats) std::memcpy(stats, out.data(), nrhs * sizeof(tm_solve_stats));
   if (status == TM_ENOTCONVERGED) return fail(ctx, status, "max_iter reached before rtol");
   return status;
 }

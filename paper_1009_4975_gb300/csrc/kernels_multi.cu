@@ -1,5 +1,6 @@
 // The FP32 operator applied to several vectors at once (paper Eq. 6-9 for each):
-// y_r = C^T K(rho) C x_r, r < nr.  Same tables, same per-vector arithmetic and
+// y_r = C^T K(rho) C x_r, r < nr; inside the multi-load CG it also sums each vector's
+// element energies (p^T A p) and sets alpha, skipping vectors whose run is done.  Same tables, same per-vector arithmetic and
 // summation order as the single-vector block pass (kernels_apply.cu), so each y_r
 // equals a single application bit for bit; the block's record is staged into shared
 // memory once for all vectors, and the node values of every vector in one stage.
@@ -11,6 +12,8 @@
 #include <mutex>
 
 #include "element.cuh"
+#include "pcg.cuh"
+#include "reduce.cuh"
 #include "tm_internal.h"
 
 namespace amr {
@@ -47,6 +50,9 @@ struct MultiParams {
   float *y;            // nr vectors, stride ld
   float *part;         // nr partial arrays, stride 3 * nslot
   int64_t ld, nslot;
+  double *dotp;        // with sc: per-CTA element-energy partials, nr x gridDim.x
+  SolveScalars *sc;    // per-vector CG scalars (nullptr: plain application); done vectors are skipped
+  unsigned int *ticket;
   ModalBlocks<float> K;
   int nr, max_local;
 };
@@ -97,6 +103,7 @@ __global__ void __launch_bounds__(kThreads, 2) apply_blocks_multi_kernel(MultiPa
   const int code[8] = {(int)(cw.x & 0xFFFF), (int)(cw.x >> 16), (int)(cw.y & 0xFFFF), (int)(cw.y >> 16),
                        (int)(cw.z & 0xFFFF), (int)(cw.z >> 16), (int)(cw.w & 0xFFFF), (int)(cw.w >> 16)};
   for (int r = 0; r < P.nr; ++r) {
+    if (P.sc && *(volatile const int *)&P.sc[r].done) continue;   // uniform over the CTA
     float *R = reinterpret_cast<float *>(vals + (size_t)r * vb);
     // 1. hanging nodes: interpolation of their masters (C)
     for (int j = tid; j < nhang; j += kThreads) {
@@ -113,7 +120,8 @@ __global__ void __launch_bounds__(kThreads, 2) apply_blocks_multi_kernel(MultiPa
       }
     }
     __syncthreads();
-    // 2. element products into the slot buffer
+    // 2. element products into the slot buffer (with the element energies for CG's p^T A p)
+    double energy = 0.0;
     if (tid < ne) {
       float X[24], Y[24];
 #pragma unroll
@@ -122,9 +130,14 @@ __global__ void __launch_bounds__(kThreads, 2) apply_blocks_multi_kernel(MultiPa
         X[3 * k + 1] = R[3 * code[k] + 1];
         X[3 * k + 2] = R[3 * code[k] + 2];
       }
-      element_op<float, kOpApply>(X, Y, coef, P.K);
+      if (P.sc) energy = (double)element_op<float, kOpBoth>(X, Y, coef, P.K);
+      else element_op<float, kOpApply>(X, Y, coef, P.K);
 #pragma unroll
       for (int j = 0; j < 24; ++j) XY[tid * kRowM + j] = Y[j];
+    }
+    if (P.sc) {
+      energy = block_sum<kThreads>(energy);
+      if (tid == 0) P.dotp[(size_t)r * gridDim.x + b] = energy;
     }
     __syncthreads();
     // 3a. hanging nodes sum their slots
@@ -163,6 +176,23 @@ __global__ void __launch_bounds__(kThreads, 2) apply_blocks_multi_kernel(MultiPa
     }
     __syncthreads();   // the slot buffer is reused by the next vector
   }
+  // CG: the last CTA sums each running vector's energies: pq = p^T A p, alpha = rz / pq
+  if (P.sc && last_cta(P.ticket)) {
+    for (int r = 0; r < P.nr; ++r) {
+      if (*(volatile const int *)&P.sc[r].done) continue;
+      const double pq = sum_partials<kThreads>(P.dotp + (size_t)r * gridDim.x, gridDim.x);
+      if (tid == 0) {
+        SolveScalars *sc = &P.sc[r];
+        sc->pq = pq;
+        sc->alpha = sc->rz / pq;
+        if (!isfinite(pq) || !isfinite(sc->alpha) || pq <= 0.0) {
+          sc->nonfinite = 1;
+          sc->done = 1;
+        }
+      }
+      __syncthreads();
+    }
+  }
 }
 
 // Second pass for every vector: shared nodes sum their partials (ascending block
@@ -197,7 +227,7 @@ size_t apply_multi_smem_bytes(const DeviceMesh &m, int nr) {
 }
 
 cudaError_t launch_apply_multi(const DeviceMesh &m, int nr, const float *ce, const float *x, float *y, float *part,
-                               cudaStream_t s) {
+                               double *dotp, SolveScalars *sc, unsigned int *ticket, cudaStream_t s) {
   static std::mutex mu;
   static size_t configured[kStaticMaxDevices] = {};
   const size_t smem = apply_multi_smem_bytes(m, nr);
@@ -216,10 +246,11 @@ cudaError_t launch_apply_multi(const DeviceMesh &m, int nr, const float *ce, con
   MultiParams P;
   P.brec = m.brec; P.rec_off = m.rec_off; P.ce = ce; P.x = x; P.y = y; P.part = part;
   P.ld = 3 * m.Nn; P.nslot = m.nslot; P.nr = nr; P.max_local = m.max_local;
+  P.dotp = dotp; P.sc = sc; P.ticket = ticket;
   for (int i = 0; i < 72; ++i) (&P.K.b[0][0][0])[i] = (float)m.modal[i];
   if (m.nblk > 0) apply_blocks_multi_kernel<<<m.nblk, kThreads, smem, s>>>(P);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || sc) return e;   // inside CG the update kernel sums the partials
   const int64_t items = m.nsh + m.nh;
   const dim3 grid((unsigned)std::max<int64_t>((items + 255) / 256, 1), (unsigned)nr);
   shared_multi_kernel<<<grid, 256, 0, s>>>(m.sh_node, m.sh_ptr, m.nsh, m.hang_node, m.nh, part, m.nslot, y, 3 * m.Nn,

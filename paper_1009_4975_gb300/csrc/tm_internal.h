@@ -141,6 +141,12 @@ struct Work {
   int *status = nullptr;       // device status word
   int8_t *mark_tmp = nullptr;  // Ne, intermediate adaptation marks
   float *part_multi = nullptr; // kMaxRhs * 3 * nslot, partials of the multi-vector operator (on first use)
+  // multi-load CG (on first use): per load case x, r, p, q (FP32) and the FP64 residual,
+  // CG scalars, element-energy partials
+  float *mvec = nullptr;       // 4 kinds (x, r, p, q) x kMaxRhs load cases x 3 Nn (kind-major)
+  double *mr64 = nullptr;      // kMaxRhs * 3 Nn
+  struct SolveScalars *msc = nullptr;   // kMaxRhs
+  double *mdotp = nullptr;     // kMaxRhs * nblk
   // solver vectors (3 * Nn)
   double *r = nullptr, *p = nullptr, *q = nullptr, *dinv = nullptr, *d = nullptr;
   float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *dinv32 = nullptr, *x32 = nullptr;
@@ -216,8 +222,9 @@ cudaError_t apply_residency(const DeviceMesh &m, int *resident32, int *resident6
 // several vectors at once (kernels_multi.cu)
 constexpr int kMaxRhs = 4;
 size_t apply_multi_smem_bytes(const DeviceMesh &m, int nr);
+struct SolveScalars;
 cudaError_t launch_apply_multi(const DeviceMesh &m, int nr, const float *ce, const float *x, float *y, float *part,
-                               cudaStream_t s);
+                               double *dotp, SolveScalars *sc, unsigned int *ticket, cudaStream_t s);
 // adaptation (kernels_amr.cu)
 cudaError_t launch_amr_mark(const DeviceMesh &m, const double *rho, double rho_solid, double r_amr, int8_t *tmp,
                             int8_t *mark, cudaStream_t s);

@@ -57,7 +57,7 @@ class tm_profile_data(C.Structure):
 
 
 EXPORTS = ["tm_create", "tm_destroy", "tm_set_stream", "tm_last_error", "tm_mesh_upload", "tm_mesh_tables",
-           "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_apply_K_f32_static", "tm_apply_K_f32_multi", "tm_jacobi_diag", "tm_pcg_solve", "tm_pcg_solve_batch", "tm_expand",
+           "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_apply_K_f32_static", "tm_apply_K_f32_multi", "tm_jacobi_diag", "tm_pcg_solve", "tm_pcg_solve_batch", "tm_pcg_solve_multi", "tm_expand",
            "tm_sensitivity", "tm_filter", "tm_oc_update", "tm_amr_mark", "tm_amr_adapt", "tm_design_difference",
            "tm_tables_adapt", "tm_tables_operator", "tm_profile", "tm_profile_read"]
 
@@ -87,6 +87,7 @@ def load_library(path: str = LIB_PATH):
         "tm_jacobi_diag": [vp, vp, vp],
         "tm_pcg_solve": [vp, vp, vp, vp, C.POINTER(tm_solve_opts), C.POINTER(tm_solve_stats)],
         "tm_pcg_solve_batch": [C.c_int, vp, vp, vp, vp, C.POINTER(tm_solve_opts), vp, vp],
+        "tm_pcg_solve_multi": [vp, C.c_int, vp, vp, vp, C.POINTER(tm_solve_opts), vp],
         "tm_expand": [vp, vp, vp],
         "tm_sensitivity": [vp, vp, vp, vp, C.POINTER(dbl)],
         "tm_filter": [vp, vp, vp, dbl, C.c_int, vp],
@@ -316,6 +317,27 @@ def tm_pcg_solve_batch(ctxs, rhos, fs, us, rtol=1e-8, max_iter=100000, precision
     if raise_on_error and rc != TM_OK:
         bad = next((i for i in range(n) if status[i] != TM_OK), 0)
         ctxs[bad].check(status[bad] if status[bad] != TM_OK else rc)
+    return out
+
+
+def tm_pcg_solve_multi(ctx: Ctx, rho, F, U, rtol=1e-8, max_iter=100000, inner_rtol=0.1, check_every=64,
+                       raise_on_error=True) -> list:
+    """Mixed solves of the load cases in the rows of F (nrhs, 3 Nn) into U, in lockstep; see include/tm.h."""
+    import torch
+    if F.dim() != 2 or F.shape != U.shape or F.shape[1] != 3 * ctx.info["Nn"]:
+        raise ValueError("F and U must be (nrhs, 3 Nn)")
+    nr = F.shape[0]
+    o = tm_solve_opts(rtol, max_iter, TM_PREC_MIXED, inner_rtol, check_every, 1)
+    st = (tm_solve_stats * nr)()
+    rc = load_library().tm_pcg_solve_multi(ctx.handle, nr, _elem(ctx, rho, "rho"), _ptr(F, torch.float64, None, "F"),
+                                           _ptr(U, torch.float64, None, "U"), C.byref(o), st)
+    out = []
+    for i in range(nr):
+        d = {k: getattr(st[i], k) for k, _ in tm_solve_stats._fields_}
+        d["status"] = rc
+        out.append(d)
+    if raise_on_error and rc != TM_OK:
+        ctx.check(rc)
     return out
 
 

@@ -41,3 +41,35 @@ def test_multi_vector_operator_rejects_too_many_vectors():
     X = torch.zeros((5, 3 * c.m.Nn), dtype=torch.float32, device=c.dev)
     with pytest.raises(P.TmError):
         P.tm_apply_K_f32_multi(ctx(), c.t(c.rho), X, torch.zeros_like(X))
+
+
+def test_multi_load_solve_matches_single_solves():
+    """Three load cases of one design solved in lockstep: every u and iteration count equals
+    the single mixed solve of that case bit for bit, and meets the solve parity criterion."""
+    import torch
+    from oracle import fem as F
+    P = tm()
+    c = case("config1b")
+    c.upload()
+    n3 = 3 * c.m.Nn
+    node = c.w.load_nodes
+    loads = [(node, [2], [-1.0]), (node, [1], [-1.0]), (np.concatenate([node, node]), [0, 2], [1.0, -0.5])]
+    Fd = torch.zeros((len(loads), n3), dtype=torch.float64, device=c.dev)
+    for r, (nd, comp, val) in enumerate(loads):
+        f = torch.zeros(n3, dtype=torch.float64, device=c.dev)
+        P.tm_build_rhs(ctx(), nd, comp, val, f)
+        Fd[r] = f
+    rho = c.t(c.rho)
+    U = torch.zeros_like(Fd)
+    stats = P.tm_pcg_solve_multi(ctx(), rho, Fd, U, rtol=1e-8, max_iter=200000)
+    torch.cuda.synchronize()
+    for r, (nd, comp, val) in enumerate(loads):
+        u1 = torch.zeros(n3, dtype=torch.float64, device=c.dev)
+        st1 = P.tm_pcg_solve(ctx(), rho, Fd[r].contiguous(), u1, rtol=1e-8, max_iter=200000,
+                             precision=P.TM_PREC_MIXED)
+        torch.cuda.synchronize()
+        assert stats[r]["iterations"] == st1["iterations"]
+        assert U[r].cpu().numpy().tobytes() == u1.cpu().numpy().tobytes()
+        fr = F.reduced_system(c.m, c.rho, nd, comp, val)[1]
+        ur = c.free(U[r].cpu().numpy())
+        assert np.linalg.norm(fr - c.A @ ur) / np.linalg.norm(fr) <= 1e-8 * (1 + 1e-3)
