@@ -37,7 +37,7 @@ from scipy import ndimage
 __all__ = [
     "Domain", "Workload", "uniform_leaves", "refine", "balance", "level_map",
     "smoothed_field", "random_field_mesh", "truss_mesh", "config1", "config1b",
-    "config2", "small_truss", "load_at", "batch_designs",
+    "config2", "small_truss", "load_at", "batch_designs", "unet_init",
 ]
 
 
@@ -292,3 +292,17 @@ def batch_designs(n: int = 16, seed0: int = 100):
     ks = np.linspace(9, 26, n).round().astype(int)
     return [truss_mesh(f"cantilever_{2 * k}x{k}x{k}_L2_truss_s{seed0 + i}", Domain(2 * k, k, k, 2, 1.0 / k),
                        seed0 + i, r0=0.045) for i, k in enumerate(ks)]
+
+
+def unet_init(shapes, seed: int = 0):
+    """Seeded initial parameters for a network given as [(name, shape)]: weights normal with
+    variance 2 / fan_in (fan_in = input channels x kernel volume), biases uniform in +-0.1."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for name, shape in shapes:
+        if len(shape) > 1:
+            fan_in = int(np.prod(shape[1:]))
+            out.append(rng.standard_normal(shape) * np.sqrt(2.0 / fan_in))
+        else:
+            out.append(rng.uniform(-0.1, 0.1, shape))
+    return out
