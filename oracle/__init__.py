@@ -15,6 +15,10 @@ Modules
 ``solve``   sparse direct solve of the reduced system, Jacobi-PCG.
 ``topopt``  compliance, element sensitivities, the filters (Eq. 3-5) and the
             optimality-criteria update.
+``amr``     adaptation marks, the sibling and incompatibility sweeps, the new
+            leaf set with density transfer (Sec. 4, 6) and Eq. 10.
+``learn``   the learned initial guess (no paper counterpart): grid transfers,
+            a 3D U-Net and its energy loss.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against something other than itself (closed forms, exact rational
