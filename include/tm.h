@@ -315,6 +315,33 @@ int tm_amr_adapt(tm_ctx *ctx, const int8_t *mark_dev, const double *rho_dev, int
 int tm_design_difference(tm_ctx *ctx, const double *rho_dev, int64_t n_other, const int32_t *leaves_other,
                          const double *rho_other, double *d_out);
 
+/* ---- Learned initial guess (no counterpart in the paper): a 3D U-Net ------------
+ * Per level i < levels: two 3x3x3 convolutions (zero padding, bias) each followed by
+ * ReLU, channels[i] features; 2x2x2 average pooling between levels; on the way up,
+ * nearest 2x upsampling, concatenation [upsampled, skip] along channels and the two
+ * convolutions of that level; a 1x1x1 output convolution to c_out channels.
+ * Activations: n x C x x x y x z FP32, contiguous (device); x, y, z multiples of
+ * 2^(levels - 1).  Parameters: one FP32 array (device), tm_unet_param_count floats,
+ * per convolution its weights (Cout x Cin x k x k x k) then its bias, in the order
+ * encoder levels 0..levels-1, decoder levels levels-2..0, output.  Workspace:
+ * tm_unet_workspace_floats floats (device), caller-owned.
+ * tm_unet_forward: y = net(x); keeps the activations in the workspace.
+ * tm_unet_backward: given dy = dL/dy, writes dL/dparams (and dL/dx when dx is not
+ * NULL); needs the workspace of a tm_unet_forward with the same params and x.
+ * Direct CUDA-core kernels with fixed summation orders.  TM_EINVAL for a bad
+ * description or null pointers.  The count functions return -1 for a bad one. */
+typedef struct {
+  int32_t levels;             /* 1..6                                               */
+  int32_t channels[6];        /* features per level                                 */
+  int32_t c_in, c_out;
+  int32_t n, x, y, z;         /* batch and grid                                     */
+} tm_unet_desc;
+int64_t tm_unet_param_count(const tm_unet_desc *d);
+int64_t tm_unet_workspace_floats(const tm_unet_desc *d);
+int tm_unet_forward(tm_ctx *ctx, const tm_unet_desc *d, const float *params, const float *x, float *y, float *ws);
+int tm_unet_backward(tm_ctx *ctx, const tm_unet_desc *d, const float *params, const float *x, const float *dy,
+                     float *dparams, float *dx, float *ws);
+
 /* Instrumentation (no counterpart in the paper): tm_profile(ctx, 1) resets the
  * counters and starts timing every operator application with a CUDA-event
  * pair on the context's stream (both passes of the operator; applications a CG

@@ -219,6 +219,18 @@ constexpr int kStaticMaxDevices = 64;
 cudaError_t static_scratch(int device, float **ce, float **part);
 cudaError_t launch_coeff_f32(const DeviceMesh &m, const double *rho, float *ce32, cudaStream_t s);
 cudaError_t apply_residency(const DeviceMesh &m, int *resident32, int *resident64);
+// U-Net layers (kernels_unet.cu)
+cudaError_t unet_conv_fwd(const float *x, const float *w, const float *b, float *y, int N, int Ci, int Co, int X,
+                          int Y, int Z, int K, bool relu, cudaStream_t s);
+cudaError_t unet_relu_bwd(const float *y, float *g, int64_t n, cudaStream_t s);
+cudaError_t unet_conv_bwd(const float *x, const float *w, const float *dy, float *dx, bool dx_accumulate, float *dw,
+                          float *db, int N, int Ci, int Co, int X, int Y, int Z, int K, cudaStream_t s);
+cudaError_t unet_pool_fwd(const float *x, float *y, int64_t NC, int X, int Y, int Z, cudaStream_t s);
+cudaError_t unet_spread(const float *in, float *out, int64_t NC, int X, int Y, int Z, bool pool_adjoint,
+                        bool accumulate, cudaStream_t s);
+cudaError_t unet_gather8(const float *in, float *out, int64_t NC, int X, int Y, int Z, cudaStream_t s);
+cudaError_t unet_channels_copy(const float *src, int Cs, int sc0, float *dst, int Cd, int dc0, int nc, int N,
+                               int64_t S, bool accumulate, cudaStream_t s);
 // several vectors at once (kernels_multi.cu)
 constexpr int kMaxRhs = 4;
 size_t apply_multi_smem_bytes(const DeviceMesh &m, int nr);

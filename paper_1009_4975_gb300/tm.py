@@ -51,6 +51,11 @@ class tm_solve_stats(C.Structure):
                 ("seconds", C.c_double), ("fp64_applies", C.c_int32), ("fp32_applies", C.c_int32)]
 
 
+class tm_unet_desc(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("channels", C.c_int32 * 6), ("c_in", C.c_int32), ("c_out", C.c_int32),
+                ("n", C.c_int32), ("x", C.c_int32), ("y", C.c_int32), ("z", C.c_int32)]
+
+
 class tm_profile_data(C.Structure):
     _fields_ = [("launches", C.c_int64), ("apply32_count", C.c_int64), ("apply64_count", C.c_int64),
                 ("apply32_ms", C.c_double), ("apply64_ms", C.c_double)]
@@ -59,7 +64,8 @@ class tm_profile_data(C.Structure):
 EXPORTS = ["tm_create", "tm_destroy", "tm_set_stream", "tm_last_error", "tm_mesh_upload", "tm_mesh_tables",
            "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_apply_K_f32_static", "tm_apply_K_f32_multi", "tm_jacobi_diag", "tm_pcg_solve", "tm_pcg_solve_batch", "tm_pcg_solve_multi", "tm_expand",
            "tm_sensitivity", "tm_filter", "tm_oc_update", "tm_amr_mark", "tm_amr_adapt", "tm_design_difference",
-           "tm_tables_adapt", "tm_tables_operator", "tm_profile", "tm_profile_read"]
+           "tm_tables_adapt", "tm_tables_operator", "tm_unet_param_count", "tm_unet_workspace_floats",
+           "tm_unet_forward", "tm_unet_backward", "tm_profile", "tm_profile_read"]
 
 _lib = None
 
@@ -97,6 +103,8 @@ def load_library(path: str = LIB_PATH):
         "tm_design_difference": [vp, vp, i64, vp, vp, C.POINTER(dbl)],
         "tm_tables_adapt": [vp, vp, vp, i64, vp, vp, C.POINTER(i64)],
         "tm_tables_operator": [vp, vp, vp, vp, vp, vp, C.POINTER(i64)],
+        "tm_unet_forward": [vp, C.POINTER(tm_unet_desc), vp, vp, vp, vp],
+        "tm_unet_backward": [vp, C.POINTER(tm_unet_desc), vp, vp, vp, vp, vp, vp],
         "tm_profile": [vp, C.c_int],
         "tm_profile_read": [vp, C.POINTER(tm_profile_data)],
     }
@@ -111,6 +119,10 @@ def load_library(path: str = LIB_PATH):
     lib.tm_tables_copy.restype = C.c_int
     lib.tm_tables_free.argtypes = [vp]
     lib.tm_tables_free.restype = None
+    for name in ("tm_unet_param_count", "tm_unet_workspace_floats"):
+        fn = getattr(lib, name)
+        fn.argtypes = [C.POINTER(tm_unet_desc)]
+        fn.restype = C.c_int64
     lib.tm_last_error.argtypes = [vp]
     lib.tm_last_error.restype = C.c_char_p
     _lib = lib
@@ -464,6 +476,37 @@ def tm_tables_operator(nx, ny, nz, max_level, h0, leaves, dirichlet_faces=1):
         return out
     finally:
         lib.tm_tables_free(h)
+
+
+def unet_desc(channels, n, grid, c_in=4, c_out=3) -> tm_unet_desc:
+    ch = (C.c_int32 * 6)(*(list(channels) + [0] * (6 - len(channels))))
+    return tm_unet_desc(len(channels), ch, c_in, c_out, n, *grid)
+
+
+def tm_unet_param_count(desc: tm_unet_desc) -> int:
+    return load_library().tm_unet_param_count(C.byref(desc))
+
+
+def tm_unet_workspace_floats(desc: tm_unet_desc) -> int:
+    return load_library().tm_unet_workspace_floats(C.byref(desc))
+
+
+def tm_unet_forward(ctx: Ctx, desc: tm_unet_desc, params, x, y, ws):
+    """y = net(x) (float32 CUDA tensors); see include/tm.h."""
+    import torch
+    ctx.check(load_library().tm_unet_forward(ctx.handle, C.byref(desc), _ptr(params, torch.float32, None, "params"),
+                                             _ptr(x, torch.float32, None, "x"), _ptr(y, torch.float32, None, "y"),
+                                             _ptr(ws, torch.float32, None, "ws")))
+
+
+def tm_unet_backward(ctx: Ctx, desc: tm_unet_desc, params, x, dy, dparams, dx, ws):
+    """dL/dparams (and dL/dx unless dx is None) from dy, after tm_unet_forward with the same ws."""
+    import torch
+    ctx.check(load_library().tm_unet_backward(ctx.handle, C.byref(desc), _ptr(params, torch.float32, None, "params"),
+                                              _ptr(x, torch.float32, None, "x"), _ptr(dy, torch.float32, None, "dy"),
+                                              _ptr(dparams, torch.float32, None, "dparams"),
+                                              None if dx is None else _ptr(dx, torch.float32, None, "dx"),
+                                              _ptr(ws, torch.float32, None, "ws")))
 
 
 def tm_profile(ctx: Ctx, enable: bool = True):
