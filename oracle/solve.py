@@ -5,6 +5,10 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 * ``direct`` -- sparse LU of A (SciPy SuperLU), the reference solution.
 * ``dense_cholesky`` -- a textbook column Cholesky, written out, for tiny systems
   (an independent check on the sparse factorisation).
+* ``twolevel_pcg`` -- PCG with the additive two-level preconditioner
+  M^-1 = D^-1 + P (P^T A P)^-1 P^T (Jacobi plus a Galerkin coarse correction on a
+  coarse space given by a prolongation P, e.g. ``grid_prolongation``); no paper
+  counterpart: the coarse-grid correction of the learned part's extension.
 * ``jacobi_pcg`` -- preconditioned CG with the diagonal of A as preconditioner.
   Diagonal (Jacobi) preconditioning is the symmetric rescaling
   ``D^{-1/2} A D^{-1/2}`` of Sec. 5 applied implicitly: CG on the rescaled
@@ -81,3 +85,61 @@ def jacobi_pcg(A: sp.spmatrix, f: np.ndarray, u0=None, rtol=1e-8, max_iter=10000
         rn = np.linalg.norm(r)
         it += 1
     return u, it, rn / fn, time.perf_counter() - t0
+
+
+def pcg(A: sp.spmatrix, f: np.ndarray, prec, u0=None, rtol=1e-8, max_iter=100000):
+    """PCG with the SPD preconditioner z = prec(r), to ||f - A u|| <= rtol ||f|| (recurrence
+    residual).  Returns (u, iterations, recurrence relative residual)."""
+    A = A.tocsr()
+    f = np.asarray(f, np.float64)
+    u = np.zeros_like(f) if u0 is None else np.array(u0, np.float64)
+    r = f - A @ u
+    fn = np.linalg.norm(f)
+    z = prec(r)
+    p = z.copy()
+    rz = r @ z
+    it = 0
+    rn = np.linalg.norm(r)
+    while rn > rtol * fn and it < max_iter:
+        q = A @ p
+        alpha = rz / (p @ q)
+        u += alpha * p
+        r -= alpha * q
+        z = prec(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+        rn = np.linalg.norm(r)
+        it += 1
+    return u, it, rn / fn
+
+
+def grid_prolongation(mesh, g: int) -> sp.csr_matrix:
+    """P (free DOFs x 3 cells): the trilinear prolongation of cell-centred values on the
+    level-g grid (oracle.learn.prolong, linear extrapolation at the boundary) at the free
+    nodes, per displacement component (DOF 3 node + c, coarse DOF 3 cell + c)."""
+    from . import fem as F
+    from . import learn as LR
+    X, Y, Z = LR.grid_shape(mesh, g)
+    ncell = X * Y * Z
+    cols = []
+    for c in range(ncell):
+        e = np.zeros(ncell)
+        e[c] = 1.0
+        cols.append(sp.csr_matrix(LR.prolong(mesh, e.reshape(X, Y, Z, 1), g)[:, :1]))
+    Pn = sp.hstack(cols).tocsr()                     # nodes x cells
+    Pf = Pn[F.free_nodes(mesh)]
+    return sp.kron(Pf, sp.eye(3)).tocsr()
+
+
+def coarse_correction(A: sp.spmatrix, P: sp.spmatrix):
+    """r -> P (P^T A P)^-1 P^T r (Galerkin coarse correction), by a sparse LU of P^T A P."""
+    lu = spla.splu((P.T @ A @ P).tocsc())
+    return lambda r: P @ lu.solve(P.T @ np.asarray(r, np.float64))
+
+
+def twolevel_pcg(A: sp.spmatrix, f: np.ndarray, P: sp.spmatrix, u0=None, rtol=1e-8, max_iter=100000):
+    """PCG with M^-1 r = D^-1 r + P (P^T A P)^-1 P^T r.  Returns (u, iterations, residual)."""
+    dinv = 1.0 / A.diagonal()
+    cc = coarse_correction(A, P)
+    return pcg(A, f, lambda r: dinv * r + cc(r), u0, rtol, max_iter)

@@ -99,3 +99,59 @@ def test_refined_mesh_agrees_with_uniform_mesh_on_a_linear_solution():
     for p in common:
         assert np.allclose(out[0][p], out[1][p], atol=1e-11)
         assert abs(out[0][p][0] - p[0] * 0.25) < 1e-11
+
+
+# ---------------------------------------------------------------- two-level preconditioner
+def _twolevel_case():
+    import workloads as W
+    from oracle import fem as F
+    from oracle import mesh as M
+    w = W.config1b()
+    d = w.dom
+    m = M.build_mesh(d.nx, d.ny, d.nz, d.L, d.h0, w.leaves)
+    A, f, C = F.reduced_system(m, w.rho[m.perm], w.load_nodes, w.load_comp, w.load_val)
+    return m, A.tocsr(), f
+
+
+def test_grid_prolongation_reproduces_linear_fields_at_free_nodes():
+    from oracle import fem as F
+    from oracle import learn as LR
+    m, A, f = _twolevel_case()
+    P = S.grid_prolongation(m, 1)
+    X, Y, Z = LR.grid_shape(m, 1)
+    hv = 1 << (m.L - 1)
+    cx, cy, cz = np.meshgrid((np.arange(X) + 0.5) * hv, (np.arange(Y) + 0.5) * hv, (np.arange(Z) + 0.5) * hv,
+                             indexing="ij")
+    B = np.array([[0.5, -0.25, 1.0], [2.0, 0.75, -1.5], [-0.125, 0.3, 0.6]])
+    cells = np.stack([cx, cy, cz], -1).reshape(-1, 3) @ B.T          # (ncell, 3), cell-major
+    nodal = m.nodes[F.free_nodes(m)].astype(np.float64) @ B.T
+    np.testing.assert_allclose(P @ cells.ravel(), nodal.ravel(), rtol=1e-12, atol=1e-12 * np.abs(nodal).max())
+
+
+def test_galerkin_correction_is_exact_on_the_coarse_space():
+    """If u* = P c, then P (P^T A P)^-1 P^T A u* = u* (Galerkin projection)."""
+    m, A, f = _twolevel_case()
+    P = S.grid_prolongation(m, 0)
+    c = np.random.default_rng(3).standard_normal(P.shape[1])
+    us = P @ c
+    got = S.coarse_correction(A, P)(A @ us)
+    assert np.abs(got - us).max() <= 1e-8 * np.abs(us).max()
+
+
+def test_twolevel_preconditioner_is_spd_and_cuts_iterations():
+    m, A, f = _twolevel_case()
+    P = S.grid_prolongation(m, 1)
+    dinv = 1.0 / A.diagonal()
+    cc = S.coarse_correction(A, P)
+    Minv = lambda r: dinv * r + cc(r)
+    rng = np.random.default_rng(4)
+    a, b = rng.standard_normal(A.shape[0]), rng.standard_normal(A.shape[0])
+    assert a @ Minv(b) == pytest.approx(b @ Minv(a), rel=1e-8)
+    assert a @ Minv(a) > 0
+    u2, it2, _ = S.twolevel_pcg(A, f, P, rtol=1e-8)
+    u1, it1, _, _ = S.jacobi_pcg(A, f, rtol=1e-8)
+    assert np.linalg.norm(f - A @ u2) <= 1.01e-8 * np.linalg.norm(f)
+    ud = S.direct(A, f)
+    e = u2 - ud
+    assert np.sqrt(e @ (A @ e) / (ud @ (A @ ud))) <= 1e-6
+    assert it2 * 3 <= it1
