@@ -155,3 +155,37 @@ def test_twolevel_preconditioner_is_spd_and_cuts_iterations():
     e = u2 - ud
     assert np.sqrt(e @ (A @ e) / (ud @ (A @ ud))) <= 1e-6
     assert it2 * 3 <= it1
+
+
+def test_cell_transfer_is_exact_for_linear_fields():
+    X, Y, Z = 8, 4, 6
+    T = S.cell_transfer(X, Y, Z)
+    B = np.array([[0.5, -0.25, 1.0], [2.0, 0.75, -1.5], [-0.125, 0.3, 0.6]])
+    def centres(nx, ny, nz, h):
+        cx, cy, cz = np.meshgrid((np.arange(nx) + 0.5) * h, (np.arange(ny) + 0.5) * h, (np.arange(nz) + 0.5) * h,
+                                 indexing="ij")
+        return np.stack([cx, cy, cz], -1).reshape(-1, 3)
+    coarse = centres(X // 2, Y // 2, Z // 2, 2.0) @ B.T
+    fine = centres(X, Y, Z, 1.0) @ B.T
+    np.testing.assert_allclose(T @ coarse.ravel(), fine.ravel(), rtol=1e-12, atol=1e-12)
+
+
+def test_vcycle_is_spd_and_keeps_most_of_the_coarse_gain():
+    from oracle import learn as LR
+    w = W.small_truss(seed=4, base=(8, 4, 4), L=2)
+    d = w.dom
+    m = M.build_mesh(d.nx, d.ny, d.nz, d.L, d.h0, w.leaves)
+    A, f, C = F.reduced_system(m, w.rho[m.perm], w.load_nodes, w.load_comp, w.load_val)
+    A = A.tocsr()
+    P = S.grid_prolongation(m, 1)
+    shape = LR.grid_shape(m, 1)
+    V = S.VCycle((P.T @ A @ P).tocsr(), shape, nu=2)
+    assert len(V.levels) == 3
+    rng = np.random.default_rng(9)
+    a, b = rng.standard_normal(P.shape[1]), rng.standard_normal(P.shape[1])
+    assert a @ V.apply(b) == pytest.approx(b @ V.apply(a), rel=1e-8)
+    assert a @ V.apply(a) > 0
+    u, it_v, _ = S.twolevel_vcycle_pcg(A, f, P, shape, nu=2)
+    it_j = S.jacobi_pcg(A, f, rtol=1e-8)[1]
+    assert np.linalg.norm(f - A @ u) <= 1.01e-8 * np.linalg.norm(f)
+    assert 4 * it_v <= it_j
