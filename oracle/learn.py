@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
-The paper has no learned component; this is the spec extension, and every
-choice below is a reading of it:
+The paper has no learned component; it is an extension of the method, and every choice
+below is a reading made for it:
 
 * **Grid.**  The uniform voxel grid of level ``g`` of the base mesh (default 1):
   ``(nx 2^g, ny 2^g, nz 2^g)`` cells of side ``hv = h0 / 2^g``, cell-centred values.
