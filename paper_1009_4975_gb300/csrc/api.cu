@@ -68,7 +68,10 @@ void release(std::vector<void *> &owned) {
 }
 
 // Scalars region layout (doubles): [0, 64) SolveScalars, [64, 80) OcState, [80] compliance,
-// [81] outer rr, [82] ff.
+// [81] outer rr, [82] ff, [90, 92) the two sums of the design difference (Eq. 10).
+// Last-CTA tickets (w.ticket[16]): 0 CG update, 1 FP64 residual, 2 CG start / residual
+// replacement, 3 sensitivity, 4 OC, 5 operator block pass, 6 design difference,
+// 7 multi-vector block pass.  Kernels that share a ticket never run concurrently (one stream).
 constexpr int kScalDoubles = 128;
 SolveScalars *solve_scalars(tm_ctx *c) { return reinterpret_cast<SolveScalars *>(c->w.scal); }
 OcState *oc_state(tm_ctx *c) { return reinterpret_cast<OcState *>(c->w.scal + 64); }
