@@ -26,6 +26,9 @@ Recipes (seeded; the shapes follow the paper's 3D cantilever workloads):
   standing in for a mid-optimisation cantilever design; leaves that meet the
   solid dilated by ``r_amr`` are refined to the finest level, as in the
   paper's refinement criterion (solid elements and a layer around them).
+* ``batch_designs`` -- sixteen truss designs with two levels on bases of 2k x k x k cells
+  (about 50k to 500k leaves), seeds 100-115, for batched solves.
+* ``unet_init`` -- seeded initial parameters of a network given by its parameter shapes.
 """
 from __future__ import annotations
 
