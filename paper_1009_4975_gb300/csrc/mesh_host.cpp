@@ -411,6 +411,7 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
   m.blk_inv.assign(nblk, 0);
   m.lcorner.assign(8 * (size_t)Ne, 0);
   std::vector<int32_t> local_of(Nn, -1);
+  std::vector<int32_t> lcount, lfill;          // per-block CSR scratch of the inverse lists
   int32_t max_local = 0;
   for (int32_t b = 0; b < nblk; ++b) {
     const std::vector<int32_t> &v = bl[b];
@@ -442,30 +443,38 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     m.blk_hang[b + 1] = m.blk_hang[b] + (int32_t)used_h.size();
     for (int64_t e = e0; e < e1; ++e)
       for (int k = 0; k < 8; ++k) m.lcorner[8 * e + k] = (uint16_t)local_of[m.conn[8 * e + k]];
-    std::vector<std::vector<uint16_t>> lists(nloc);
+    // inverse lists, built as one block-local CSR: per local node its slots (element order),
+    // then its fold entries (hanging order)
+    if (used_h.size() >= (size_t)kQuarterBit) return "too many hanging nodes in a block";
+    lcount.assign(nloc + 1, 0);
+    for (int64_t e = e0; e < e1; ++e)
+      for (int k = 0; k < 8; ++k) lcount[local_of[m.conn[8 * e + k]] + 1]++;
+    for (size_t j = 0; j < used_h.size(); ++j)
+      for (int q = 0; q < 4; ++q) {
+        const int32_t mm = m.hang_master[4 * used_h[j] + q];
+        if (mm >= 0) lcount[local_of[mm] + 1]++;
+      }
+    for (int32_t i = 0; i < nloc; ++i) lcount[i + 1] += lcount[i];
+    if (lcount[nloc] > 0xFFFF) return "inverse list of a block too long";
+    m.blk_inv[b] = (int32_t)m.inv.size();
+    m.blk_iptr[b + 1] = m.blk_iptr[b] + nloc + 1;
+    const size_t inv0 = m.inv.size();
+    m.inv.resize(inv0 + lcount[nloc]);
+    lfill.assign(lcount.begin(), lcount.end() - 1);
     for (int64_t e = e0; e < e1; ++e)
       for (int k = 0; k < 8; ++k)   // the slot's offset in the block's per-element result buffer
-        lists[local_of[m.conn[8 * e + k]]].push_back((uint16_t)((e - e0) * kSlotRow + 3 * k));
+        m.inv[inv0 + lfill[local_of[m.conn[8 * e + k]]]++] = (uint16_t)((e - e0) * kSlotRow + 3 * k);
     for (size_t j = 0; j < used_h.size(); ++j) {
       const int32_t h = used_h[j];
       const bool quarter = m.hang_master[4 * h + 2] >= 0;
       for (int q = 0; q < 4; ++q) {
         const int32_t mm = m.hang_master[4 * h + q];
         m.hent.push_back(mm >= 0 ? (uint16_t)local_of[mm] : (uint16_t)0xFFFF);
-        if (mm >= 0) lists[local_of[mm]].push_back((uint16_t)(kFoldBit | (quarter ? kQuarterBit : 0) | j));
+        if (mm >= 0)
+          m.inv[inv0 + lfill[local_of[mm]]++] = (uint16_t)(kFoldBit | (quarter ? kQuarterBit : 0) | j);
       }
     }
-    if (used_h.size() >= (size_t)kQuarterBit) return "too many hanging nodes in a block";
-    m.blk_inv[b] = (int32_t)m.inv.size();
-    m.blk_iptr[b + 1] = m.blk_iptr[b] + nloc + 1;
-    uint32_t off = 0;
-    for (int32_t i = 0; i < nloc; ++i) {
-      m.iptr.push_back((uint16_t)off);
-      m.inv.insert(m.inv.end(), lists[i].begin(), lists[i].end());
-      off += (uint32_t)lists[i].size();
-    }
-    if (off > 0xFFFF) return "inverse list of a block too long";
-    m.iptr.push_back((uint16_t)off);
+    for (int32_t i = 0; i <= nloc; ++i) m.iptr.push_back((uint16_t)lcount[i]);
     m.blk_elem[b + 1] = (int32_t)e1;
     for (int32_t n : order) local_of[n] = -1;
     for (int32_t h : used_h) local_of[m.hang_node[h]] = -1;
@@ -548,7 +557,6 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
   // ---- 8. Jacobi diagonal coefficients: d_{m,c} = sum_e c_e q_{e,m,c}
   {
     std::map<std::array<int64_t, 3>, int> tab_index;
-    std::vector<std::vector<std::pair<int32_t, uint16_t>>> rows(Nn);
     {
       // entry 0: a corner that is its own node in an element without hanging corners
       const double q = m.K0[0];
@@ -557,11 +565,18 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
       tab_index[kq] = 0;
       m.dg_tab.insert(m.dg_tab.end(), {q, q, q});
     }
+    // pass 1: count the entries of every node; elements with hanging corners list their
+    // (node, coefficient triple) entries once, in element order, for pass 2
+    std::vector<int32_t> cnt(Nn + 1, 0);
+    std::vector<int32_t> ex_node;     // entries of elements with hanging corners
+    std::vector<uint16_t> ex_q;
+    std::vector<int32_t> ex_end(Ne, 0);   // prefix end of each element's entries (others: unchanged)
     for (int64_t e = 0; e < Ne; ++e) {
       bool plain = true;
       for (int k = 0; k < 8; ++k) plain &= m.hang_index[m.conn[8 * e + k]] < 0;
       if (plain) {
-        for (int k = 0; k < 8; ++k) rows[m.conn[8 * e + k]].push_back({(int32_t)e, (uint16_t)0});
+        for (int k = 0; k < 8; ++k) cnt[m.conn[8 * e + k] + 1]++;
+        ex_end[e] = (int32_t)ex_node.size();
         continue;
       }
       // corner expansion: (node, weight) pairs
@@ -612,18 +627,39 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
         } else {
           qi = it->second;
         }
-        rows[uniq[u]].push_back({(int32_t)e, (uint16_t)qi});
+        ex_node.push_back(uniq[u]);
+        ex_q.push_back((uint16_t)qi);
+        cnt[uniq[u] + 1]++;
       }
+      ex_end[e] = (int32_t)ex_node.size();
     }
+    // pass 2: fill the node-major CSR in element order
     m.dg_ptr.assign(Nn + 1, 0);
-    for (int64_t n = 0; n < Nn; ++n) m.dg_ptr[n + 1] = m.dg_ptr[n] + (int32_t)rows[n].size();
+    for (int64_t n = 0; n < Nn; ++n) m.dg_ptr[n + 1] = m.dg_ptr[n] + cnt[n + 1];
     m.dg_elem.resize(m.dg_ptr[Nn]);
     m.dg_q.resize(m.dg_ptr[Nn]);
-    for (int64_t n = 0; n < Nn; ++n)
-      for (size_t i = 0; i < rows[n].size(); ++i) {
-        m.dg_elem[m.dg_ptr[n] + i] = rows[n][i].first;
-        m.dg_q[m.dg_ptr[n] + i] = rows[n][i].second;
+    std::vector<int32_t> fill(m.dg_ptr.begin(), m.dg_ptr.end() - 1);
+    int32_t x0 = 0;
+    for (int64_t e = 0; e < Ne; ++e) {
+      if (ex_end[e] == x0) {          // no hanging corners: the 8 corners with the plain triple
+        bool plain = true;
+        for (int k = 0; k < 8; ++k) plain &= m.hang_index[m.conn[8 * e + k]] < 0;
+        if (plain) {
+          for (int k = 0; k < 8; ++k) {
+            const int32_t n = m.conn[8 * e + k];
+            m.dg_elem[fill[n]] = (int32_t)e;
+            m.dg_q[fill[n]++] = 0;
+          }
+          continue;
+        }
       }
+      for (int32_t i = x0; i < ex_end[e]; ++i) {
+        const int32_t n = ex_node[i];
+        m.dg_elem[fill[n]] = (int32_t)e;
+        m.dg_q[fill[n]++] = ex_q[i];
+      }
+      x0 = ex_end[e];
+    }
   }
   return "";
 }
