@@ -48,16 +48,23 @@ static std::vector<int64_t> radix_order(const std::vector<uint64_t> &key) {
   for (uint64_t k : key) mx |= k;
   int bits = 0;
   while (bits < 64 && (mx >> bits)) ++bits;
+  // keys travel with their indices, so every pass streams both arrays in order
   std::vector<int64_t> idx(n), tmp(n);
+  std::vector<uint64_t> k(key), ktmp(n);
   std::iota(idx.begin(), idx.end(), 0);
   const int R = 11, B = 1 << R;
   std::vector<size_t> cnt(B + 1);
   for (int sh = 0; sh < bits; sh += R) {
     std::fill(cnt.begin(), cnt.end(), 0);
-    for (size_t i = 0; i < n; ++i) cnt[((key[idx[i]] >> sh) & (B - 1)) + 1]++;
+    for (size_t i = 0; i < n; ++i) cnt[((k[i] >> sh) & (B - 1)) + 1]++;
     for (int b = 0; b < B; ++b) cnt[b + 1] += cnt[b];
-    for (size_t i = 0; i < n; ++i) tmp[cnt[(key[idx[i]] >> sh) & (B - 1)]++] = idx[i];
+    for (size_t i = 0; i < n; ++i) {
+      const size_t d = cnt[(k[i] >> sh) & (B - 1)]++;
+      tmp[d] = idx[i];
+      ktmp[d] = k[i];
+    }
     idx.swap(tmp);
+    k.swap(ktmp);
   }
   return idx;
 }
@@ -608,11 +615,19 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
         double v[8] = {};
         for (int i = 0; i < np; ++i)
           if (nodes[i] == uniq[u]) v[corner_of[i]] += wts[i];
+        // q_c = v^T K0_cc v over the corners where v is nonzero, in ascending corner order
+        // (the zero terms of the full double sum add nothing)
+        int nz[8], nnz = 0;
+        for (int a = 0; a < 8; ++a)
+          if (v[a] != 0.0) nz[nnz++] = a;
         double q[3];
         for (int c = 0; c < 3; ++c) {
           double s = 0;
-          for (int a = 0; a < 8; ++a)
-            for (int b2 = 0; b2 < 8; ++b2) s += v[a] * v[b2] * m.K0[(3 * a + c) * 24 + 3 * b2 + c];
+          for (int ia = 0; ia < nnz; ++ia)
+            for (int ib = 0; ib < nnz; ++ib) {
+              const int a = nz[ia], b2 = nz[ib];
+              s += v[a] * v[b2] * m.K0[(3 * a + c) * 24 + 3 * b2 + c];
+            }
           q[c] = s;
         }
         std::array<int64_t, 3> kq;
