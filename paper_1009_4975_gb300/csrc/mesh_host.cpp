@@ -394,20 +394,28 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
   const int32_t nblk = (int32_t)blks.size();
   m.nblk = nblk;
   std::vector<std::vector<int32_t>> bl(nblk);   // regular nodes per block, ascending
-  for (int32_t b = 0; b < nblk; ++b) {
-    std::vector<int32_t> &v = bl[b];
-    for (int64_t e = blks[b].e0; e < blks[b].e1; ++e)
-      for (int k = 0; k < 8; ++k) {
-        const int32_t n = m.conn[8 * e + k];
-        const int32_t h = m.hang_index[n];
-        if (h < 0) v.push_back(n);
-        else
-          for (int j = 0; j < 4; ++j)
-            if (m.hang_master[4 * h + j] >= 0) v.push_back(m.hang_master[4 * h + j]);
-      }
-    std::sort(v.begin(), v.end());
-    v.erase(std::unique(v.begin(), v.end()), v.end());
-    for (int32_t n : v) nblocks_of[n]++;
+  {
+    std::vector<int32_t> seen(Nn, -1);          // block that last listed the node
+    for (int32_t b = 0; b < nblk; ++b) {
+      std::vector<int32_t> &v = bl[b];
+      auto add = [&](int32_t n) {
+        if (seen[n] != b) {
+          seen[n] = b;
+          v.push_back(n);
+        }
+      };
+      for (int64_t e = blks[b].e0; e < blks[b].e1; ++e)
+        for (int k = 0; k < 8; ++k) {
+          const int32_t n = m.conn[8 * e + k];
+          const int32_t h = m.hang_index[n];
+          if (h < 0) add(n);
+          else
+            for (int j = 0; j < 4; ++j)
+              if (m.hang_master[4 * h + j] >= 0) add(m.hang_master[4 * h + j]);
+        }
+      std::sort(v.begin(), v.end());
+      for (int32_t n : v) nblocks_of[n]++;
+    }
   }
   m.blk_elem.assign(nblk + 1, 0);
   m.blk_node.assign(nblk + 1, 0);
