@@ -167,6 +167,15 @@ void tm_tables_free(tm_tables *t);
 int tm_tables_operator(const tm_tables *t, int32_t *rec_off, uint8_t *brec, double *modal, int32_t *sh_node,
                        int32_t *sh_ptr, int64_t *rec_bytes);
 
+/* Host-only evaluation of a finite-element field of the tables' mesh at integer points
+ * (the warm start after remeshing: the old displacement at the new mesh's nodes, see
+ * Sec. 5 on mapping the solution onto the updated mesh).  u_full (host, 3 * Nn doubles,
+ * hanging entries interpolated as tm_expand writes them) is trilinear on every leaf and
+ * continuous; out (host, 3 * n_points) receives its value at points (host, 3 * n_points
+ * int32 finest-grid coordinates, inside the closed box; TM_EINVAL otherwise). */
+int tm_tables_transfer(const tm_tables *t, const double *u_full, int64_t n_points, const int32_t *points,
+                       double *out);
+
 /* Host-only form of tm_amr_adapt on built tables (marks and rho on the host, in
  * the tables' element order); same rules, outputs and errors. */
 int tm_tables_adapt(const tm_tables *t, const int8_t *mark, const double *rho, int64_t capacity,

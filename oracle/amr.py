@@ -26,6 +26,12 @@ Readings (the paper states the rules in words only):
   integral of rho over the box is unchanged.
 * Eq. 10: D(rho1, rho2) = int |rho1 - rho2| / int rho1, both designs sampled on
   the finest grid (every cell takes the density of the leaf covering it).
+* Displacement transfer to an adapted mesh (the warm start after remeshing; the paper
+  maps the solution onto the updated mesh): the old finite-element field -- trilinear
+  on each old leaf, hanging values interpolated -- evaluated at the new nodes.  The
+  field is continuous, so any old leaf whose closed box contains a point gives its
+  value; the leaf covering the finest cell at the point's coordinates, clamped to the
+  box, is used.
 """
 from __future__ import annotations
 
@@ -214,3 +220,24 @@ def design_difference(nx, ny, nz, L, leaves1, rho1, leaves2, rho2) -> float:
     a = rasterize(nx, ny, nz, L, leaves1, rho1)
     b = rasterize(nx, ny, nz, L, leaves2, rho2)
     return float(np.abs(a - b).sum() / a.sum())
+
+
+def transfer_field(old: Mesh, u_full_old, points) -> np.ndarray:
+    """(n, 3) values at integer finest-grid `points` (n, 3) of the old mesh's field u_full_old
+    (3 Nn, hanging entries interpolated, i.e. C u)."""
+    u = np.asarray(u_full_old, np.float64).reshape(-1, 3)
+    owner = leaf_owner_map(old.nx, old.ny, old.nz, old.L, old.leaves)
+    ext = np.array(owner.shape)
+    pts = np.asarray(points, np.int64)
+    cell = np.minimum(pts, ext - 1)                      # a cell whose closed box holds the point
+    e = owner[cell[:, 0], cell[:, 1], cell[:, 2]]
+    lf = old.leaves[e]
+    s = (1 << (old.L - lf[:, 3])).astype(np.float64)
+    t = (pts - lf[:, :3]) / s[:, None]                   # local coordinates in [0, 1]
+    out = np.zeros((pts.shape[0], 3))
+    for k in range(8):
+        i, j, m_ = k & 1, (k >> 1) & 1, (k >> 2) & 1
+        w = ((t[:, 0] if i else 1 - t[:, 0]) * (t[:, 1] if j else 1 - t[:, 1])
+             * (t[:, 2] if m_ else 1 - t[:, 2]))
+        out += w[:, None] * u[old.conn[e, k]]
+    return out

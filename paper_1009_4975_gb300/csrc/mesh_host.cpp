@@ -753,6 +753,35 @@ int tm_tables_operator(const tm_tables *t, int32_t *rec_off, uint8_t *brec, doub
   return TM_OK;
 }
 
+int tm_tables_transfer(const tm_tables *t, const double *u_full, int64_t n_points, const int32_t *points,
+                       double *out) {
+  if (!t || !u_full || (n_points > 0 && (!points || !out)) || n_points < 0) return TM_EINVAL;
+  const amr::HostMesh &h = t->m;
+  const int64_t fx = (int64_t)h.nx << h.L, fy = (int64_t)h.ny << h.L, fz = (int64_t)h.nz << h.L;
+  for (int64_t i = 0; i < n_points; ++i) {
+    const int64_t p[3] = {points[3 * i], points[3 * i + 1], points[3 * i + 2]};
+    if (p[0] < 0 || p[1] < 0 || p[2] < 0 || p[0] > fx || p[1] > fy || p[2] > fz) return TM_EINVAL;
+    // a cell whose closed box holds the point, and the leaf covering it
+    const int64_t cx = std::min(p[0], fx - 1), cy = std::min(p[1], fy - 1), cz = std::min(p[2], fz - 1);
+    const int64_t e = h.cellmap[(size_t)((cz * fy + cy) * fx + cx)];
+    const int32_t *l = &h.leaf[4 * e];
+    const double s = (double)(1 << (h.L - l[3]));
+    const double tx = (p[0] - l[0]) / s, ty = (p[1] - l[1]) / s, tz = (p[2] - l[2]) / s;
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 8; ++k) {   // trilinear interpolation of the corner values
+      const double w = ((k & 1) ? tx : 1.0 - tx) * (((k >> 1) & 1) ? ty : 1.0 - ty) * (((k >> 2) & 1) ? tz : 1.0 - tz);
+      const double *uc = u_full + 3 * (size_t)h.conn[8 * e + k];
+      v[0] += w * uc[0];
+      v[1] += w * uc[1];
+      v[2] += w * uc[2];
+    }
+    out[3 * i] = v[0];
+    out[3 * i + 1] = v[1];
+    out[3 * i + 2] = v[2];
+  }
+  return TM_OK;
+}
+
 void tm_tables_free(tm_tables *t) { delete t; }
 
 }  // extern "C"

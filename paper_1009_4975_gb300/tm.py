@@ -64,7 +64,7 @@ class tm_profile_data(C.Structure):
 EXPORTS = ["tm_create", "tm_destroy", "tm_set_stream", "tm_last_error", "tm_mesh_upload", "tm_mesh_tables",
            "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_apply_K_f32_static", "tm_apply_K_f32_multi", "tm_jacobi_diag", "tm_pcg_solve", "tm_pcg_solve_batch", "tm_pcg_solve_multi", "tm_expand",
            "tm_sensitivity", "tm_filter", "tm_oc_update", "tm_amr_mark", "tm_amr_adapt", "tm_design_difference",
-           "tm_tables_adapt", "tm_tables_operator", "tm_unet_param_count", "tm_unet_workspace_floats",
+           "tm_tables_adapt", "tm_tables_operator", "tm_tables_transfer", "tm_unet_param_count", "tm_unet_workspace_floats",
            "tm_unet_forward", "tm_unet_backward", "tm_profile", "tm_profile_read"]
 
 _lib = None
@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH):
         "tm_design_difference": [vp, vp, i64, vp, vp, C.POINTER(dbl)],
         "tm_tables_adapt": [vp, vp, vp, i64, vp, vp, C.POINTER(i64)],
         "tm_tables_operator": [vp, vp, vp, vp, vp, vp, C.POINTER(i64)],
+        "tm_tables_transfer": [vp, vp, i64, vp, vp],
         "tm_unet_forward": [vp, C.POINTER(tm_unet_desc), vp, vp, vp, vp],
         "tm_unet_backward": [vp, C.POINTER(tm_unet_desc), vp, vp, vp, vp, vp, vp],
         "tm_profile": [vp, C.c_int],
@@ -507,6 +508,34 @@ def tm_unet_backward(ctx: Ctx, desc: tm_unet_desc, params, x, dy, dparams, dx, w
                                               _ptr(dparams, torch.float32, None, "dparams"),
                                               None if dx is None else _ptr(dx, torch.float32, None, "dx"),
                                               _ptr(ws, torch.float32, None, "ws")))
+
+
+def tm_tables_transfer(nx, ny, nz, max_level, h0, leaves, u_full, points, dirichlet_faces=1):
+    """Host-only: the field u_full (3 Nn, node order of the tables built from `leaves`) at the
+    integer points (n, 3); returns (n, 3)."""
+    lib = load_library()
+    lv = np.ascontiguousarray(np.asarray(leaves, np.int32).reshape(-1, 4))
+    d = tm_mesh_desc(nx, ny, nz, max_level, h0, lv.shape[0], lv.ctypes.data_as(C.POINTER(C.c_int32)),
+                     dirichlet_faces, 1.0, 1e-9, 0.3, 3.0)
+    info = tm_mesh_info()
+    h = C.c_void_p()
+    err = C.create_string_buffer(512)
+    rc = lib.tm_tables_build(C.byref(d), C.byref(h), C.byref(info), err, 512)
+    if rc != TM_OK:
+        raise TmError(rc, err.value.decode())
+    try:
+        u = np.ascontiguousarray(np.asarray(u_full, np.float64).ravel())
+        if u.size != 3 * info.Nn:
+            raise ValueError("u_full must have 3 Nn entries")
+        pts = np.ascontiguousarray(np.asarray(points, np.int32).reshape(-1, 3))
+        out = np.zeros(pts.shape, np.float64)
+        rc = lib.tm_tables_transfer(h, C.c_void_p(u.ctypes.data), pts.shape[0], C.c_void_p(pts.ctypes.data),
+                                    C.c_void_p(out.ctypes.data))
+        if rc != TM_OK:
+            raise TmError(rc, "tm_tables_transfer: point outside the box")
+        return out
+    finally:
+        lib.tm_tables_free(h)
 
 
 def tm_profile(ctx: Ctx, enable: bool = True):

@@ -68,3 +68,21 @@ def test_adapt_rejects_malformed_marks(tm):
     bad = -np.ones(mu.Ne, np.int8)                      # level 0 cannot derefine
     with pytest.raises(tm.TmError):
         tm.tm_tables_adapt(d.nx, d.ny, d.nz, d.L, d.h0, mu.leaves, bad, np.full(mu.Ne, 0.5))
+
+
+def test_transfer_matches_the_oracle(tm):
+    """The library's host transfer of a constrained field to the nodes of an adapted mesh
+    equals the oracle's evaluation (same trilinear sums, to rounding)."""
+    from oracle import fem as F
+    w, m, rho = _case(1)
+    d = w.dom
+    C = F.constraint_matrix(m)
+    uf = C @ np.random.default_rng(6).standard_normal(C.shape[1])
+    marks = A.final_marks(m, rho, 0.5, 1.6 * d.h_min)
+    l2, _ = A.adapt(m, marks, rho)
+    m2 = M.build_mesh(d.nx, d.ny, d.nz, d.L, d.h0, l2)
+    want = A.transfer_field(m, uf, m2.nodes)
+    got = tm.tm_tables_transfer(d.nx, d.ny, d.nz, d.L, d.h0, m.leaves, uf, m2.nodes)
+    np.testing.assert_allclose(got, want, rtol=1e-14, atol=1e-14 * np.abs(uf).max())
+    with pytest.raises(tm.TmError):
+        tm.tm_tables_transfer(d.nx, d.ny, d.nz, d.L, d.h0, m.leaves, uf, [[-1, 0, 0]])

@@ -272,3 +272,44 @@ def test_design_difference_weights_by_volume():
     vals = np.arange(1.0, 9.0)
     dd = A.design_difference(1, 1, 1, 1, coarse, [4.5], kids, vals)
     assert dd == pytest.approx(np.abs(vals - 4.5).mean() / 4.5, rel=1e-15)
+
+
+# ---------------------------------------------------------------- displacement transfer
+def test_transfer_reproduces_linear_fields_and_is_the_identity_on_the_same_mesh():
+    from oracle import fem as F
+    w = W.config1b(2)
+    d = w.dom
+    m = _mesh(d, w.leaves)
+    B = np.array([[0.5, -0.25, 1.0], [2.0, 0.75, -1.5], [-0.125, 0.3, 0.6]])
+    a = np.array([0.3, -1.2, 2.0])
+    lin = lambda p: a + p.astype(np.float64) @ B.T
+    u_old = lin(m.nodes).ravel()
+    # adapted mesh: refine everything below the finest level
+    fin = np.where(m.leaves[:, 3] < d.L, 1, 0).astype(np.int8)
+    l2, _ = A.adapt(m, fin, np.ones(m.Ne))
+    m2 = _mesh(d, l2)
+    got = A.transfer_field(m, u_old, m2.nodes)
+    np.testing.assert_allclose(got, lin(m2.nodes), rtol=1e-13, atol=1e-13 * np.abs(lin(m2.nodes)).max())
+    # same mesh: the nodal values come back
+    rng = np.random.default_rng(1)
+    uf = F.constraint_matrix(m) @ rng.standard_normal(F.constraint_matrix(m).shape[1])   # a C u field
+    np.testing.assert_allclose(A.transfer_field(m, uf, m.nodes), uf.reshape(-1, 3), rtol=0, atol=1e-14)
+
+
+def test_transfer_of_a_constrained_field_is_continuous_across_leaves():
+    """A point on a face shared by leaves of different levels gets the same value from each."""
+    from oracle import fem as F
+    w = W.config1b(3)
+    d = w.dom
+    m = _mesh(d, w.leaves)
+    C = F.constraint_matrix(m)
+    uf = C @ np.random.default_rng(2).standard_normal(C.shape[1])
+    # evaluate at every node through each leaf that contains it (closed box) and compare
+    u = uf.reshape(-1, 3)
+    for e in range(0, m.Ne, 7):
+        lf = m.leaves[e]
+        s = 1 << (d.L - int(lf[3]))
+        for k in range(8):
+            p = lf[:3] + s * np.array([k & 1, (k >> 1) & 1, (k >> 2) & 1])
+            got = A.transfer_field(m, uf, p[None])[0]
+            np.testing.assert_allclose(got, u[m.conn[e, k]], rtol=1e-13, atol=1e-13 * np.abs(u).max())
