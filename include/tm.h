@@ -205,9 +205,10 @@ int tm_apply_K_f32(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float
 int tm_apply_K_f32_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const float *x_dev, float *y_dev);
 
 /* The FP32 operator of tm_apply_K_f32 for callers that cannot allocate device
- * memory at call time -- code running while a CUDA stream is being captured into
- * a graph, callers under a strict memory budget, or hosts that forbid
- * cudaMalloc/cudaFree after start-up.  It has no counterpart in the paper.
+ * memory when they call: services whose device memory is a fixed pool reserved
+ * at start-up, host applications whose allocator forbids cudaMalloc/cudaFree
+ * after initialisation, and plug-ins that may only use buffers the host hands
+ * them.  It has no counterpart in the paper.
  * It allocates nothing: its scratch (the element coefficients and the
  * shared-node partials) lives in one statically sized device array of 32 MiB
  * that every GPU loading the library holds until the process exits.  The caller
@@ -218,7 +219,8 @@ int tm_apply_K_f32_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const flo
  * call before any stream capture.  All calls share the one array and every call
  * overwrites all of it that it reads, so nothing carries over between calls;
  * calls that overlap on the GPU (other streams, other contexts of the same
- * device) race on it. */
+ * device) race on it, so the caller serialises them.  tm_profile does not time
+ * this entry point (it counts its launches only). */
 int tm_apply_K_f32_static(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float *y_dev);
 
 /* d_dev = diag(C^T K(rho) C) on the A-space (1 at constrained DOFs): the

@@ -331,7 +331,7 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
   std::vector<void *> &wo = w.owned;
   int64_t &WB = w.bytes;
   const size_t nv = 3 * (size_t)m.Nn;
-  w.nred = (int64_t)m.nblk + (m.nsh + m.nh + 255) / 256 + 4 * 152 * 8 + 64;
+  w.nred = (int64_t)m.nblk + (m.nsh + m.nh + 255) / 256 + 4 * 8 * (int64_t)device_sms() + 64;
   TM_CUDA(ctx, alloc(wo, WB, &w.part64, 3 * (size_t)m.nslot));
   TM_CUDA(ctx, alloc(wo, WB, &w.part32, 3 * (size_t)m.nslot));
   TM_CUDA(ctx, alloc(wo, WB, &w.ce64, (size_t)m.Ne));

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kAmrThreads) amr_sweep_balance_kernel(const in
 int amr_grid(int64_t n) {
   int64_t g = (n + kAmrThreads - 1) / kAmrThreads;
   if (g < 1) g = 1;
-  if (g > 152 * 8) g = 152 * 8;
+  if (g > 8 * device_sms()) g = 8 * device_sms();
   return (int)g;
 }
 

@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "element.cuh"
@@ -266,6 +267,17 @@ __global__ void __launch_bounds__(256) apply_shared_kernel(const int32_t *sh_nod
   }
 }
 
+int device_sms() {
+  static std::atomic<int> cached[kStaticMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return 152;
+  int n = cached[dev].load(std::memory_order_relaxed);
+  if (n > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 152;
+  cached[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+
 // One thread per item (the second pass is latency-bound: no grid-stride reuse).
 int item_grid(int64_t n) {
   const int64_t g = (n + 255) / 256;
@@ -275,7 +287,7 @@ int item_grid(int64_t n) {
 int shared_grid(int64_t n) {
   int64_t g = (n + 255) / 256;
   if (g < 1) g = 1;
-  if (g > 1216) g = 1216;  // 8 CTAs per SM on 152 SMs; grid-stride beyond
+  if (g > 8 * device_sms()) g = 8 * device_sms();  // 8 CTAs per SM; grid-stride beyond
   return (int)g;
 }
 
@@ -389,9 +401,11 @@ cudaError_t launch_coeff(const DeviceMesh &m, const Work &w, const double *rho, 
 // address; its address is fetched once per device with that device current.
 static __device__ __align__(256) float g_static_scratch[kStaticElems + 3 * kStaticSlots];
 static float *g_static_ptr[kStaticMaxDevices];
+static std::mutex g_static_mu;   // first calls from several host threads look the address up once
 
 cudaError_t static_scratch(int device, float **ce, float **part) {
   if (device < 0 || device >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
   if (!g_static_ptr[device]) {
     void *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);

@@ -289,7 +289,7 @@ __global__ void mask_kernel(const uint8_t *nflag, double *u, int64_t Nn) {
 int vec_grid(int64_t n) {
   int64_t g = (n + kVecThreads - 1) / kVecThreads;
   if (g < 1) g = 1;
-  if (g > 152 * 8) g = 152 * 8;
+  if (g > 8 * device_sms()) g = 8 * device_sms();
   return (int)g;
 }
 

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kTopThreads) sensitivity_kernel(const int32_t 
 int top_grid(int64_t n) {
   int64_t g = (n + kTopThreads - 1) / kTopThreads;
   if (g < 1) g = 1;
-  if (g > 152 * 8) g = 152 * 8;
+  if (g > 8 * device_sms()) g = 8 * device_sms();
   return (int)g;
 }
 

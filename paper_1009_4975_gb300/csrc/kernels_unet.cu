@@ -18,7 +18,7 @@ constexpr int kT = 256;
 int grid_of(int64_t n) {
   int64_t g = (n + kT - 1) / kT;
   if (g < 1) g = 1;
-  if (g > 152 * 16) g = 152 * 16;
+  if (g > 16 * device_sms()) g = 16 * device_sms();
   return (int)g;
 }
 

@@ -217,6 +217,9 @@ constexpr int64_t kStaticElems = int64_t(1) << 21;   // coefficients: meshes up 
 constexpr int64_t kStaticSlots = int64_t(1) << 21;   // shared-node partials: up to 2,097,152
 constexpr int kStaticMaxDevices = 64;
 cudaError_t static_scratch(int device, float **ce, float **part);
+// Multiprocessors of the current device (queried once per device); grid-stride kernels cap
+// their grids at a multiple of it.
+int device_sms();
 cudaError_t launch_coeff_f32(const DeviceMesh &m, const double *rho, float *ce32, cudaStream_t s);
 cudaError_t apply_residency(const DeviceMesh &m, int *resident32, int *resident64);
 // U-Net layers (kernels_unet.cu)
