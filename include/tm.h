@@ -98,7 +98,18 @@ typedef struct {
   int32_t no_graphs;          /* 0: each batch of check_every CG iterations is a   */
                               /* CUDA graph replayed on a library stream; 1: plain */
                               /* launches on the context's stream                   */
+  int32_t precond;            /* TM_PRECOND_JACOBI (0) or TM_PRECOND_TWOLEVEL (1) */
+  int32_t smooth_sweeps;      /* two-level: l1-Jacobi sweeps before and after the  */
+                              /* coarse-grid step on each level (<= 0: 1)         */
 } tm_solve_opts;
+
+/* Preconditioners of tm_pcg_solve.  TM_PRECOND_JACOBI: the diagonal of A (the rescaling of
+ * Sec. 5).  TM_PRECOND_TWOLEVEL (TM_PREC_MIXED only): the diagonal plus a Galerkin coarse
+ * correction on the vertex lattice of the base grid, applied through a V-cycle (see
+ * tm_coarse_setup).  The paper keeps the slowly converging part of the spectrum from solve
+ * to solve in a recycled Krylov subspace (Sec. 5); the coarse space takes that role here. */
+#define TM_PRECOND_JACOBI 0
+#define TM_PRECOND_TWOLEVEL 1
 
 typedef struct {
   int32_t iterations;         /* CG iterations performed                          */
@@ -107,6 +118,9 @@ typedef struct {
   double seconds;             /* device time of the solve (CUDA events)           */
   int32_t fp64_applies;       /* FP64 operator applications                       */
   int32_t fp32_applies;       /* FP32 operator applications                       */
+  int32_t coarse_levels;      /* two-level: lattice levels of the V-cycle; else 0 */
+  int32_t pad_;
+  double setup_seconds;       /* two-level: host time of the per-density set-up   */
 } tm_solve_stats;
 
 /* Counters of tm_profile / tm_profile_read. */
@@ -262,6 +276,48 @@ int tm_pcg_solve_batch(int n, tm_ctx *const *ctxs, const double *const *rho_dev,
  * load cases are allocated on the first call for the uploaded mesh. */
 int tm_pcg_solve_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const double *f_dev, double *u_dev,
                        const tm_solve_opts *opts, tm_solve_stats *stats);
+
+/* ---- Two-level preconditioner (TM_PRECOND_TWOLEVEL).  An extension with no paper
+ * counterpart: it takes the role of the recycled Krylov subspace of Sec. 5, removing the
+ * smooth, slowly converging part of the error by a projection onto a coarse space.
+ *   M^-1 r = D^-1 r + P0 V_0(P0^T r)
+ * Levels: level 0 is the vertex lattice of the base grid (nx x ny x nz cells of side h0);
+ * level l+1 halves every cell count of level l and exists while all three are even and
+ * level l has more than 64 cells; the last level is solved directly and must have at most
+ * 1200 unknowns (TM_EINVAL otherwise).  A lattice vector of a level with X x Y x Z cells
+ * holds 3 floats per node, node i + (X+1)(j + (Y+1)k), component fastest; entries at nodes
+ * on clamped faces are 0.  P0 is the trilinear interpolation of level-0 values at the free
+ * mesh nodes (the coarse space is nested in the finite-element space because every leaf
+ * lies in one base cell, consistent with the hanging-node interpolation of Eq. 6); level
+ * operators are Galerkin, A_0 = P0^T A P0 and A_(l+1) = P^T A_l P with nodal
+ * interpolation P; V_0 is a V-cycle with `nu` l1-Jacobi sweeps before and after the
+ * coarse-grid step on each level.  All device vectors below are FP32, caller-owned, and
+ * stream-ordered on the context's stream. */
+
+/* Build the level operators for the density rho_dev (Ne doubles, canonical order): cell
+ * matrices from the moments of E(x) over each cell, l1-Jacobi diagonals and the coarsest
+ * dense inverse (on the host; synchronises the stream).  levels_out (host, may be NULL):
+ * the number of levels; shapes_out (host, 3 per level, may be NULL): their cell counts.
+ * tm_pcg_solve with TM_PRECOND_TWOLEVEL does this itself.  TM_EINVAL when the base grid
+ * does not coarsen to a small enough level. */
+int tm_coarse_setup(tm_ctx *ctx, const double *rho_dev, int32_t *levels_out, int32_t *shapes_out);
+
+/* Copy level `level`'s cell matrices (X*Y*Z cells x 24 x 24 floats, cells x fastest, local
+ * DOF 3 q + c of corner q = a + 2b + 4c) into K_dev.  TM_ESTATE before tm_coarse_setup. */
+int tm_coarse_cells(tm_ctx *ctx, int level, float *K_dev);
+
+/* y_dev = A_level x_dev on lattice vectors of that level (TM_ESTATE before set-up). */
+int tm_coarse_apply(tm_ctx *ctx, int level, const float *x_dev, float *y_dev);
+
+/* b0_dev = P0^T r_dev: r_dev an FP32 A-space vector (3 Nn), b0_dev a level-0 lattice vector. */
+int tm_coarse_restrict(tm_ctx *ctx, const float *r_dev, float *b0_dev);
+
+/* y_dev = P0 v0_dev: the FP32 A-space vector of the level-0 lattice vector v0_dev (0 at
+ * hanging and clamped DOFs). */
+int tm_coarse_prolong(tm_ctx *ctx, const float *v0_dev, float *y_dev);
+
+/* x0_dev = V_0(b0_dev) with nu >= 1 sweeps (level-0 lattice vectors). */
+int tm_coarse_vcycle(tm_ctx *ctx, const float *b0_dev, float *x0_dev, int nu);
 
 /* u_full = C u (Eq. 9): hanging DOFs interpolated, Dirichlet DOFs 0. */
 int tm_expand(tm_ctx *ctx, const double *u_dev, double *u_full_dev);

@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <chrono>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "pcg.cuh"
@@ -71,7 +73,8 @@ void release(std::vector<void *> &owned) {
 // [81] outer rr, [82] ff, [90, 92) the two sums of the design difference (Eq. 10).
 // Last-CTA tickets (w.ticket[16]): 0 CG update, 1 FP64 residual, 2 CG start / residual
 // replacement, 3 sensitivity, 4 OC, 5 operator block pass, 6 design difference,
-// 7 multi-vector block pass.  Kernels that share a ticket never run concurrently (one stream).
+// 7 multi-vector block pass, 8 two-level CG scalars.  Kernels that share a ticket never run
+// concurrently (one stream).
 constexpr int kScalDoubles = 128;
 SolveScalars *solve_scalars(tm_ctx *c) { return reinterpret_cast<SolveScalars *>(c->w.scal); }
 OcState *oc_state(tm_ctx *c) { return reinterpret_cast<OcState *>(c->w.scal + 64); }
@@ -206,6 +209,97 @@ __global__ void scatter_loads_kernel(const int64_t *idx, const double *val, int6
   }
 }
 
+void release_coarse(tm_ctx *ctx) {
+  release(ctx->coarse.owned);
+  ctx->coarse = CoarseHierarchy();
+  ctx->coarse_ready = false;
+}
+
+// Tables and buffers of the two-level preconditioner for the uploaded mesh (first use).
+int ensure_coarse(tm_ctx *ctx) {
+  CoarseHierarchy &h = ctx->coarse;
+  if (h.nlev > 0) return TM_OK;
+  const HostMesh &hm = ctx->host;
+  std::vector<int> shapes;
+  std::string msg = coarse_shapes(hm, shapes);
+  if (!msg.empty()) return fail(ctx, TM_EINVAL, "two-level preconditioner: " + msg);
+  std::vector<int32_t> cell_elem, cptr, cnode, ncell;
+  std::vector<uint32_t> code;
+  std::vector<double> Q;
+  coarse_tables(hm, cell_elem, cptr, cnode, ncell, code);
+  coarse_moment_matrices(hm.nu, Q);
+  std::vector<void *> &o = h.owned;
+  int64_t &B = h.bytes;
+  TM_CUDA(ctx, upload(o, B, &h.cell_elem, cell_elem));
+  TM_CUDA(ctx, upload(o, B, &h.cptr, cptr));
+  TM_CUDA(ctx, upload(o, B, &h.cnode, cnode));
+  TM_CUDA(ctx, upload(o, B, &h.ncell, ncell));
+  TM_CUDA(ctx, upload(o, B, &h.code, code));
+  TM_CUDA(ctx, upload(o, B, &h.Q, Q));
+  const int nlev = (int)shapes.size() / 3;
+  for (int l = 0; l < nlev; ++l) {
+    CoarseLevel &c = h.lev[l];
+    c.X = shapes[3 * l]; c.Y = shapes[3 * l + 1]; c.Z = shapes[3 * l + 2];
+    c.nodes = (c.X + 1) * (c.Y + 1) * (c.Z + 1);
+    c.H = std::ldexp(hm.h0, l);
+    const size_t cells = (size_t)c.X * c.Y * c.Z, n3 = 3 * (size_t)c.nodes;
+    TM_CUDA(ctx, alloc(o, B, &c.mom, 27 * cells));
+    TM_CUDA(ctx, alloc(o, B, &c.K, 576 * cells));
+    TM_CUDA(ctx, alloc(o, B, &c.dinv, n3));
+    TM_CUDA(ctx, alloc(o, B, &c.b, n3));
+    TM_CUDA(ctx, alloc(o, B, &c.x, n3));
+    TM_CUDA(ctx, alloc(o, B, &c.x2, n3));
+    TM_CUDA(ctx, alloc(o, B, &c.t, n3));
+  }
+  const CoarseLevel &cl = h.lev[nlev - 1];
+  const size_t nc = 3 * (size_t)cl.nodes;
+  TM_CUDA(ctx, alloc(o, B, &h.Kc64, 576 * (size_t)cl.X * cl.Y * cl.Z));
+  TM_CUDA(ctx, alloc(o, B, &h.Ainv, nc * nc));
+  TM_CUDA(ctx, alloc(o, B, &h.part, 24 * (size_t)h.lev[0].X * h.lev[0].Y * h.lev[0].Z));
+  h.faces = hm.dirichlet_faces;
+  h.nlev = nlev;
+  return TM_OK;
+}
+
+// Level operators, smoother diagonals and the coarsest inverse for the density rho.  Host time
+// in *seconds (may be NULL).
+int coarse_setup(tm_ctx *ctx, const double *rho, double *seconds) {
+  const auto t0 = std::chrono::steady_clock::now();
+  int rc = ensure_coarse(ctx);
+  if (rc) return rc;
+  CoarseHierarchy &h = ctx->coarse;
+  TM_CUDA(ctx, coarse_setup_launch(ctx->dm, h, rho, ctx->stream));
+  ctx->launches += 3 * (int64_t)h.nlev - 1;
+  const CoarseLevel &cl = h.lev[h.nlev - 1];
+  h.Kc_host.resize(576 * (size_t)cl.X * cl.Y * cl.Z);
+  TM_CUDA(ctx, cudaMemcpyAsync(h.Kc_host.data(), h.Kc64, h.Kc_host.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  std::vector<float> Ainv;
+  std::string msg = coarse_dense_inverse(h.Kc_host, cl.X, cl.Y, cl.Z, h.faces, Ainv);
+  if (!msg.empty()) return fail(ctx, TM_ENONFINITE, "two-level preconditioner: " + msg);
+  TM_CUDA(ctx, cudaMemcpyAsync(h.Ainv, Ainv.data(), Ainv.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->coarse_ready = true;
+  if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return TM_OK;
+}
+
+// The two-level part of one preconditioner application on the FP32 residual r: P0^T r, the
+// V-cycle, the CG scalars (mode: 0 iteration, 1 start, 2 residual replacement; finish_kernel)
+// and the search direction p from z = D^-1 r + P0 V(P0^T r).
+int enqueue_twolevel(tm_ctx *ctx, int mode, const float *r, float *p, const float *dinv, int nu) {
+  const CoarseHierarchy &h = ctx->coarse;
+  SolveScalars *sc = solve_scalars(ctx);
+  TM_CUDA(ctx, coarse_restrict_launch(ctx->dm, h, r, true, &sc->done, ctx->stream));
+  int nl = 0;
+  TM_CUDA(ctx, coarse_vcycle_launch(h, nu, &sc->done, ctx->stream, &nl));
+  TM_CUDA(ctx, coarse_finish_launch(h, mode, sc, ctx->w.red, ctx->w.ticket + 8, ctx->stream));
+  TM_CUDA(ctx, coarse_pupdate_launch(ctx->dm, h, p, r, dinv, mode, sc, ctx->stream));
+  ctx->launches += 4 + nl;
+  return TM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -237,6 +331,7 @@ int tm_destroy(tm_ctx *ctx) {
   cudaStreamSynchronize(ctx->stream);
   cudaStreamSynchronize(ctx->gstream);
   drop_graphs(ctx);
+  release_coarse(ctx);
   release(ctx->dm.owned);
   release(ctx->w.owned);
   for (auto &pe : ctx->ev_pending) {
@@ -267,6 +362,7 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
   TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   drop_graphs(ctx);
   ctx->has_mesh = false;
+  release_coarse(ctx);
   release(ctx->dm.owned);
   release(ctx->w.owned);
   ctx->dm = DeviceMesh();
@@ -650,20 +746,31 @@ int read_run(tm_ctx *ctx, SolveScalars *s) {
 }
 
 // Enqueue `count` CG iterations on vectors of type T (operator coefficients ce,
-// partials part), solution x of type TX.  Four launches per iteration.
+// partials part), solution x of type TX.  Three launches per iteration with the Jacobi
+// preconditioner; with the two-level one (FP32 only) the coarse step replaces the p update.
 template <typename TX, typename T>
-int enqueue_iterations(tm_ctx *ctx, int count, const T *ce, T *part, TX *x, T *r, T *p, T *q, const T *dinv) {
+int enqueue_iterations(tm_ctx *ctx, int count, const T *ce, T *part, TX *x, T *r, T *p, T *q, const T *dinv,
+                       int precond, int nu) {
   Work &w = ctx->w;
   SolveScalars *sc = solve_scalars(ctx);
   const int64_t n = 3 * ctx->dm.Nn;
   const DeviceMesh &m = ctx->dm;
+  const bool twolevel = precond == TM_PRECOND_TWOLEVEL;
   for (int k = 0; k < count; ++k) {
     int rc = timed_apply_blocks<T>(ctx, ce, p, q, part, w.red, sc, &sc->done);
     if (rc) return rc;
     TM_CUDA(ctx, launch_update_nodes<TX, T>(x, p, q, r, dinv, m.Nn, m.sh_of_node, m.sh_ptr, part, sc, w.red,
-                                            w.ticket, ctx->stream));
+                                            w.ticket, ctx->stream, twolevel));
+    ctx->launches += 1;
+    if constexpr (std::is_same<T, float>::value) {
+      if (twolevel) {
+        rc = enqueue_twolevel(ctx, 0, r, p, dinv, nu);
+        if (rc) return rc;
+        continue;
+      }
+    }
     TM_CUDA(ctx, launch_pupdate<T>(p, r, dinv, n, sc, ctx->stream));
-    ctx->launches += 2;
+    ctx->launches += 1;
   }
   return TM_OK;
 }
@@ -678,11 +785,12 @@ void recycle(tm_ctx *ctx, const tm_ctx::Pending &pe) {
 // A batch of `count` CG iterations as a CUDA graph on the context's own stream,
 // captured once per (vector set, batch size, profiling) and replayed.
 template <typename TX, typename T>
-int batch_graph(tm_ctx *ctx, int count, const T *ce, T *part, TX *x, T *r, T *p, T *q, const T *dinv,
-                tm_ctx::Graph **out) {
+int batch_graph(tm_ctx *ctx, int count, const T *ce, T *part, TX *x, T *r, T *p, T *q, const T *dinv, int precond,
+                int nu, tm_ctx::Graph **out) {
   const void *key[4] = {(const void *)x, (const void *)r, (const void *)ce, (const void *)part};
   for (auto &g : ctx->graphs)
-    if (g.count == count && g.prof == ctx->prof_on && std::memcmp(g.key, key, sizeof(key)) == 0) {
+    if (g.count == count && g.prof == ctx->prof_on && g.precond == precond && g.nu == nu &&
+        std::memcmp(g.key, key, sizeof(key)) == 0) {
       *out = &g;
       return TM_OK;
     }
@@ -707,13 +815,16 @@ int batch_graph(tm_ctx *ctx, int count, const T *ce, T *part, TX *x, T *r, T *p,
   std::memcpy(g.key, key, sizeof(key));
   g.count = count;
   g.prof = ctx->prof_on;
+  g.precond = precond;
+  g.nu = nu;
+  const int64_t launches0 = ctx->launches;
   cudaStream_t user = ctx->stream;
   ctx->stream = ctx->gstream;
   ctx->capturing = true;
   const size_t base = ctx->ev_pending.size();
   cudaError_t e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal);
   int rc = TM_OK;
-  if (e == cudaSuccess) rc = enqueue_iterations<TX, T>(ctx, count, ce, part, x, r, p, q, dinv);
+  if (e == cudaSuccess) rc = enqueue_iterations<TX, T>(ctx, count, ce, part, x, r, p, q, dinv, precond, nu);
   cudaGraph_t graph = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(ctx->gstream, &graph);
   ctx->capturing = false;
@@ -724,7 +835,8 @@ int batch_graph(tm_ctx *ctx, int count, const T *ce, T *part, TX *x, T *r, T *p,
     g.ev.back().graph_owned = true;
   }
   ctx->ev_pending.resize(base);
-  ctx->launches -= 3 * count;   // counted at replay
+  g.launches = (int)(ctx->launches - launches0);
+  ctx->launches = launches0;    // counted at replay
   if (e != cudaSuccess) return fail(ctx, TM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   if (rc) return rc;
   if (e2 != cudaSuccess) return fail(ctx, TM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e2));
@@ -738,13 +850,13 @@ int batch_graph(tm_ctx *ctx, int count, const T *ce, T *part, TX *x, T *r, T *p,
 
 template <typename TX, typename T>
 int run_cg(tm_ctx *ctx, int check_every, bool graphs, int *iters_out, int *nonfinite, const T *ce, T *part, TX *x,
-           T *r, T *p, T *q, const T *dinv) {
+           T *r, T *p, T *q, const T *dinv, int precond = TM_PRECOND_JACOBI, int nu = 1) {
   SolveScalars s;
   int rc = read_run(ctx, &s);
   if (rc) return rc;
   tm_ctx::Graph *g = nullptr;
   if (graphs) {
-    rc = batch_graph<TX, T>(ctx, check_every, ce, part, x, r, p, q, dinv, &g);
+    rc = batch_graph<TX, T>(ctx, check_every, ce, part, x, r, p, q, dinv, precond, nu, &g);
     if (rc) return rc;
   }
   while (!s.done) {
@@ -757,10 +869,10 @@ int run_cg(tm_ctx *ctx, int check_every, bool graphs, int *iters_out, int *nonfi
       TM_CUDA(ctx, cudaGraphLaunch(g->exec, ctx->gstream));
       TM_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->gstream));
       TM_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
-      ctx->launches += 3 * (int64_t)check_every;
+      ctx->launches += g->launches;
       for (const auto &pe : g->ev) ctx->ev_pending.push_back(pe);
     } else {
-      rc = enqueue_iterations<TX, T>(ctx, check_every, ce, part, x, r, p, q, dinv);
+      rc = enqueue_iterations<TX, T>(ctx, check_every, ce, part, x, r, p, q, dinv, precond, nu);
       if (rc) return rc;
     }
     TM_CUDA(ctx, cudaMemcpyAsync(&s, solve_scalars(ctx), sizeof(s), cudaMemcpyDeviceToHost, ctx->stream));
@@ -791,6 +903,12 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
   if (!(opts->rtol > 0) || opts->max_iter < 1) return fail(ctx, TM_EINVAL, "need rtol > 0 and max_iter >= 1");
   if (opts->precision != TM_PREC_FP64 && opts->precision != TM_PREC_MIXED)
     return fail(ctx, TM_EINVAL, "unknown precision");
+  if (opts->precond != TM_PRECOND_JACOBI && opts->precond != TM_PRECOND_TWOLEVEL)
+    return fail(ctx, TM_EINVAL, "unknown preconditioner");
+  if (opts->precond == TM_PRECOND_TWOLEVEL && opts->precision != TM_PREC_MIXED)
+    return fail(ctx, TM_EINVAL, "the two-level preconditioner runs with TM_PREC_MIXED");
+  const bool twolevel = opts->precond == TM_PRECOND_TWOLEVEL;
+  const int nu = opts->smooth_sweeps > 0 ? opts->smooth_sweeps : 1;
   const DeviceMesh &m = ctx->dm;
   Work &w = ctx->w;
   cudaStream_t st = ctx->stream;
@@ -861,6 +979,11 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
     int left = opts->max_iter;
     double rel = 0, scale_old = 0;
     bool first = true;
+    if (twolevel) {
+      rc = coarse_setup(ctx, rho_dev, &out.setup_seconds);
+      if (rc) return rc;
+      out.coarse_levels = ctx->coarse.nlev;
+    }
     TM_CUDA(ctx, cudaMemsetAsync(w.q32, 0, n * sizeof(float), st));
     TM_CUDA(ctx, cudaMemsetAsync(w.x32, 0, n * sizeof(float), st));
     for (int sweep = 0; sweep < 4096; ++sweep) {
@@ -884,17 +1007,25 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
         if (rc) return rc;
         TM_CUDA(ctx, launch_start<float>(w.r, nullptr, scale, w.r32, w.p32, w.dinv32, n, solve_scalars(ctx), w.red,
                                          w.ticket + 2, st));
+        if (twolevel) {
+          rc = enqueue_twolevel(ctx, 1, w.r32, w.p32, w.dinv32, nu);
+          if (rc) return rc;
+        }
         first = false;
       } else {
         TM_CUDA(ctx, launch_replace(w.r, scale, scale / scale_old, w.r32, w.p32, w.dinv32, n, abs_stop, left,
-                                    solve_scalars(ctx), w.red, w.ticket + 2, st));
-        ctx->launches += 1;
+                                    solve_scalars(ctx), w.red, w.ticket + 2, st, twolevel));
+        ctx->launches += twolevel ? 0 : 1;
+        if (twolevel) {
+          rc = enqueue_twolevel(ctx, 2, w.r32, w.p32, w.dinv32, nu);
+          if (rc) return rc;
+        }
       }
       ctx->launches += 1;
       scale_old = scale;
       int it = 0, nf = 0;
       rc = run_cg<float, float>(ctx, check, graphs, &it, &nf, w.ce32, w.part32, w.x32, w.r32, w.p32, w.q32,
-                                w.dinv32);
+                                w.dinv32, twolevel ? TM_PRECOND_TWOLEVEL : TM_PRECOND_JACOBI, nu);
       if (rc) return rc;
       out.iterations += it;
       out.fp32_applies += it;
@@ -925,6 +1056,7 @@ int tm_pcg_solve_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const doubl
   if (!rho_dev || !f_dev || !u_dev || !opts) return fail(ctx, TM_EINVAL, "null pointer");
   if (nrhs < 1 || nrhs > kMaxRhs) return fail(ctx, TM_EINVAL, "nrhs must be in [1, " + std::to_string(kMaxRhs) + "]");
   if (opts->precision != TM_PREC_MIXED) return fail(ctx, TM_EINVAL, "multi-load solves are TM_PREC_MIXED only");
+  if (opts->precond != TM_PRECOND_JACOBI) return fail(ctx, TM_EINVAL, "multi-load solves use the Jacobi preconditioner");
   if (!(opts->rtol > 0) || opts->max_iter < 1) return fail(ctx, TM_EINVAL, "need rtol > 0 and max_iter >= 1");
   const DeviceMesh &m = ctx->dm;
   Work &w = ctx->w;
@@ -1124,4 +1256,90 @@ int tm_oc_update(tm_ctx *ctx, const double *rho_dev, const double *dc_dev, doubl
   return TM_OK;
 }
 
+// ---------------------------------------------------------------- two-level preconditioner
+int tm_coarse_setup(tm_ctx *ctx, const double *rho_dev, int32_t *levels_out, int32_t *shapes_out) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!rho_dev) return fail(ctx, TM_EINVAL, "null pointer");
+  int rc = coarse_setup(ctx, rho_dev, nullptr);
+  if (rc) return rc;
+  const CoarseHierarchy &h = ctx->coarse;
+  if (levels_out) *levels_out = h.nlev;
+  if (shapes_out)
+    for (int l = 0; l < h.nlev; ++l) {
+      shapes_out[3 * l] = h.lev[l].X;
+      shapes_out[3 * l + 1] = h.lev[l].Y;
+      shapes_out[3 * l + 2] = h.lev[l].Z;
+    }
+  return TM_OK;
+}
+
+#define TM_CHECK_COARSE(ctx)                                                                 \
+  do {                                                                                       \
+    if (!(ctx)->coarse_ready) return fail(ctx, TM_ESTATE, "no two-level set-up for this mesh"); \
+  } while (0)
+
+int tm_coarse_cells(tm_ctx *ctx, int level, float *K_dev) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  TM_CHECK_COARSE(ctx);
+  const CoarseHierarchy &h = ctx->coarse;
+  if (level < 0 || level >= h.nlev || !K_dev) return fail(ctx, TM_EINVAL, "bad level or null pointer");
+  const CoarseLevel &c = h.lev[level];
+  TM_CUDA(ctx, cudaMemcpyAsync(K_dev, c.K, 576 * (size_t)c.X * c.Y * c.Z * sizeof(float), cudaMemcpyDeviceToDevice,
+                               ctx->stream));
+  return TM_OK;
+}
+
+int tm_coarse_apply(tm_ctx *ctx, int level, const float *x_dev, float *y_dev) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  TM_CHECK_COARSE(ctx);
+  const CoarseHierarchy &h = ctx->coarse;
+  if (level < 0 || level >= h.nlev || !x_dev || !y_dev) return fail(ctx, TM_EINVAL, "bad level or null pointer");
+  TM_CUDA(ctx, coarse_level_apply_launch(h, level, x_dev, y_dev, ctx->stream));
+  ctx->launches += 1;
+  return TM_OK;
+}
+
+int tm_coarse_restrict(tm_ctx *ctx, const float *r_dev, float *b0_dev) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  TM_CHECK_COARSE(ctx);
+  if (!r_dev || !b0_dev) return fail(ctx, TM_EINVAL, "null pointer");
+  const CoarseHierarchy &h = ctx->coarse;
+  TM_CUDA(ctx, coarse_restrict_launch(ctx->dm, h, r_dev, false, nullptr, ctx->stream));
+  TM_CUDA(ctx, cudaMemcpyAsync(b0_dev, h.lev[0].b, 3 * (size_t)h.lev[0].nodes * sizeof(float),
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+  ctx->launches += 2;
+  return TM_OK;
+}
+
+int tm_coarse_prolong(tm_ctx *ctx, const float *v0_dev, float *y_dev) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  TM_CHECK_COARSE(ctx);
+  if (!v0_dev || !y_dev) return fail(ctx, TM_EINVAL, "null pointer");
+  TM_CUDA(ctx, coarse_prolong_launch(ctx->dm, ctx->coarse, v0_dev, y_dev, ctx->stream));
+  ctx->launches += 1;
+  return TM_OK;
+}
+
+int tm_coarse_vcycle(tm_ctx *ctx, const float *b0_dev, float *x0_dev, int nu) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  TM_CHECK_COARSE(ctx);
+  if (!b0_dev || !x0_dev || nu < 1) return fail(ctx, TM_EINVAL, "null pointer or nu < 1");
+  const CoarseHierarchy &h = ctx->coarse;
+  const size_t bytes = 3 * (size_t)h.lev[0].nodes * sizeof(float);
+  TM_CUDA(ctx, cudaMemcpyAsync(h.lev[0].b, b0_dev, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  TM_CUDA(ctx, coarse_first_sweep_launch(h, ctx->stream));
+  int nl = 0;
+  TM_CUDA(ctx, coarse_vcycle_launch(h, nu, nullptr, ctx->stream, &nl));
+  TM_CUDA(ctx, cudaMemcpyAsync(x0_dev, h.lev[0].x, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  ctx->launches += 1 + nl;
+  return TM_OK;
+}
+
 }  // extern "C"
+

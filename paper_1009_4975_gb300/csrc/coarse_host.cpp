@@ -1,0 +1,206 @@
+// Host tables of the two-level preconditioner (kernels_coarse.cu): the level shapes, which
+// leaves and mesh nodes belong to which base cell, the moment matrices Q_abc of the cell basis
+// and the dense inverse of the coarsest level.  Integer work and small dense algebra only.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "tm_internal.h"
+
+namespace amr {
+
+// Level 0 is the base grid; a level is added while all three cell counts are even and the
+// current level has more than 64 cells.
+std::string coarse_shapes(const HostMesh &m, std::vector<int> &shapes) {
+  shapes.clear();
+  if (m.L > 9) return "node positions in a base cell need max_level <= 9";
+  int X = m.nx, Y = m.ny, Z = m.nz;
+  shapes.insert(shapes.end(), {X, Y, Z});
+  while (!(X % 2 || Y % 2 || Z % 2 || (int64_t)X * Y * Z <= 64)) {
+    X /= 2; Y /= 2; Z /= 2;
+    shapes.insert(shapes.end(), {X, Y, Z});
+    if ((int)shapes.size() / 3 >= kMaxCoarseLevels) break;
+  }
+  const int n = (int)shapes.size() / 3;
+  X = shapes[3 * (n - 1)]; Y = shapes[3 * (n - 1) + 1]; Z = shapes[3 * (n - 1) + 2];
+  const int64_t dofs = 3 * (int64_t)(X + 1) * (Y + 1) * (Z + 1);
+  if (dofs > kMaxCoarsestDofs)
+    return "the base grid " + std::to_string(m.nx) + "x" + std::to_string(m.ny) + "x" + std::to_string(m.nz) +
+           " halves only down to " + std::to_string(X) + "x" + std::to_string(Y) + "x" + std::to_string(Z) +
+           " cells (" + std::to_string(dofs) + " coarsest unknowns, at most " + std::to_string(kMaxCoarsestDofs) +
+           " are solved directly)";
+  return "";
+}
+
+// cell_elem: per base cell (x fastest) the canonical range of its leaves (contiguous in Morton
+// order).  cptr/cnode: per base cell the mesh nodes it owns, i.e. those in its half-open box,
+// the box closed at the upper faces of the domain.  ncell/code: per node its owning cell and its
+// position there (finest units, 10 bits per axis) with bit 31 set for hanging or clamped nodes.
+void coarse_tables(const HostMesh &m, std::vector<int32_t> &cell_elem, std::vector<int32_t> &cptr,
+                   std::vector<int32_t> &cnode, std::vector<int32_t> &ncell, std::vector<uint32_t> &code) {
+  const int X = m.nx, Y = m.ny, Z = m.nz, S = 1 << m.L;
+  const int64_t ncells = (int64_t)X * Y * Z;
+  cell_elem.assign(2 * ncells, 0);
+  for (int64_t e = 0; e < m.Ne;) {
+    const int32_t *l = &m.leaf[4 * e];
+    const int64_t c = (l[0] / S) + X * ((l[1] / S) + (int64_t)Y * (l[2] / S));
+    int64_t e1 = e + 1;
+    while (e1 < m.Ne) {
+      const int32_t *q = &m.leaf[4 * e1];
+      if ((q[0] / S) + X * ((q[1] / S) + (int64_t)Y * (q[2] / S)) != c) break;
+      ++e1;
+    }
+    cell_elem[2 * c] = (int32_t)e;
+    cell_elem[2 * c + 1] = (int32_t)e1;
+    e = e1;
+  }
+  ncell.assign(m.Nn, 0);
+  code.assign(m.Nn, 0);
+  std::vector<int32_t> cnt(ncells + 1, 0);
+  for (int64_t n = 0; n < m.Nn; ++n) {
+    const int32_t *p = &m.node_xyz[3 * n];
+    const int cx = std::min(p[0] / S, X - 1), cy = std::min(p[1] / S, Y - 1), cz = std::min(p[2] / S, Z - 1);
+    const int64_t c = cx + X * (cy + (int64_t)Y * cz);
+    ncell[n] = (int32_t)c;
+    uint32_t cd = (uint32_t)(p[0] - cx * S) | ((uint32_t)(p[1] - cy * S) << 10) | ((uint32_t)(p[2] - cz * S) << 20);
+    if (m.nflag[n]) cd |= 0x80000000u;
+    code[n] = cd;
+    cnt[c + 1]++;
+  }
+  cptr.assign(ncells + 1, 0);
+  for (int64_t c = 0; c < ncells; ++c) cptr[c + 1] = cptr[c] + cnt[c + 1];
+  cnode.assign(m.Nn, 0);
+  std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+  for (int64_t n = 0; n < m.Nn; ++n) cnode[fill[ncell[n]]++] = (int32_t)n;
+}
+
+// Q_abc (27 x 576, entry (3 I + c) * 24 + 3 J + c'): the coefficient of s_x^a s_y^b s_z^c in the
+// D-weighted product of the centred-coordinate gradients of the cell basis functions I and J,
+//   sum over alpha, beta of M[c][c'][alpha][beta] d_alpha phi_I d_beta phi_J,
+// with phi_I(s) = prod_a (1 + sigma_a s_a) / 2 and M the contraction of the isotropic D (E = 1)
+// with the strain-displacement pattern (Voigt order xx, yy, zz, xy, yz, zx).
+void coarse_moment_matrices(double nu, std::vector<double> &Q) {
+  const double lam = nu / ((1 + nu) * (1 - 2 * nu)), mu = 1.0 / (2 * (1 + nu));
+  double D[6][6] = {};
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q) D[p][q] = lam;
+  for (int p = 0; p < 3; ++p) D[p][p] = lam + 2 * mu;
+  for (int p = 3; p < 6; ++p) D[p][p] = mu;
+  // G[p][c][alpha]: strain p = sum over (c, alpha) of G * d_alpha u_c
+  double G[6][3][3] = {};
+  G[0][0][0] = 1; G[1][1][1] = 1; G[2][2][2] = 1;
+  G[3][0][1] = 1; G[3][1][0] = 1;
+  G[4][1][2] = 1; G[4][2][1] = 1;
+  G[5][0][2] = 1; G[5][2][0] = 1;
+  double M[3][3][3][3] = {};
+  for (int c = 0; c < 3; ++c)
+    for (int c2 = 0; c2 < 3; ++c2)
+      for (int al = 0; al < 3; ++al)
+        for (int be = 0; be < 3; ++be) {
+          double s = 0;
+          for (int p = 0; p < 6; ++p)
+            for (int q = 0; q < 6; ++q) s += G[p][c][al] * D[p][q] * G[q][c2][be];
+          M[c][c2][al][be] = s;
+        }
+  // 1D factor of d_alpha phi_I along axis a as a polynomial (c0, c1) in s
+  auto factor = [](int I, int a, int alpha, double out[2]) {
+    const double sg = ((I >> a) & 1) ? 1.0 : -1.0;
+    if (a == alpha) { out[0] = sg / 2; out[1] = 0; }
+    else { out[0] = 0.5; out[1] = sg / 2; }
+  };
+  Q.assign(27 * 576, 0.0);
+  for (int I = 0; I < 8; ++I)
+    for (int J = 0; J < 8; ++J)
+      for (int al = 0; al < 3; ++al)
+        for (int be = 0; be < 3; ++be) {
+          double P[3][3];   // per axis, coefficients of s^0, s^1, s^2 of the product
+          for (int a = 0; a < 3; ++a) {
+            double f[2], g[2];
+            factor(I, a, al, f);
+            factor(J, a, be, g);
+            P[a][0] = f[0] * g[0];
+            P[a][1] = f[0] * g[1] + f[1] * g[0];
+            P[a][2] = f[1] * g[1];
+          }
+          for (int c = 0; c < 3; ++c)
+            for (int c2 = 0; c2 < 3; ++c2) {
+              const double w = M[c][c2][al][be];
+              if (w == 0) continue;
+              const int ent = (3 * I + c) * 24 + 3 * J + c2;
+              for (int z = 0; z < 3; ++z)
+                for (int y = 0; y < 3; ++y)
+                  for (int x = 0; x < 3; ++x) Q[(x + 3 * y + 9 * z) * 576 + ent] += w * P[0][x] * P[1][y] * P[2][z];
+            }
+        }
+}
+
+// Dense inverse of the coarsest level's matrix (assembled from its FP64 cell matrices over the
+// free DOFs) by Cholesky factorisation; returned over all 3 (X+1)(Y+1)(Z+1) DOFs, with zero rows
+// and columns at clamped nodes.
+std::string coarse_dense_inverse(const std::vector<double> &Kc, int X, int Y, int Z, unsigned faces,
+                                 std::vector<float> &Ainv) {
+  const int nodes = (X + 1) * (Y + 1) * (Z + 1), n = 3 * nodes;
+  auto fixed = [&](int i, int j, int k) {
+    return ((faces & 1u) && i == 0) || ((faces & 2u) && i == X) || ((faces & 4u) && j == 0) ||
+           ((faces & 8u) && j == Y) || ((faces & 16u) && k == 0) || ((faces & 32u) && k == Z);
+  };
+  std::vector<int> fmap(n, -1);
+  int nf = 0;
+  for (int I = 0; I < nodes; ++I) {
+    const int i = I % (X + 1), j = (I / (X + 1)) % (Y + 1), k = I / ((X + 1) * (Y + 1));
+    if (!fixed(i, j, k))
+      for (int c = 0; c < 3; ++c) fmap[3 * I + c] = nf++;
+  }
+  std::vector<double> A((size_t)nf * nf, 0.0);
+  for (int cz = 0; cz < Z; ++cz)
+    for (int cy = 0; cy < Y; ++cy)
+      for (int cx = 0; cx < X; ++cx) {
+        const double *K = &Kc[576 * (size_t)(cx + X * (cy + Y * cz))];
+        int dof[24];
+        for (int q = 0; q < 8; ++q) {
+          const int I = (cx + (q & 1)) + (X + 1) * ((cy + ((q >> 1) & 1)) + (Y + 1) * (cz + (q >> 2)));
+          for (int c = 0; c < 3; ++c) dof[3 * q + c] = fmap[3 * I + c];
+        }
+        for (int r = 0; r < 24; ++r)
+          if (dof[r] >= 0)
+            for (int s = 0; s < 24; ++s)
+              if (dof[s] >= 0) A[(size_t)dof[r] * nf + dof[s]] += K[r * 24 + s];
+      }
+  // Cholesky A = L L^T (lower triangle in place)
+  for (int j = 0; j < nf; ++j) {
+    double d = A[(size_t)j * nf + j];
+    for (int k = 0; k < j; ++k) d -= A[(size_t)j * nf + k] * A[(size_t)j * nf + k];
+    if (!(d > 0)) return "the coarsest level's matrix is not positive definite";
+    const double ljj = std::sqrt(d);
+    A[(size_t)j * nf + j] = ljj;
+    for (int i = j + 1; i < nf; ++i) {
+      double s = A[(size_t)i * nf + j];
+      for (int k = 0; k < j; ++k) s -= A[(size_t)i * nf + k] * A[(size_t)j * nf + k];
+      A[(size_t)i * nf + j] = s / ljj;
+    }
+  }
+  // columns of A^-1: solve L L^T x = e_j
+  std::vector<double> inv((size_t)nf * nf), y(nf);
+  for (int j = 0; j < nf; ++j) {
+    for (int i = 0; i < nf; ++i) {
+      double s = i == j ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= A[(size_t)i * nf + k] * y[k];
+      y[i] = s / A[(size_t)i * nf + i];
+    }
+    for (int i = nf - 1; i >= 0; --i) {
+      double s = y[i];
+      for (int k = i + 1; k < nf; ++k) s -= A[(size_t)k * nf + i] * inv[(size_t)k * nf + j];
+      inv[(size_t)i * nf + j] = s / A[(size_t)i * nf + i];
+    }
+  }
+  Ainv.assign((size_t)n * n, 0.f);
+  for (int r = 0; r < n; ++r)
+    if (fmap[r] >= 0)
+      for (int s = 0; s < n; ++s)
+        if (fmap[s] >= 0) Ainv[(size_t)r * n + s] = (float)(0.5 * (inv[(size_t)fmap[r] * nf + fmap[s]] +
+                                                                    inv[(size_t)fmap[s] * nf + fmap[r]]));
+  return "";
+}
+
+}  // namespace amr

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kVecThreads) update_nodes_kernel(TX *x, const 
                                                                    int64_t Nn, const int32_t *sh_of_node,
                                                                    const int32_t *sh_ptr, const T *part,
                                                                    SolveScalars *sc, double *partials,
-                                                                   unsigned int *ticket) {
+                                                                   unsigned int *ticket, int twolevel) {
   if (sc->done) return;
   const double alpha = sc->alpha;
   const T a = (T)alpha;
@@ -116,9 +116,14 @@ __global__ void __launch_bounds__(kVecThreads) update_nodes_kernel(TX *x, const 
     }
     block_sum2<kVecThreads>(s0, s1);
     if (threadIdx.x == 0) {
-      sc->beta = s0 / sc->rz;
-      sc->rz_prev = sc->rz;
-      sc->rz = s0;
+      if (twolevel) {
+        sc->scratch[0] = s0;     // r^T D^-1 r; the coarse term and beta follow (kernels_coarse.cu)
+        sc->rz_prev = sc->rz;    // the rz the current p was built from (a residual replacement needs it)
+      } else {
+        sc->beta = s0 / sc->rz;
+        sc->rz_prev = sc->rz;
+        sc->rz = s0;
+      }
       sc->rr = s1;
       sc->it += 1;
       if (s1 > sc->rrmax) sc->rrmax = s1;
@@ -252,6 +257,8 @@ __global__ void __launch_bounds__(kVecThreads) replace_dots_kernel(const double 
       const double prev = sc->rz_prev * c * c;
       sc->beta = s0 / prev;
       sc->rp = s1 / s0;        // gamma
+      sc->scratch[2] = prev;   // kept for the two-level preconditioner's beta and gamma
+      sc->scratch[3] = s1;
       sc->rz = s0;
       sc->rr = s2;
       sc->rr0 = s2;
@@ -308,18 +315,18 @@ template cudaError_t launch_update<float, float>(float *, const float *, const f
 template <typename TX, typename T>
 cudaError_t launch_update_nodes(TX *x, const T *p, const T *q, T *r, const T *dinv, int64_t Nn,
                                 const int32_t *sh_of_node, const int32_t *sh_ptr, const T *part, SolveScalars *sc,
-                                double *partials, unsigned int *ticket, cudaStream_t s) {
+                                double *partials, unsigned int *ticket, cudaStream_t s, bool twolevel) {
   update_nodes_kernel<TX, T><<<vec_grid(Nn), kVecThreads, 0, s>>>(x, p, q, r, dinv, Nn, sh_of_node, sh_ptr, part, sc,
-                                                                   partials, ticket);
+                                                                   partials, ticket, twolevel ? 1 : 0);
   return cudaGetLastError();
 }
 template cudaError_t launch_update_nodes<double, double>(double *, const double *, const double *, double *,
                                                          const double *, int64_t, const int32_t *, const int32_t *,
                                                          const double *, SolveScalars *, double *, unsigned int *,
-                                                         cudaStream_t);
+                                                         cudaStream_t, bool);
 template cudaError_t launch_update_nodes<float, float>(float *, const float *, const float *, float *, const float *,
                                                        int64_t, const int32_t *, const int32_t *, const float *,
-                                                       SolveScalars *, double *, unsigned int *, cudaStream_t);
+                                                       SolveScalars *, double *, unsigned int *, cudaStream_t, bool);
 
 template <typename T>
 cudaError_t launch_pupdate(T *p, const T *r, const T *dinv, int64_t n, SolveScalars *sc, cudaStream_t s) {
@@ -351,11 +358,11 @@ cudaError_t launch_residual64(const double *f, const double *q, double *r, int64
 
 cudaError_t launch_replace(const double *r64, double scale, double c, float *r, float *p, const float *dinv,
                            int64_t n, double stop_abs_rr, int max_it, SolveScalars *sc, double *partials,
-                           unsigned int *ticket, cudaStream_t s) {
+                           unsigned int *ticket, cudaStream_t s, bool dots_only) {
   replace_dots_kernel<<<vec_grid(n), kVecThreads, 0, s>>>(r64, scale, c, r, p, dinv, n, stop_abs_rr, max_it, sc,
                                                           partials, ticket);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || dots_only) return e;
   replace_p_kernel<<<vec_grid(n), kVecThreads, 0, s>>>(r, p, dinv, n, sc);
   return cudaGetLastError();
 }

@@ -25,7 +25,7 @@ cudaError_t launch_update(TX *x, const T *p, const T *q, T *r, const T *dinv, in
 template <typename TX, typename T>
 cudaError_t launch_update_nodes(TX *x, const T *p, const T *q, T *r, const T *dinv, int64_t Nn,
                                 const int32_t *sh_of_node, const int32_t *sh_ptr, const T *part, SolveScalars *sc,
-                                double *partials, unsigned int *ticket, cudaStream_t s);
+                                double *partials, unsigned int *ticket, cudaStream_t s, bool twolevel = false);
 template <typename T>
 cudaError_t launch_pupdate(T *p, const T *r, const T *dinv, int64_t n, SolveScalars *sc, cudaStream_t s);
 template <typename T>
@@ -37,9 +37,10 @@ cudaError_t launch_correct(double *u, float *d, double scale, int64_t n, cudaStr
 // Residual replacement of the mixed solver: r = scale * r64 (the FP64 true residual),
 // p *= c (the previous run's units to the new ones), then p made orthogonal to r
 // within span{Dinv r} and p = Dinv r + beta p; CG then continues with the kept direction.
+// dots_only: stop after the dot products (the two-level preconditioner builds p itself).
 cudaError_t launch_replace(const double *r64, double scale, double c, float *r, float *p, const float *dinv,
                            int64_t n, double stop_abs_rr, int max_it, SolveScalars *sc, double *partials,
-                           unsigned int *ticket, cudaStream_t s);
+                           unsigned int *ticket, cudaStream_t s, bool dots_only = false);
 cudaError_t launch_mask(const uint8_t *nflag, double *u, int64_t Nn, cudaStream_t s);
 
 }  // namespace amr

@@ -129,6 +129,56 @@ struct DeviceMesh {
   int64_t bytes = 0;
 };
 
+// Two-level preconditioner (kernels_coarse.cu): levels of the uniform vertex lattice, level 0
+// the base grid.  Lattice vectors hold 3 values per node, x fastest, clamped nodes at 0.
+constexpr int kMaxCoarseLevels = 12;
+struct SolveScalars;
+constexpr int kMaxCoarsestDofs = 1200;   // the coarsest level is solved by a dense inverse (host Cholesky)
+struct CoarseLevel {
+  int X = 0, Y = 0, Z = 0, nodes = 0;    // cells per axis, (X+1)(Y+1)(Z+1) nodes
+  double H = 0;                          // cell side
+  double *mom = nullptr;                 // cells x 27 moments of E (FP64)
+  float *K = nullptr;                    // cells x 24 x 24 cell matrices
+  float *dinv = nullptr;                 // 3 * nodes: inverse l1 row sums (0 at clamped nodes)
+  float *b = nullptr, *x = nullptr, *x2 = nullptr, *t = nullptr;   // 3 * nodes each
+};
+struct CoarseHierarchy {
+  int nlev = 0;
+  unsigned faces = 0;                    // the mesh's clamped faces
+  CoarseLevel lev[kMaxCoarseLevels];
+  int32_t *cell_elem = nullptr;          // 2 per base cell: its leaves' canonical range
+  int32_t *cptr = nullptr, *cnode = nullptr;   // per base cell: the mesh nodes it owns (CSR)
+  int32_t *ncell = nullptr;              // per mesh node: its base cell
+  uint32_t *code = nullptr;              // per mesh node: position in the cell, bit 31 = no unknowns
+  double *Q = nullptr;                   // 27 x 576: moment -> cell-matrix coefficients
+  float *part = nullptr;                 // base cells x 24: partial restrictions
+  double *Kc64 = nullptr;                // coarsest level's cell matrices in FP64
+  float *Ainv = nullptr;                 // coarsest level: dense inverse over all its DOFs
+  std::vector<double> Kc_host;           // host copy of Kc64 (inverse formed on the host)
+  std::vector<void *> owned;
+  int64_t bytes = 0;
+};
+// Host side (coarse_host.cpp): level shapes (empty string) or why the mesh has no usable
+// hierarchy; the per-node and per-cell tables; the moment matrices; the coarsest inverse.
+std::string coarse_shapes(const HostMesh &m, std::vector<int> &shapes);
+void coarse_tables(const HostMesh &m, std::vector<int32_t> &cell_elem, std::vector<int32_t> &cptr,
+                   std::vector<int32_t> &cnode, std::vector<int32_t> &ncell, std::vector<uint32_t> &code);
+void coarse_moment_matrices(double nu, std::vector<double> &Q);
+std::string coarse_dense_inverse(const std::vector<double> &Kc, int X, int Y, int Z, unsigned faces,
+                                 std::vector<float> &Ainv);
+cudaError_t coarse_setup_launch(const DeviceMesh &m, CoarseHierarchy &h, const double *rho, cudaStream_t s);
+cudaError_t coarse_restrict_launch(const DeviceMesh &m, const CoarseHierarchy &h, const float *r, bool first_sweep,
+                                   const int *done, cudaStream_t s);
+cudaError_t coarse_vcycle_launch(const CoarseHierarchy &h, int nu, const int *done, cudaStream_t s, int *launches);
+cudaError_t coarse_finish_launch(const CoarseHierarchy &h, int mode, struct SolveScalars *sc, double *partials,
+                                 unsigned int *ticket, cudaStream_t s);
+cudaError_t coarse_pupdate_launch(const DeviceMesh &m, const CoarseHierarchy &h, float *p, const float *r,
+                                  const float *dinv, int mode, const struct SolveScalars *sc, cudaStream_t s);
+cudaError_t coarse_prolong_launch(const DeviceMesh &m, const CoarseHierarchy &h, const float *v, float *y,
+                                  cudaStream_t s);
+cudaError_t coarse_level_apply_launch(const CoarseHierarchy &h, int l, const float *x, float *y, cudaStream_t s);
+cudaError_t coarse_first_sweep_launch(const CoarseHierarchy &h, cudaStream_t s);
+
 // Work buffers of one context (sized for the current mesh).
 struct Work {
   double *part64 = nullptr;    // 3 * nslot, partial sums of shared nodes (FP64 operator)
@@ -165,6 +215,8 @@ struct tm_ctx {
   amr::HostMesh host;
   amr::DeviceMesh dm;
   amr::Work w;
+  amr::CoarseHierarchy coarse;   // two-level preconditioner (allocated on first use per mesh)
+  bool coarse_ready = false;     // its operators match the last density set up
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // profiling (tm_profile): kernel launch count and CUDA-event operator timing
   bool prof_on = false;
@@ -181,6 +233,8 @@ struct tm_ctx {
   struct Graph {
     const void *key[4] = {};
     int count = 0;
+    int precond = 0, nu = 0;   // two-level batches differ from Jacobi batches
+    int launches = 0;          // kernels per replay
     bool prof = false;
     cudaGraphExec_t exec = nullptr;
     std::vector<Pending> ev;

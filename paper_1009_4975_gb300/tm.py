@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libtm.so")
 
 TM_OK, TM_EINVAL, TM_ECUDA, TM_ENOTCONVERGED, TM_ENONFINITE, TM_ETIMEOUT, TM_ENOMEM, TM_ESTATE = range(8)
 TM_PREC_FP64, TM_PREC_MIXED = 0, 1
+TM_PRECOND_JACOBI, TM_PRECOND_TWOLEVEL = 0, 1
 _NAMES = {1: "TM_EINVAL", 2: "TM_ECUDA", 3: "TM_ENOTCONVERGED", 4: "TM_ENONFINITE", 5: "TM_ETIMEOUT",
           6: "TM_ENOMEM", 7: "TM_ESTATE"}
 
@@ -43,12 +44,14 @@ class tm_mesh_info(C.Structure):
 
 class tm_solve_opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
-                ("inner_rtol", C.c_double), ("check_every", C.c_int32), ("no_graphs", C.c_int32)]
+                ("inner_rtol", C.c_double), ("check_every", C.c_int32), ("no_graphs", C.c_int32),
+                ("precond", C.c_int32), ("smooth_sweeps", C.c_int32)]
 
 
 class tm_solve_stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("sweeps", C.c_int32), ("rel_residual", C.c_double),
-                ("seconds", C.c_double), ("fp64_applies", C.c_int32), ("fp32_applies", C.c_int32)]
+                ("seconds", C.c_double), ("fp64_applies", C.c_int32), ("fp32_applies", C.c_int32),
+                ("coarse_levels", C.c_int32), ("pad_", C.c_int32), ("setup_seconds", C.c_double)]
 
 
 class tm_unet_desc(C.Structure):
@@ -65,7 +68,8 @@ EXPORTS = ["tm_create", "tm_destroy", "tm_set_stream", "tm_last_error", "tm_mesh
            "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_apply_K_f32_static", "tm_apply_K_f32_multi", "tm_jacobi_diag", "tm_pcg_solve", "tm_pcg_solve_batch", "tm_pcg_solve_multi", "tm_expand",
            "tm_sensitivity", "tm_filter", "tm_oc_update", "tm_amr_mark", "tm_amr_adapt", "tm_design_difference",
            "tm_tables_adapt", "tm_tables_operator", "tm_tables_transfer", "tm_unet_param_count", "tm_unet_workspace_floats",
-           "tm_unet_forward", "tm_unet_backward", "tm_profile", "tm_profile_read"]
+           "tm_unet_forward", "tm_unet_backward", "tm_profile", "tm_profile_read", "tm_coarse_setup",
+           "tm_coarse_cells", "tm_coarse_apply", "tm_coarse_restrict", "tm_coarse_prolong", "tm_coarse_vcycle"]
 
 _lib = None
 
@@ -107,6 +111,12 @@ def load_library(path: str = LIB_PATH):
         "tm_unet_forward": [vp, C.POINTER(tm_unet_desc), vp, vp, vp, vp],
         "tm_unet_backward": [vp, C.POINTER(tm_unet_desc), vp, vp, vp, vp, vp, vp],
         "tm_profile": [vp, C.c_int],
+        "tm_coarse_setup": [vp, vp, vp, vp],
+        "tm_coarse_cells": [vp, C.c_int, vp],
+        "tm_coarse_apply": [vp, C.c_int, vp, vp],
+        "tm_coarse_restrict": [vp, vp, vp],
+        "tm_coarse_prolong": [vp, vp, vp],
+        "tm_coarse_vcycle": [vp, vp, vp, C.c_int],
         "tm_profile_read": [vp, C.POINTER(tm_profile_data)],
     }
     for name, args in sig.items():
@@ -151,6 +161,7 @@ class Ctx:
         self.handle = handle
         self.device = device
         self.info = None
+        self.coarse = None
 
     def check(self, rc):
         if rc != TM_OK:
@@ -294,9 +305,10 @@ def tm_jacobi_diag(ctx: Ctx, rho, d):
 
 
 def tm_pcg_solve(ctx: Ctx, rho, f, u, rtol=1e-8, max_iter=100000, precision=TM_PREC_FP64, inner_rtol=0.1,
-                 check_every=64, raise_on_error=True, graphs=True) -> dict:
+                 check_every=64, raise_on_error=True, graphs=True, precond=TM_PRECOND_JACOBI,
+                 smooth_sweeps=1) -> dict:
     import torch
-    o = tm_solve_opts(rtol, max_iter, precision, inner_rtol, check_every, 0 if graphs else 1)
+    o = tm_solve_opts(rtol, max_iter, precision, inner_rtol, check_every, 0 if graphs else 1, precond, smooth_sweeps)
     s = tm_solve_stats()
     rc = load_library().tm_pcg_solve(ctx.handle, _elem(ctx, rho, "rho"), _vec(ctx, f, torch.float64, "f"),
                                      _vec(ctx, u, torch.float64, "u"), C.byref(o), C.byref(s))
@@ -546,3 +558,50 @@ def tm_profile_read(ctx: Ctx) -> dict:
     d = tm_profile_data()
     ctx.check(load_library().tm_profile_read(ctx.handle, C.byref(d)))
     return {k: getattr(d, k) for k, _ in tm_profile_data._fields_}
+
+
+# ---------------------------------------------------------------- two-level preconditioner
+def _lattice(ctx: Ctx, level: int) -> int:
+    X, Y, Z = ctx.coarse["shapes"][level]
+    return 3 * (X + 1) * (Y + 1) * (Z + 1)
+
+
+def tm_coarse_setup(ctx: Ctx, rho) -> dict:
+    """Level operators of the two-level preconditioner for rho; returns the levels' cell counts."""
+    lv = C.c_int32(0)
+    sh = (C.c_int32 * 36)()
+    ctx.check(load_library().tm_coarse_setup(ctx.handle, _elem(ctx, rho, "rho"), C.byref(lv), sh))
+    ctx.coarse = {"levels": lv.value, "shapes": [tuple(sh[3 * i:3 * i + 3]) for i in range(lv.value)]}
+    return ctx.coarse
+
+
+def tm_coarse_cells(ctx: Ctx, level: int, K):
+    import torch
+    X, Y, Z = ctx.coarse["shapes"][level]
+    ctx.check(load_library().tm_coarse_cells(ctx.handle, level, _ptr(K, torch.float32, X * Y * Z * 576, "K")))
+
+
+def tm_coarse_apply(ctx: Ctx, level: int, x, y):
+    import torch
+    n = _lattice(ctx, level)
+    ctx.check(load_library().tm_coarse_apply(ctx.handle, level, _ptr(x, torch.float32, n, "x"),
+                                             _ptr(y, torch.float32, n, "y")))
+
+
+def tm_coarse_restrict(ctx: Ctx, r, b0):
+    import torch
+    ctx.check(load_library().tm_coarse_restrict(ctx.handle, _vec(ctx, r, torch.float32, "r"),
+                                                _ptr(b0, torch.float32, _lattice(ctx, 0), "b0")))
+
+
+def tm_coarse_prolong(ctx: Ctx, v0, y):
+    import torch
+    ctx.check(load_library().tm_coarse_prolong(ctx.handle, _ptr(v0, torch.float32, _lattice(ctx, 0), "v0"),
+                                               _vec(ctx, y, torch.float32, "y")))
+
+
+def tm_coarse_vcycle(ctx: Ctx, b0, x0, nu=1):
+    import torch
+    n = _lattice(ctx, 0)
+    ctx.check(load_library().tm_coarse_vcycle(ctx.handle, _ptr(b0, torch.float32, n, "b0"),
+                                              _ptr(x0, torch.float32, n, "x0"), int(nu)))
