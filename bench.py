@@ -2,10 +2,13 @@
 cantilever mesh (base 48x24x24, three refinement levels along a seeded truss, ~2M elements,
 ~5.4M unknowns), through the C ABI of libtm.
 
-One step = one optimisation iteration on the fixed mesh: Jacobi-PCG solve of C^T K(rho) C u = f to
-a relative residual of 1e-8 (FP32 CG with reliable updates: FP64 true-residual replacement after
-every 10x reduction, warm-started from the previous u), expansion u_full = C u, compliance sensitivities, the volume-weighted filter of Eq. 5
-and the OC update.  Metric: GDOF*iter/s = unknowns * CG iterations / solve-step seconds.
+One step = one optimisation iteration on the fixed mesh: PCG solve of C^T K(rho) C u = f to a
+relative residual of 1e-8 (FP32 CG with reliable updates: FP64 true-residual replacement after every
+10x reduction, warm-started from the previous u; preconditioner: Jacobi plus a Galerkin coarse
+correction on the base-grid lattice applied by a V-cycle), expansion u_full = C u, compliance
+sensitivities, the volume-weighted filter of Eq. 5 and the OC update.  Metric: GDOF*iter/s =
+unknowns * CG iterations / step seconds; time to tolerance is reported beside it for the chosen
+solver, the Jacobi mixed solver and FP64 Jacobi-PCG on the same system from the same warm start.
 
 Arms:
   (default)            the GPU library; prints one JSON line (rank 0).
@@ -182,9 +185,11 @@ def run_gpu(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     rmin = w.r_min
 
+    precond = P.TM_PRECOND_TWOLEVEL if args.precond == "twolevel" else P.TM_PRECOND_JACOBI
+
     def step(rho_in, rho_out, prec=P.TM_PREC_MIXED):
-        st = P.tm_pcg_solve(ctx, rho_in, f, u, rtol=1e-8, max_iter=200000, precision=prec, check_every=64,
-                            graphs=not args.no_graphs)
+        st = P.tm_pcg_solve(ctx, rho_in, f, u, rtol=1e-8, max_iter=200000, precision=prec, check_every=args.check_every,
+                            graphs=not args.no_graphs, precond=precond, smooth_sweeps=args.nu)
         P.tm_expand(ctx, u, uf)
         comp = P.tm_sensitivity(ctx, rho_in, uf, dc)
         P.tm_filter(ctx, rho_in, dc, rmin, 0, dch)
@@ -266,15 +271,24 @@ def run_gpu(args):
     u64 = u_first.clone()
     st64 = P.tm_pcg_solve(ctx, rho_first, f, u64, rtol=1e-8, max_iter=args.fp64_iters, precision=P.TM_PREC_FP64,
                           check_every=64, raise_on_error=False)
+    uj = u_first.clone()
+    stj = P.tm_pcg_solve(ctx, rho_first, f, uj, rtol=1e-8, max_iter=200000, precision=P.TM_PREC_MIXED,
+                         check_every=64, raise_on_error=False)
+    jacobi_mixed = {"iterations": stj["iterations"], "time_to_tolerance_ms": 1e3 * stj["seconds"],
+                    "gdof_iter_per_s": nfree * stj["iterations"] / stj["seconds"] / 1e9,
+                    "rel_residual": stj["rel_residual"], "converged": stj["status"] == 0}
     fp64 = {"gdof_iter_per_s": nfree * st64["iterations"] / st64["seconds"] / 1e9,
             "ms_per_iter": 1e3 * st64["seconds"] / max(st64["iterations"], 1),
             "iterations": st64["iterations"], "rel_residual": st64["rel_residual"],
             "converged": st64["status"] == 0, "time_to_tolerance_ms": 1e3 * st64["seconds"],
-            "chosen_same_system": {"iterations": step_iters[0], "time_to_tolerance_ms": step_solve_ms[0]}}
+            "chosen_same_system": {"iterations": step_iters[0], "time_to_tolerance_ms": step_solve_ms[0]},
+            "jacobi_mixed_same_system": jacobi_mixed,
+            "speedup_to_tolerance_chosen_vs_fp64": 1e3 * st64["seconds"] / step_solve_ms[0]}
 
     if rank != 0:
         return
-    precision = precision_report(P, ctx, rho_first, f, u_first, u64) if args.reports else None
+    solver = dict(precond=precond, smooth_sweeps=args.nu)
+    precision = precision_report(P, ctx, rho_first, f, u_first, u64, solver) if args.reports else None
     batch = batch_report(P, W) if (args.batch and args.reports) else None
     adapt = adaptation_timing(P, ctx, cur, d, Ne, dev) if args.reports else None
     peak, peak_kind = _peaks()
@@ -289,8 +303,10 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (operator and CG vectors; f64 true residuals, solution and reductions)",
         "data": "synthetic (seeded octree truss cantilever)",
         "config": {"workload": w.name, "elements": Ne, "nodes": Nn, "unknowns": nfree,
-                   "hanging_nodes": info["n_hanging"], "solver": "mixed: FP32-operator Jacobi-PCG with reliable updates "
-                   "(FP64 true-residual replacement every 10x reduction), rtol 1e-8, warm start", "step": "solve+expand+sensitivity+filter+OC",
+                   "hanging_nodes": info["n_hanging"], "solver": ("mixed: FP32-operator PCG with reliable updates (FP64 true-residual replacement every 10x "
+                   "reduction), rtol 1e-8, warm start; preconditioner " +
+                   (f"Jacobi + Galerkin coarse correction on the base-grid lattice (V-cycle, {args.nu} l1-Jacobi sweeps)"
+                    if precond == P.TM_PRECOND_TWOLEVEL else "Jacobi")), "step": "solve+expand+sensitivity+filter+OC",
                    "l2": "flushed (512 MB write) before every step", "parallelism": f"replicas x{ws}"},
         "time_to_tolerance_ms": solve_ms / args.steps,
         "cg_iterations_per_step": iters / args.steps,
@@ -315,16 +331,18 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
 
 
-def precision_report(P, ctx, rho, f, u0, u64):
-    """Errors of the mixed and FP64 solvers at the bench tolerance (1e-8) on the first timed
+def precision_report(P, ctx, rho, f, u0, u64, solver):
+    """Errors of the chosen and FP64 solvers at the bench tolerance (1e-8) on the first timed
     system, against a solve of the same system to 1e-12 (FP64 residual): energy-norm error of u
-    (FP64 operator), relative compliance error, sensitivity error relative to max |dc|."""
+    (FP64 operator), relative compliance error, sensitivity error relative to max |dc|.  The
+    errors against the oracle's direct solution are measured by the GPU precision tests on
+    meshes the oracle factors."""
     import torch
     ref = u0.clone()
     st_ref = P.tm_pcg_solve(ctx, rho, f, ref, rtol=1e-12, max_iter=400000, precision=P.TM_PREC_MIXED,
-                            raise_on_error=False)
+                            raise_on_error=False, **solver)
     um = u0.clone()
-    P.tm_pcg_solve(ctx, rho, f, um, rtol=1e-8, max_iter=200000, precision=P.TM_PREC_MIXED)
+    P.tm_pcg_solve(ctx, rho, f, um, rtol=1e-8, max_iter=200000, precision=P.TM_PREC_MIXED, **solver)
     uf = torch.zeros_like(f)
     dc = torch.zeros_like(rho)
 
@@ -339,7 +357,7 @@ def precision_report(P, ctx, rho, f, u0, u64):
     e_ref = float(torch.dot(ref, au))
     out = {"reference": "mixed solve of the same system to rel. residual 1e-12",
            "reference_rel_residual": st_ref["rel_residual"]}
-    for name, u in (("mixed_1e-8", um), ("fp64_1e-8", u64)):
+    for name, u in (("chosen_1e-8", um), ("fp64_1e-8", u64)):
         c, dcu = fields(u)
         e = u - ref
         P.tm_apply_K(ctx, rho, e, au)
@@ -530,6 +548,10 @@ def main():
                     help="skip the batched-solve report (16 independent designs)")
     ap.add_argument("--no-reports", dest="reports", action="store_false",
                     help="skip the precision, batch and adaptation reports (profiling runs)")
+    ap.add_argument("--precond", default="twolevel", choices=["twolevel", "jacobi"],
+                    help="preconditioner of the chosen (mixed) solver")
+    ap.add_argument("--nu", type=int, default=1, help="two-level: l1-Jacobi sweeps before and after the coarse step")
+    ap.add_argument("--check-every", type=int, default=64, help="CG iterations per CUDA-graph batch")
     ap.add_argument("--no-graphs", action="store_true",
                     help="plain kernel launches instead of CUDA-graph batches (for launch-list profiling)")
     ap.add_argument("--profile-apply", type=int, default=0,

@@ -5,8 +5,9 @@ Both solvers stop at ||f - A u|| / ||f|| <= 1e-8.  Measured against the direct s
 the energy-norm error of u, the relative error of the compliance c = f^T u and the error of
 the sensitivities dc relative to max |dc|.  FP64 Jacobi-PCG at this tolerance shows errors of
 about 1e-9 (u, dc) and 1e-12 (c) on these meshes; the bounds below are 100x to 1000x that, and
-the mixed solver (FP32 operator and vectors inside FP64 refinement) must meet the same bounds
-as the FP64 solver."""
+the mixed solver (FP32 operator and vectors inside FP64 refinement), with the Jacobi and with
+the two-level preconditioner, must meet the same bounds as the FP64 solver.  A second test checks
+the same at the benchmark's recipe on a mesh the oracle still factors (20,249 elements)."""
 import numpy as np
 import pytest
 
@@ -52,14 +53,14 @@ def test_precisions_along_an_optimisation_run():
     for it in range(SNAPSHOTS[-1] + 1):
         if it in SNAPSHOTS:
             rho_h = rho.cpu().numpy()
-            for prec in (P.TM_PREC_FP64, P.TM_PREC_MIXED):
+            for prec, pc in ((P.TM_PREC_FP64, 0), (P.TM_PREC_MIXED, 0), (P.TM_PREC_MIXED, P.TM_PRECOND_TWOLEVEL)):
                 us = torch.zeros_like(f)
-                st = P.tm_pcg_solve(ctx(), rho, f, us, rtol=1e-8, max_iter=200000, precision=prec)
+                st = P.tm_pcg_solve(ctx(), rho, f, us, rtol=1e-8, max_iter=200000, precision=prec, precond=pc)
                 assert st["status"] == 0
                 P.tm_expand(ctx(), us, uf)
                 comp = P.tm_sensitivity(ctx(), rho, uf, dc)
                 eu, ec, edc = _errors(c, rho_h, c.free(us.cpu().numpy()), dc.cpu().numpy(), comp)
-                report.append((it, prec, st["iterations"], eu, ec, edc))
+                report.append((it, prec + 2 * (pc > 0), st["iterations"], eu, ec, edc))
                 assert eu <= 1e-6 and ec <= 1e-9 and edc <= 1e-6, report[-1]
         # one optimisation step (mixed solve, warm start)
         P.tm_pcg_solve(ctx(), rho, f, u, rtol=1e-8, max_iter=200000, precision=P.TM_PREC_MIXED)
@@ -69,6 +70,28 @@ def test_precisions_along_an_optimisation_run():
         P.tm_oc_update(ctx(), rho, dch, 0.3, 0.2, 0.5, w.rho_min, new)
         rho, new = new, rho
     for r in report:
-        print("snapshot %2d precision %d: %5d iterations, energy err %.2e, c err %.2e, dc err %.2e" % r)
+        print("snapshot %2d solver %d: %5d iterations, energy err %.2e, c err %.2e, dc err %.2e" % r)
     # the design moved: the last snapshot is a different system from the first
     assert float((rho - c.t(c.rho)).abs().max()) > 0.1
+
+
+def test_chosen_solver_against_the_direct_solution_at_the_benchmark_recipe():
+    """The two-level mixed solver (the benchmark's chosen solver) and FP64 Jacobi-PCG at 1e-8 on
+    the 12x6x6 two-level truss cantilever, against the oracle's sparse LU solution."""
+    import torch
+    P = tm()
+    c = case("small_truss")
+    c.upload()
+    rho = c.t(c.rho)
+    f = c.t(c.full(c.f))
+    uf = torch.zeros_like(f)
+    dc = torch.zeros_like(rho)
+    for prec, pc in ((P.TM_PREC_FP64, 0), (P.TM_PREC_MIXED, P.TM_PRECOND_TWOLEVEL)):
+        u = torch.zeros_like(f)
+        st = P.tm_pcg_solve(ctx(), rho, f, u, rtol=1e-8, max_iter=200000, precision=prec, precond=pc)
+        P.tm_expand(ctx(), u, uf)
+        comp = P.tm_sensitivity(ctx(), rho, uf, dc)
+        eu, ec, edc = _errors(c, c.rho, c.free(u.cpu().numpy()), dc.cpu().numpy(), comp)
+        print("small_truss solver %d: %5d iterations, energy err %.2e, c err %.2e, dc err %.2e"
+              % (prec + 2 * (pc > 0), st["iterations"], eu, ec, edc))
+        assert eu <= 1e-6 and ec <= 1e-9 and edc <= 1e-6, (prec, pc, eu, ec, edc)
