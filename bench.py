@@ -291,6 +291,8 @@ def run_gpu(args):
     precision = precision_report(P, ctx, rho_first, f, u_first, u64, solver) if args.reports else None
     batch = batch_report(P, W) if (args.batch and args.reports) else None
     adapt = adaptation_timing(P, ctx, cur, d, Ne, dev) if args.reports else None
+    adaptive = (adaptive_report(P, W, w, solver, args.adaptive_iters, args.remesh_every)
+                if (args.reports and args.adaptive_iters > 0) else None)
     peak, peak_kind = _peaks()
     a_ms = prof["apply32_ms"] / max(prof["apply32_count"], 1)
     algo = ALGO_BYTES_PER_ELEM_F32 * Ne
@@ -316,6 +318,7 @@ def run_gpu(args):
         "precision": precision,
         "batch": batch,
         "adaptation": adapt,
+        "adaptive_loop": adaptive,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "roofline": {"bound": "hbm", "kernel": "apply_blocks_kernel<float> (operator block pass; the partial "
@@ -445,6 +448,80 @@ def adaptation_timing(P, ctx, rho, d, Ne, dev):
             "new_elements": int(leaves.shape[0]), "design_difference": dd, "design_difference_s": dd_s}
 
 
+def adaptive_report(P, W, w, solver, iters, every):
+    """The benchmark's optimisation loop with dynamic adaptation (paper Fig. 1, Sec. 4): `iters` OC
+    iterations (volume fraction 0.2) from the benchmark design, a refinement/derefinement every
+    `every` iterations (marks with rho_s = 0.5, r_AMR = 2 h_min), the displacement transferred to
+    each new mesh on the device as the next warm start.  Two library contexts alternate, so the old
+    mesh stays resident while the new one is built.  Not part of a timed step."""
+    import numpy as np
+    import torch
+    d = w.dom
+    r_amr = 2.0 * d.h_min
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def build(leaves):
+        c = P.tm_create(dev.index, stream=torch.cuda.current_stream())
+        t0 = time.perf_counter()
+        info = P.tm_mesh_upload(c, d.nx, d.ny, d.nz, d.L, d.h0, leaves, w.dirichlet_faces, w.E0, w.Emin, w.nu,
+                                w.penal)
+        up = time.perf_counter() - t0
+        f = torch.zeros(3 * info["Nn"], dtype=torch.float64, device=dev)
+        P.tm_build_rhs(c, w.load_nodes, w.load_comp, w.load_val, f)
+        return c, f, info, up, P.tm_mesh_tables(c)
+
+    wall0 = time.perf_counter()
+    ctx, f, info, _, tabs = build(w.leaves)
+    leaves = np.asarray(w.leaves)
+    rho = torch.as_tensor(w.rho[tabs["perm"]], device=dev)
+    u = torch.zeros_like(f)
+    steps, remeshes = [], []
+    for it in range(iters):
+        st = P.tm_pcg_solve(ctx, rho, f, u, rtol=1e-8, max_iter=200000, precision=P.TM_PREC_MIXED, **solver)
+        uf = torch.zeros_like(f)
+        P.tm_expand(ctx, u, uf)
+        dc = torch.zeros_like(rho)
+        comp = P.tm_sensitivity(ctx, rho, uf, dc)
+        dch = torch.zeros_like(rho)
+        P.tm_filter(ctx, rho, dc, w.r_min, 0, dch)
+        new = torch.zeros_like(rho)
+        chg = P.tm_oc_update(ctx, rho, dch, 0.2, 0.2, 0.5, w.rho_min, new)
+        steps.append({"it": it, "elements": info["Ne"], "unknowns": info["n_free"], "iterations": st["iterations"],
+                      "solve_ms": 1e3 * st["seconds"], "compliance": comp, "change": chg})
+        rho = new
+        if it % every != every - 1 or it == iters - 1:
+            continue
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mk = torch.empty(info["Ne"], dtype=torch.int8, device=dev)
+        P.tm_amr_mark(ctx, rho, 0.5, r_amr, mk)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        new_leaves, new_rho = P.tm_amr_adapt(ctx, mk, rho)
+        t2 = time.perf_counter()
+        ctx2, f2, info2, up, tabs2 = build(new_leaves)
+        t3 = time.perf_counter()
+        pts = torch.as_tensor(tabs2["node_xyz"], device=dev)
+        u2 = torch.zeros(3 * info2["Nn"], dtype=torch.float64, device=dev)
+        P.tm_transfer_displacement(ctx, uf, pts, u2)
+        torch.cuda.synchronize()
+        t4 = time.perf_counter()
+        rho2 = torch.as_tensor(new_rho[tabs2["perm"]], device=dev)
+        dd = P.tm_design_difference(ctx2, rho2, leaves[tabs["perm"]], rho.cpu().numpy())
+        remeshes.append({"after_it": it, "elements_before": info["Ne"], "elements_after": info2["Ne"],
+                         "marks_ms": 1e3 * (t1 - t0), "adapt_host_s": t2 - t1, "upload_s": up,
+                         "transfer_ms": 1e3 * (t4 - t3), "design_difference": dd, "total_s": t4 - t0})
+        P.tm_destroy(ctx)
+        ctx, f, info, u, rho, tabs, leaves = ctx2, f2, info2, u2, rho2, tabs2, np.asarray(new_leaves)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    P.tm_destroy(ctx)
+    return {"iterations": iters, "remesh_every": every, "remeshes": len(remeshes), "wall_s": wall,
+            "solve_s": sum(x["solve_ms"] for x in steps) / 1e3, "remesh_s": sum(r["total_s"] for r in remeshes),
+            "cg_iterations": sum(x["iterations"] for x in steps), "final_compliance": steps[-1]["compliance"],
+            "elements_final": steps[-1]["elements"], "steps": steps, "remesh": remeshes}
+
+
 def run_profile_apply(args):
     """Profiling workload for ncu: upload the benchmark mesh and run K FP32 operator applications."""
     import torch
@@ -550,8 +627,12 @@ def main():
                     help="skip the precision, batch and adaptation reports (profiling runs)")
     ap.add_argument("--precond", default="twolevel", choices=["twolevel", "jacobi"],
                     help="preconditioner of the chosen (mixed) solver")
-    ap.add_argument("--nu", type=int, default=1, help="two-level: l1-Jacobi sweeps before and after the coarse step")
-    ap.add_argument("--check-every", type=int, default=64, help="CG iterations per CUDA-graph batch")
+    ap.add_argument("--nu", type=int, default=2, help="two-level: l1-Jacobi sweeps before and after the coarse step")
+    ap.add_argument("--check-every", type=int, default=8,
+                    help="CG iterations per CUDA-graph batch (iterations enqueued past convergence return at once)")
+    ap.add_argument("--adaptive-iters", type=int, default=60,
+                    help="report: OC iterations of the adaptive loop with remeshing (0: skip)")
+    ap.add_argument("--remesh-every", type=int, default=5, help="report: OC iterations between remeshes")
     ap.add_argument("--no-graphs", action="store_true",
                     help="plain kernel launches instead of CUDA-graph batches (for launch-list profiling)")
     ap.add_argument("--profile-apply", type=int, default=0,

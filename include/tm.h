@@ -190,6 +190,15 @@ int tm_tables_operator(const tm_tables *t, int32_t *rec_off, uint8_t *brec, doub
 int tm_tables_transfer(const tm_tables *t, const double *u_full, int64_t n_points, const int32_t *points,
                        double *out);
 
+/* Device form of tm_tables_transfer on the context's (old) mesh: the field u_full_dev (device,
+ * 3 Nn doubles of the uploaded mesh, hanging entries interpolated, as tm_expand gives it)
+ * evaluated at points_dev (device, 3 * n_points int32 finest-grid coordinates, e.g. the nodes
+ * of the adapted mesh) into out_dev (device, 3 * n_points doubles): the warm start of the solve
+ * after remeshing (Sec. 5 solves a sequence of systems; the paper maps data to the updated mesh,
+ * Sec. 4).  Synchronises the stream; TM_EINVAL if a point lies outside the closed box. */
+int tm_transfer_displacement(tm_ctx *ctx, const double *u_full_dev, int64_t n_points, const int32_t *points_dev,
+                             double *out_dev);
+
 /* Host-only form of tm_amr_adapt on built tables (marks and rho on the host, in
  * the tables' element order); same rules, outputs and errors. */
 int tm_tables_adapt(const tm_tables *t, const int8_t *mark, const double *rho, int64_t capacity,

@@ -227,6 +227,8 @@ int ensure_coarse(tm_ctx *ctx) {
   std::vector<uint32_t> code;
   std::vector<double> Q;
   coarse_tables(hm, cell_elem, cptr, cnode, ncell, code);
+  std::vector<int32_t> seg_ptr, seg_cell, cseg;
+  coarse_segments(cptr, seg_ptr, seg_cell, cseg);
   coarse_moment_matrices(hm.nu, Q);
   std::vector<void *> &o = h.owned;
   int64_t &B = h.bytes;
@@ -235,6 +237,10 @@ int ensure_coarse(tm_ctx *ctx) {
   TM_CUDA(ctx, upload(o, B, &h.cnode, cnode));
   TM_CUDA(ctx, upload(o, B, &h.ncell, ncell));
   TM_CUDA(ctx, upload(o, B, &h.code, code));
+  TM_CUDA(ctx, upload(o, B, &h.seg_ptr, seg_ptr));
+  TM_CUDA(ctx, upload(o, B, &h.seg_cell, seg_cell));
+  TM_CUDA(ctx, upload(o, B, &h.cseg, cseg));
+  h.nseg = (int32_t)seg_cell.size();
   TM_CUDA(ctx, upload(o, B, &h.Q, Q));
   const int nlev = (int)shapes.size() / 3;
   for (int l = 0; l < nlev; ++l) {
@@ -255,7 +261,7 @@ int ensure_coarse(tm_ctx *ctx) {
   const size_t nc = 3 * (size_t)cl.nodes;
   TM_CUDA(ctx, alloc(o, B, &h.Kc64, 576 * (size_t)cl.X * cl.Y * cl.Z));
   TM_CUDA(ctx, alloc(o, B, &h.Ainv, nc * nc));
-  TM_CUDA(ctx, alloc(o, B, &h.part, 24 * (size_t)h.lev[0].X * h.lev[0].Y * h.lev[0].Z));
+  TM_CUDA(ctx, alloc(o, B, &h.part, 24 * (size_t)h.nseg));
   h.faces = hm.dirichlet_faces;
   h.nlev = nlev;
   return TM_OK;
@@ -698,6 +704,24 @@ int tm_design_difference(tm_ctx *ctx, const double *rho_dev, int64_t n_other, co
   TM_CUDA(ctx, e);
   ctx->launches += 2;
   *d_out = out[0] / out[1];
+  return TM_OK;
+}
+
+int tm_transfer_displacement(tm_ctx *ctx, const double *u_full_dev, int64_t n_points, const int32_t *points_dev,
+                             double *out_dev) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (n_points < 0 || !u_full_dev || (n_points > 0 && (!points_dev || !out_dev)))
+    return fail(ctx, TM_EINVAL, "bad arguments");
+  if (n_points == 0) return TM_OK;
+  int *bad = ctx->w.status + 1;
+  TM_CUDA(ctx, cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream));
+  TM_CUDA(ctx, launch_transfer(ctx->dm, u_full_dev, points_dev, n_points, out_dev, bad, ctx->stream));
+  ctx->launches += 1;
+  int nbad = 0;
+  TM_CUDA(ctx, cudaMemcpyAsync(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (nbad) return fail(ctx, TM_EINVAL, std::to_string(nbad) + " transfer points outside the mesh's box");
   return TM_OK;
 }
 

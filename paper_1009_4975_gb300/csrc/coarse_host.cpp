@@ -75,6 +75,25 @@ void coarse_tables(const HostMesh &m, std::vector<int32_t> &cell_elem, std::vect
   for (int64_t n = 0; n < m.Nn; ++n) cnode[fill[ncell[n]]++] = (int32_t)n;
 }
 
+// Segments of the restriction: each cell's node run cut into pieces of at most kSegNodes, so
+// that one warp per segment has balanced work (cells hold 8 to (2^L + 1)^3 nodes).
+void coarse_segments(const std::vector<int32_t> &cptr, std::vector<int32_t> &seg_ptr, std::vector<int32_t> &seg_cell,
+                     std::vector<int32_t> &cseg) {
+  const int64_t ncells = (int64_t)cptr.size() - 1;
+  seg_ptr.clear();
+  seg_cell.clear();
+  cseg.assign(ncells + 1, 0);
+  for (int64_t c = 0; c < ncells; ++c) {
+    cseg[c] = (int32_t)seg_cell.size();
+    for (int32_t p = cptr[c]; p < cptr[c + 1]; p += kSegNodes) {
+      seg_ptr.push_back(p);
+      seg_cell.push_back((int32_t)c);
+    }
+  }
+  cseg[ncells] = (int32_t)seg_cell.size();
+  seg_ptr.push_back(cptr[ncells]);
+}
+
 // Q_abc (27 x 576, entry (3 I + c) * 24 + 3 J + c'): the coefficient of s_x^a s_y^b s_z^c in the
 // D-weighted product of the centred-coordinate gradients of the cell basis functions I and J,
 //   sum over alpha, beta of M[c][c'][alpha][beta] d_alpha phi_I d_beta phi_J,
@@ -180,18 +199,28 @@ std::string coarse_dense_inverse(const std::vector<double> &Kc, int X, int Y, in
       A[(size_t)i * nf + j] = s / ljj;
     }
   }
-  // columns of A^-1: solve L L^T x = e_j
-  std::vector<double> inv((size_t)nf * nf), y(nf);
-  for (int j = 0; j < nf; ++j) {
-    for (int i = 0; i < nf; ++i) {
-      double s = i == j ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) s -= A[(size_t)i * nf + k] * y[k];
-      y[i] = s / A[(size_t)i * nf + i];
+  // Y = L^-1 (lower triangular), row by row: Y[i, :] = (e_i - sum_{k<i} L[i, k] Y[k, :]) / L[i, i];
+  // then A^-1 = Y^T Y, accumulated one row of Y at a time (contiguous inner loops).
+  std::vector<double> Yl((size_t)nf * nf, 0.0), inv((size_t)nf * nf, 0.0);
+  for (int i = 0; i < nf; ++i) {
+    double *yi = &Yl[(size_t)i * nf];
+    yi[i] = 1.0;
+    for (int k = 0; k < i; ++k) {
+      const double l = A[(size_t)i * nf + k];
+      if (l == 0.0) continue;
+      const double *yk = &Yl[(size_t)k * nf];
+      for (int c = 0; c <= k; ++c) yi[c] -= l * yk[c];
     }
-    for (int i = nf - 1; i >= 0; --i) {
-      double s = y[i];
-      for (int k = i + 1; k < nf; ++k) s -= A[(size_t)k * nf + i] * inv[(size_t)k * nf + j];
-      inv[(size_t)i * nf + j] = s / A[(size_t)i * nf + i];
+    const double d = 1.0 / A[(size_t)i * nf + i];
+    for (int c = 0; c <= i; ++c) yi[c] *= d;
+  }
+  for (int k = 0; k < nf; ++k) {
+    const double *yk = &Yl[(size_t)k * nf];
+    for (int r = 0; r <= k; ++r) {
+      const double a = yk[r];
+      if (a == 0.0) continue;
+      double *ir = &inv[(size_t)r * nf];
+      for (int c = 0; c <= k; ++c) ir[c] += a * yk[c];
     }
   }
   Ainv.assign((size_t)n * n, 0.f);

@@ -1,6 +1,7 @@
 // Dynamic mesh adaptation on the device (paper Sec. 4): refinement/derefinement
-// marks, the sibling sweep and the incompatibility sweep; and the design
-// difference of Eq. 10 on the finest grid.
+// marks, the sibling sweep and the incompatibility sweep; the design difference of
+// Eq. 10 on the finest grid; and the transfer of the displacement to the nodes of an
+// adapted mesh (the warm start after remeshing).
 //
 // Marks: +1 refine, 0 keep, -1 derefine.
 //  * mark: element e is solid when rho_e >= rho_s; it is marked +1 when it is
@@ -191,6 +192,51 @@ cudaError_t launch_design_difference(const DeviceMesh &m, const double *rho1, co
   const int64_t ncell = (int64_t)m.fx * m.fy * m.fz;
   design_diff_kernel<<<amr_grid(ncell), kAmrThreads, 0, s>>>(m.cellmap, rho1, map2, rho2, ncell, partials, ticket,
                                                              out);
+  return cudaGetLastError();
+}
+
+// Displacement transfer: the old mesh's finite-element field (u_full: hanging entries
+// interpolated, so the field is continuous and trilinear on each leaf) evaluated at integer
+// finest-grid points.  Each point takes the leaf covering a finest cell whose closed box holds it
+// (coordinates clamped to the last cell), and the trilinear interpolation of that leaf's corner
+// values.  Points outside the closed box are counted in *bad and give 0.
+__global__ void __launch_bounds__(kAmrThreads) transfer_kernel(const int32_t *leaf, const int32_t *conn,
+                                                               const int32_t *cellmap, int fx, int fy, int fz, int L,
+                                                               const double *u_full, const int32_t *pts, int64_t n,
+                                                               double *out, int *bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int px = pts[3 * i], py = pts[3 * i + 1], pz = pts[3 * i + 2];
+    if (px < 0 || py < 0 || pz < 0 || px > fx || py > fy || pz > fz) {
+      atomicAdd(bad, 1);
+      out[3 * i] = out[3 * i + 1] = out[3 * i + 2] = 0.0;
+      continue;
+    }
+    const int e = cell_owner(cellmap, fx, fy, min(px, fx - 1), min(py, fy - 1), min(pz, fz - 1));
+    const int *l = leaf + 4 * (size_t)e;
+    const double s = (double)(1 << (L - l[3]));
+    const double tx = (px - l[0]) / s, ty = (py - l[1]) / s, tz = (pz - l[2]) / s;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const double w = ((k & 1) ? tx : 1.0 - tx) * (((k >> 1) & 1) ? ty : 1.0 - ty) * (((k >> 2) & 1) ? tz : 1.0 - tz);
+      const double *uc = u_full + 3 * (size_t)conn[8 * (size_t)e + k];
+      v0 += w * uc[0];
+      v1 += w * uc[1];
+      v2 += w * uc[2];
+    }
+    out[3 * i] = v0;
+    out[3 * i + 1] = v1;
+    out[3 * i + 2] = v2;
+  }
+}
+
+cudaError_t launch_transfer(const DeviceMesh &m, const double *u_full, const int32_t *pts, int64_t n, double *out,
+                            int *bad, cudaStream_t s) {
+  int64_t g = (n + kAmrThreads - 1) / kAmrThreads;
+  if (g < 1) g = 1;
+  if (g > 8 * device_sms()) g = 8 * device_sms();
+  transfer_kernel<<<(int)g, kAmrThreads, 0, s>>>(m.leaf, m.conn, m.cellmap, m.fx, m.fy, m.fz, m.L, u_full, pts, n, out,
+                                                  bad);
   return cudaGetLastError();
 }
 

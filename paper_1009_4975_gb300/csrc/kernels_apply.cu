@@ -121,7 +121,8 @@ __device__ __forceinline__ void issue_values(const uint4 *rec, const T *x, T *R,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kApplyThreads, sizeof(T) == 4 ? 4 : 2) apply_blocks_kernel(ApplyParams<T> P) {
+__global__ void __launch_bounds__(kApplyThreads, (sizeof(T) == 4 ? 4 : 2) * 256 / kApplyThreads)
+    apply_blocks_kernel(ApplyParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (P.done && *(volatile const int *)P.done) return;
   T *XY = reinterpret_cast<T *>(smem_raw);

@@ -300,18 +300,21 @@ __global__ void __launch_bounds__(kT) level_prolong_kernel(const float *x_c, int
 }
 
 // Coarsest level: x = Ainv b over all of its DOFs (Ainv symmetric, zero rows and columns at
-// clamped DOFs).  One CTA; thread r reads column r (= row r), consecutive threads consecutive
-// addresses.
+// clamped DOFs).  One CTA; one warp per row (lanes stride the row, then a fixed shuffle tree).
 __global__ void __launch_bounds__(1024) dense_solve_kernel(const float *Ainv, const float *b, float *x, int n,
                                                            const int *done) {
   if (done_set(done)) return;
   extern __shared__ float sb[];
   for (int i = threadIdx.x; i < n; i += blockDim.x) sb[i] = b[i];
   __syncthreads();
-  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; r < n; r += nw) {
+    const float *row = Ainv + (int64_t)r * n;
     float s = 0.f;
-    for (int j = 0; j < n; ++j) s = fmaf(Ainv[(int64_t)j * n + r], sb[j], s);
-    x[r] = s;
+    for (int j = lane; j < n; j += 32) s = fmaf(row[j], sb[j], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[r] = s;
   }
 }
 
@@ -327,19 +330,20 @@ __device__ __forceinline__ void trilinear8(uint32_t code, int L, float w[8]) {
     w[q] = ((q & 1) ? tx : 1.f - tx) * ((q & 2) ? ty : 1.f - ty) * ((q & 4) ? tz : 1.f - tz);
 }
 
-// Stage 1 of P0^T r: one warp per base cell sums w_q r over the mesh nodes it owns (a node is
-// owned by the cell holding it in its half-open box, clamped at the upper faces of the domain).
-__global__ void fine_restrict_cells_kernel(const float *r, const int32_t *cptr, const int32_t *cnode,
-                                           const uint32_t *code, int ncell, int L, float *part, const int *done) {
+// Stage 1 of P0^T r: one warp per segment (a run of <= 64 nodes of one base cell) sums w_q r over
+// its nodes; a node belongs to the cell holding it in its half-open box, clamped at the upper
+// faces of the domain.  Lane sums, then a fixed shuffle tree.
+__global__ void fine_restrict_cells_kernel(const float *r, const int32_t *seg_ptr, const int32_t *cnode,
+                                           const uint32_t *code, int nseg, int L, float *part, const int *done) {
   if (done_set(done)) return;
   const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (warp >= ncell) return;
+  if (warp >= nseg) return;
   float acc[24];
 #pragma unroll
   for (int q = 0; q < 24; ++q) acc[q] = 0.f;
-  const int p1 = cptr[warp + 1];
-  for (int p = cptr[warp] + lane; p < p1; p += 32) {
+  const int p1 = seg_ptr[warp + 1];
+  for (int p = seg_ptr[warp] + lane; p < p1; p += 32) {
     const int n = cnode[p];
     const uint32_t cd = code[n];
     if (cd >> 31) continue;
@@ -367,10 +371,11 @@ __global__ void fine_restrict_cells_kernel(const float *r, const int32_t *cptr, 
   }
 }
 
-// Stage 2: each level-0 DOF sums its <= 8 cells' partials (fixed order); with dinv also x = dinv b.
-__global__ void __launch_bounds__(kT) fine_restrict_nodes_kernel(const float *part, int X, int Y, int Z,
-                                                                 unsigned faces, float *b, const float *dinv,
-                                                                 float *x, const int *done) {
+// Stage 2: each level-0 DOF sums the partials of its <= 8 cells' segments (fixed order); with dinv
+// also x = dinv b.
+__global__ void __launch_bounds__(kT) fine_restrict_nodes_kernel(const float *part, const int32_t *cseg, int X,
+                                                                 int Y, int Z, unsigned faces, float *b,
+                                                                 const float *dinv, float *x, const int *done) {
   if (done_set(done)) return;
   const int nodes = (X + 1) * (Y + 1) * (Z + 1);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -386,7 +391,8 @@ __global__ void __launch_bounds__(kT) fine_restrict_nodes_kernel(const float *pa
         for (int cx = i - 1; cx <= i; ++cx) {
           if (cx < 0 || cx >= X) continue;
           const int q = (i - cx) + 2 * (j - cy) + 4 * (k - cz);
-          s += part[24 * (int64_t)(cx + X * (cy + Y * cz)) + 3 * q + c];
+          const int cc = cx + X * (cy + Y * cz);
+          for (int sg = cseg[cc]; sg < cseg[cc + 1]; ++sg) s += part[24 * (int64_t)sg + 3 * q + c];
         }
       }
     }
@@ -522,12 +528,13 @@ cudaError_t coarse_restrict_launch(const DeviceMesh &m, const CoarseHierarchy &h
                                    const int *done, cudaStream_t s) {
   const CoarseLevel &l0 = h.lev[0];
   const int nc0 = l0.X * l0.Y * l0.Z;
-  fine_restrict_cells_kernel<<<grid_for(32 * (int64_t)nc0), kT, 0, s>>>(r, h.cptr, h.cnode, h.code, nc0, m.L, h.part,
-                                                                        done);
+  fine_restrict_cells_kernel<<<grid_for(32 * (int64_t)h.nseg), kT, 0, s>>>(r, h.seg_ptr, h.cnode, h.code, h.nseg, m.L,
+                                                                           h.part, done);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const bool sweep = first_sweep && h.nlev > 1;
-  fine_restrict_nodes_kernel<<<grid_for(3 * (int64_t)l0.nodes), kT, 0, s>>>(h.part, l0.X, l0.Y, l0.Z, h.faces, l0.b,
+  fine_restrict_nodes_kernel<<<grid_for(3 * (int64_t)l0.nodes), kT, 0, s>>>(h.part, h.cseg, l0.X, l0.Y, l0.Z, h.faces,
+                                                                           l0.b,
                                                                            sweep ? l0.dinv : nullptr,
                                                                            sweep ? l0.x2 : nullptr, done);
   return cudaGetLastError();

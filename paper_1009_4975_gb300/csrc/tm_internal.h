@@ -16,7 +16,10 @@ namespace amr {
 // Operator kernel geometry: one CTA per block of consecutive (Morton-ordered)
 // elements.  A block's "local nodes" are the non-hanging nodes its elements
 // touch directly or through a hanging corner's masters.
-constexpr int kBlockElems = 256;     // elements per block (ragged last block)
+#ifndef TM_BLOCK_ELEMS
+#define TM_BLOCK_ELEMS 256
+#endif
+constexpr int kBlockElems = TM_BLOCK_ELEMS;   // elements per block (ragged last block)
 constexpr int kMaxLocal = 1024;      // local nodes per block
 constexpr int kSlotRow = 25;         // per-element row of the operator's result buffer (24 + 1 pad)
 constexpr int kFoldBit = 0x8000;     // inverse-list entry names a hanging node to fold in
@@ -148,10 +151,14 @@ struct CoarseHierarchy {
   CoarseLevel lev[kMaxCoarseLevels];
   int32_t *cell_elem = nullptr;          // 2 per base cell: its leaves' canonical range
   int32_t *cptr = nullptr, *cnode = nullptr;   // per base cell: the mesh nodes it owns (CSR)
+  int32_t nseg = 0;                      // restriction segments: runs of <= 64 of a cell's nodes
+  int32_t *seg_ptr = nullptr;            // nseg + 1: segment s covers cnode[seg_ptr[s], seg_ptr[s+1])
+  int32_t *seg_cell = nullptr;           // nseg: its cell
+  int32_t *cseg = nullptr;               // base cells + 1: cell c's segments [cseg[c], cseg[c+1])
   int32_t *ncell = nullptr;              // per mesh node: its base cell
   uint32_t *code = nullptr;              // per mesh node: position in the cell, bit 31 = no unknowns
   double *Q = nullptr;                   // 27 x 576: moment -> cell-matrix coefficients
-  float *part = nullptr;                 // base cells x 24: partial restrictions
+  float *part = nullptr;                 // segments x 24: partial restrictions
   double *Kc64 = nullptr;                // coarsest level's cell matrices in FP64
   float *Ainv = nullptr;                 // coarsest level: dense inverse over all its DOFs
   std::vector<double> Kc_host;           // host copy of Kc64 (inverse formed on the host)
@@ -163,6 +170,9 @@ struct CoarseHierarchy {
 std::string coarse_shapes(const HostMesh &m, std::vector<int> &shapes);
 void coarse_tables(const HostMesh &m, std::vector<int32_t> &cell_elem, std::vector<int32_t> &cptr,
                    std::vector<int32_t> &cnode, std::vector<int32_t> &ncell, std::vector<uint32_t> &code);
+constexpr int kSegNodes = 64;
+void coarse_segments(const std::vector<int32_t> &cptr, std::vector<int32_t> &seg_ptr, std::vector<int32_t> &seg_cell,
+                     std::vector<int32_t> &cseg);
 void coarse_moment_matrices(double nu, std::vector<double> &Q);
 std::string coarse_dense_inverse(const std::vector<double> &Kc, int X, int Y, int Z, unsigned faces,
                                  std::vector<float> &Ainv);
@@ -297,6 +307,8 @@ cudaError_t launch_apply_multi(const DeviceMesh &m, int nr, const float *ce, con
 // adaptation (kernels_amr.cu)
 cudaError_t launch_amr_mark(const DeviceMesh &m, const double *rho, double rho_solid, double r_amr, int8_t *tmp,
                             int8_t *mark, cudaStream_t s);
+cudaError_t launch_transfer(const DeviceMesh &m, const double *u_full, const int32_t *pts, int64_t n, double *out,
+                            int *bad, cudaStream_t s);
 cudaError_t launch_design_difference(const DeviceMesh &m, const double *rho1, const int32_t *leaves2, int64_t n2,
                                      const double *rho2, int32_t *map2, double *partials, unsigned int *ticket,
                                      double *out, cudaStream_t s);

@@ -69,7 +69,7 @@ EXPORTS = ["tm_create", "tm_destroy", "tm_set_stream", "tm_last_error", "tm_mesh
            "tm_sensitivity", "tm_filter", "tm_oc_update", "tm_amr_mark", "tm_amr_adapt", "tm_design_difference",
            "tm_tables_adapt", "tm_tables_operator", "tm_tables_transfer", "tm_unet_param_count", "tm_unet_workspace_floats",
            "tm_unet_forward", "tm_unet_backward", "tm_profile", "tm_profile_read", "tm_coarse_setup",
-           "tm_coarse_cells", "tm_coarse_apply", "tm_coarse_restrict", "tm_coarse_prolong", "tm_coarse_vcycle"]
+           "tm_coarse_cells", "tm_coarse_apply", "tm_coarse_restrict", "tm_coarse_prolong", "tm_coarse_vcycle", "tm_transfer_displacement"]
 
 _lib = None
 
@@ -117,6 +117,7 @@ def load_library(path: str = LIB_PATH):
         "tm_coarse_restrict": [vp, vp, vp],
         "tm_coarse_prolong": [vp, vp, vp],
         "tm_coarse_vcycle": [vp, vp, vp, C.c_int],
+        "tm_transfer_displacement": [vp, vp, i64, vp, vp],
         "tm_profile_read": [vp, C.POINTER(tm_profile_data)],
     }
     for name, args in sig.items():
@@ -605,3 +606,13 @@ def tm_coarse_vcycle(ctx: Ctx, b0, x0, nu=1):
     n = _lattice(ctx, 0)
     ctx.check(load_library().tm_coarse_vcycle(ctx.handle, _ptr(b0, torch.float32, n, "b0"),
                                               _ptr(x0, torch.float32, n, "x0"), int(nu)))
+
+
+def tm_transfer_displacement(ctx: Ctx, u_full, points, out):
+    """Old field u_full (3 Nn, this context's mesh) at the integer points (n, 3) int32 device
+    tensor into out (3 n doubles, device)."""
+    import torch
+    n = int(points.shape[0])
+    ctx.check(load_library().tm_transfer_displacement(ctx.handle, _vec(ctx, u_full, torch.float64, "u_full"), n,
+                                                      _ptr(points, torch.int32, 3 * n, "points"),
+                                                      _ptr(out, torch.float64, 3 * n, "out")))
