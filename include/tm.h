@@ -418,6 +418,32 @@ int tm_unet_forward(tm_ctx *ctx, const tm_unet_desc *d, const float *params, con
 int tm_unet_backward(tm_ctx *ctx, const tm_unet_desc *d, const float *params, const float *x, const float *dy,
                      float *dparams, float *dx, float *ws);
 
+/* ---- Transfers and optimiser of the learned initial guess (no paper counterpart).  The
+ * voxel grid of level g (0 <= g <= max_level) has X = nx 2^g, Y = ny 2^g, Z = nz 2^g cells
+ * of side h0 / 2^g (at least 2 per axis); voxel arrays are channel-major with z fastest
+ * (c, i, j, k), FP32, device.  P is the trilinear interpolation of cell-centred values at the
+ * mesh nodes, with the lower cell index clamped to [0, n - 2] per axis (linear extrapolation in
+ * the boundary half-cells); P^T is its adjoint on the A-space.  Tables are built on the first
+ * call for a mesh and grid level (host work). */
+
+/* Network input x_dev (4 channels): channel 0 the volume average of rho over each voxel,
+ * channels 1-3 P^T f_dev (f_dev: the A-space load vector, as tm_build_rhs gives it) divided by
+ * s = max |P^T f|, returned in *s_out (host; synchronises the stream).  TM_EINVAL when s = 0. */
+int tm_learn_input(tm_ctx *ctx, const double *rho_dev, const double *f_dev, int g, float *x_dev, double *s_out);
+
+/* u0_dev (A-space FP64, 0 at constrained DOFs) = s P(out_dev): the initial guess from the
+ * network output out_dev (3 channels). */
+int tm_learn_guess(tm_ctx *ctx, const float *out_dev, double s, int g, double *u0_dev);
+
+/* dout_dev (3 channels) = s P^T (au0_dev - f_dev): the gradient of the energy loss
+ * 0.5 u0^T A u0 - f^T u0 with respect to the network output when au0_dev = A u0 (tm_apply_K). */
+int tm_learn_output_grad(tm_ctx *ctx, const double *au0_dev, const double *f_dev, double s, int g, float *dout_dev);
+
+/* One Adam step (Kingma and Ba, 2015) on n FP32 parameters with their gradients, first and
+ * second moment estimates m_dev and v_dev (zero before step 1), step >= 1 counting from 1. */
+int tm_adam_step(tm_ctx *ctx, int64_t n, float *params_dev, const float *grads_dev, float *m_dev, float *v_dev,
+                 int step, float lr, float beta1, float beta2, float eps);
+
 /* Instrumentation (no counterpart in the paper): tm_profile(ctx, 1) resets the
  * counters and starts timing every operator application with a CUDA-event
  * pair on the context's stream (both passes of the operator; applications a CG

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "kernels_apply.cu", "kernels_pcg.cu", "kernels_topopt.cu", "kernels_amr.cu", "kernels_multi.cu", "kernels_unet.cu", "kernels_coarse.cu", "mesh_host.cpp", "coarse_host.cpp"]
+SOURCES = ["api.cu", "kernels_apply.cu", "kernels_pcg.cu", "kernels_topopt.cu", "kernels_amr.cu", "kernels_multi.cu", "kernels_unet.cu", "kernels_coarse.cu", "kernels_learn.cu", "mesh_host.cpp", "coarse_host.cpp"]
 
 
 def nvcc() -> str:

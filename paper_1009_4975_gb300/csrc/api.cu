@@ -70,10 +70,11 @@ void release(std::vector<void *> &owned) {
 }
 
 // Scalars region layout (doubles): [0, 64) SolveScalars, [64, 80) OcState, [80] compliance,
-// [81] outer rr, [82] ff, [90, 92) the two sums of the design difference (Eq. 10).
+// [81] outer rr, [82] ff, [90, 92) the two sums of the design difference (Eq. 10), [92] the load
+// scale of the learned guess's input.
 // Last-CTA tickets (w.ticket[16]): 0 CG update, 1 FP64 residual, 2 CG start / residual
 // replacement, 3 sensitivity, 4 OC, 5 operator block pass, 6 design difference,
-// 7 multi-vector block pass, 8 two-level CG scalars.  Kernels that share a ticket never run
+// 7 multi-vector block pass, 8 two-level CG scalars, 9 load scale of the learned guess.  Kernels that share a ticket never run
 // concurrently (one stream).
 constexpr int kScalDoubles = 128;
 SolveScalars *solve_scalars(tm_ctx *c) { return reinterpret_cast<SolveScalars *>(c->w.scal); }
@@ -215,6 +216,43 @@ void release_coarse(tm_ctx *ctx) {
   ctx->coarse_ready = false;
 }
 
+void release_learn(tm_ctx *ctx) {
+  release(ctx->learn.owned);
+  ctx->learn = LearnTables();
+}
+
+// Voxel grid of level g and its tables for the uploaded mesh (first use, or another g).
+int ensure_learn(tm_ctx *ctx, int g) {
+  const HostMesh &hm = ctx->host;
+  if (g < 0 || g > hm.L) return fail(ctx, TM_EINVAL, "voxel level g must be in [0, max_level]");
+  const int X = hm.nx << g, Y = hm.ny << g, Z = hm.nz << g;
+  if (X < 2 || Y < 2 || Z < 2) return fail(ctx, TM_EINVAL, "the voxel grid needs at least 2 cells per axis");
+  LearnTables &t = ctx->learn;
+  if (t.g == g) return TM_OK;
+  release_learn(ctx);
+  const int hv = 1 << (hm.L - g);
+  std::vector<int32_t> cnt((size_t)X * Y * Z + 1, 0), anchor(hm.Nn);
+  auto lower = [](int p, int n, int h) {
+    const int i = (int)std::floor((double)p / h - 0.5);
+    return i < 0 ? 0 : (i > n - 2 ? n - 2 : i);
+  };
+  for (int64_t n = 0; n < hm.Nn; ++n) {
+    const int32_t *p = &hm.node_xyz[3 * n];
+    const int a = (lower(p[0], X, hv) * Y + lower(p[1], Y, hv)) * Z + lower(p[2], Z, hv);
+    anchor[n] = a;
+    cnt[a + 1]++;
+  }
+  for (size_t i = 1; i < cnt.size(); ++i) cnt[i] += cnt[i - 1];
+  std::vector<int32_t> vnode(hm.Nn), fill(cnt.begin(), cnt.end() - 1);
+  for (int64_t n = 0; n < hm.Nn; ++n) vnode[fill[anchor[n]]++] = (int32_t)n;
+  TM_CUDA(ctx, upload(t.owned, t.bytes, &t.nxyz, hm.node_xyz));
+  TM_CUDA(ctx, upload(t.owned, t.bytes, &t.vptr, cnt));
+  TM_CUDA(ctx, upload(t.owned, t.bytes, &t.vnode, vnode));
+  TM_CUDA(ctx, alloc(t.owned, t.bytes, &t.pf, 3 * (size_t)X * Y * Z));
+  t.g = g; t.X = X; t.Y = Y; t.Z = Z; t.hv = hv;
+  return TM_OK;
+}
+
 // Tables and buffers of the two-level preconditioner for the uploaded mesh (first use).
 int ensure_coarse(tm_ctx *ctx) {
   CoarseHierarchy &h = ctx->coarse;
@@ -338,6 +376,7 @@ int tm_destroy(tm_ctx *ctx) {
   cudaStreamSynchronize(ctx->gstream);
   drop_graphs(ctx);
   release_coarse(ctx);
+  release_learn(ctx);
   release(ctx->dm.owned);
   release(ctx->w.owned);
   for (auto &pe : ctx->ev_pending) {
@@ -369,6 +408,7 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
   drop_graphs(ctx);
   ctx->has_mesh = false;
   release_coarse(ctx);
+  release_learn(ctx);
   release(ctx->dm.owned);
   release(ctx->w.owned);
   ctx->dm = DeviceMesh();
@@ -722,6 +762,59 @@ int tm_transfer_displacement(tm_ctx *ctx, const double *u_full_dev, int64_t n_po
   TM_CUDA(ctx, cudaMemcpyAsync(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (nbad) return fail(ctx, TM_EINVAL, std::to_string(nbad) + " transfer points outside the mesh's box");
+  return TM_OK;
+}
+
+int tm_learn_input(tm_ctx *ctx, const double *rho_dev, const double *f_dev, int g, float *x_dev, double *s_out) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!rho_dev || !f_dev || !x_dev) return fail(ctx, TM_EINVAL, "null pointer");
+  int rc = ensure_learn(ctx, g);
+  if (rc) return rc;
+  double *s_dev = scal_at(ctx, 92);
+  TM_CUDA(ctx, learn_input_launch(ctx->dm, ctx->learn, rho_dev, f_dev, ctx->learn.pf, ctx->w.red, ctx->w.ticket + 9,
+                                  s_dev, x_dev, ctx->stream));
+  ctx->launches += 4;
+  double s = 0;
+  rc = read_scalar(ctx, s_dev, &s);
+  if (rc) return rc;
+  if (!(s > 0) || !std::isfinite(s)) return fail(ctx, TM_EINVAL, "the load restricts to zero on the voxel grid");
+  if (s_out) *s_out = s;
+  return TM_OK;
+}
+
+int tm_learn_guess(tm_ctx *ctx, const float *out_dev, double s, int g, double *u0_dev) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!out_dev || !u0_dev) return fail(ctx, TM_EINVAL, "null pointer");
+  int rc = ensure_learn(ctx, g);
+  if (rc) return rc;
+  TM_CUDA(ctx, learn_guess_launch(ctx->dm, ctx->learn, out_dev, s, u0_dev, ctx->stream));
+  ctx->launches += 1;
+  return TM_OK;
+}
+
+int tm_learn_output_grad(tm_ctx *ctx, const double *au0_dev, const double *f_dev, double s, int g, float *dout_dev) {
+  TM_CHECK_CTX(ctx);
+  TM_CHECK_MESH(ctx);
+  if (!au0_dev || !f_dev || !dout_dev) return fail(ctx, TM_EINVAL, "null pointer");
+  int rc = ensure_learn(ctx, g);
+  if (rc) return rc;
+  TM_CUDA(ctx, learn_grad_launch(ctx->dm, ctx->learn, au0_dev, f_dev, s, ctx->learn.pf, dout_dev, ctx->stream));
+  ctx->launches += 2;
+  return TM_OK;
+}
+
+int tm_adam_step(tm_ctx *ctx, int64_t n, float *params_dev, const float *grads_dev, float *m_dev, float *v_dev,
+                 int step, float lr, float beta1, float beta2, float eps) {
+  TM_CHECK_CTX(ctx);
+  if (n < 0 || (n > 0 && (!params_dev || !grads_dev || !m_dev || !v_dev)) || step < 1 || !(lr > 0) ||
+      !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+    return fail(ctx, TM_EINVAL, "bad Adam arguments");
+  if (n == 0) return TM_OK;
+  const float c1 = 1.f - std::pow(beta1, (float)step), c2 = 1.f - std::pow(beta2, (float)step);
+  TM_CUDA(ctx, adam_launch(params_dev, grads_dev, m_dev, v_dev, n, lr, beta1, beta2, eps, c1, c2, ctx->stream));
+  ctx->launches += 1;
   return TM_OK;
 }
 

@@ -189,6 +189,25 @@ cudaError_t coarse_prolong_launch(const DeviceMesh &m, const CoarseHierarchy &h,
 cudaError_t coarse_level_apply_launch(const CoarseHierarchy &h, int l, const float *x, float *y, cudaStream_t s);
 cudaError_t coarse_first_sweep_launch(const CoarseHierarchy &h, cudaStream_t s);
 
+// Learned initial guess (kernels_learn.cu): the voxel grid of level g and its gather tables.
+struct LearnTables {
+  int g = -1, X = 0, Y = 0, Z = 0, hv = 0;   // grid level, cells, cell side in finest units
+  int32_t *nxyz = nullptr;               // 3 per mesh node (finest units)
+  int32_t *vptr = nullptr, *vnode = nullptr;   // nodes grouped by their lower stencil cell (CSR)
+  double *pf = nullptr;                  // 3 x cells scratch of the restrictions
+  std::vector<void *> owned;
+  int64_t bytes = 0;
+};
+cudaError_t learn_input_launch(const DeviceMesh &m, const LearnTables &t, const double *rho, const double *f,
+                               double *pf, double *partials, unsigned int *ticket, double *s_dev, float *x,
+                               cudaStream_t st);
+cudaError_t learn_guess_launch(const DeviceMesh &m, const LearnTables &t, const float *out, double s, double *u0,
+                               cudaStream_t st);
+cudaError_t learn_grad_launch(const DeviceMesh &m, const LearnTables &t, const double *au0, const double *f, double s,
+                              double *pf, float *dout, cudaStream_t st);
+cudaError_t adam_launch(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
+                        float eps, float c1, float c2, cudaStream_t st);
+
 // Work buffers of one context (sized for the current mesh).
 struct Work {
   double *part64 = nullptr;    // 3 * nslot, partial sums of shared nodes (FP64 operator)
@@ -226,6 +245,7 @@ struct tm_ctx {
   amr::DeviceMesh dm;
   amr::Work w;
   amr::CoarseHierarchy coarse;   // two-level preconditioner (allocated on first use per mesh)
+  amr::LearnTables learn;        // learned initial guess (allocated on first use per mesh and grid)
   bool coarse_ready = false;     // its operators match the last density set up
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // profiling (tm_profile): kernel launch count and CUDA-event operator timing

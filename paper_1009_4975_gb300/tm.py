@@ -69,7 +69,8 @@ EXPORTS = ["tm_create", "tm_destroy", "tm_set_stream", "tm_last_error", "tm_mesh
            "tm_sensitivity", "tm_filter", "tm_oc_update", "tm_amr_mark", "tm_amr_adapt", "tm_design_difference",
            "tm_tables_adapt", "tm_tables_operator", "tm_tables_transfer", "tm_unet_param_count", "tm_unet_workspace_floats",
            "tm_unet_forward", "tm_unet_backward", "tm_profile", "tm_profile_read", "tm_coarse_setup",
-           "tm_coarse_cells", "tm_coarse_apply", "tm_coarse_restrict", "tm_coarse_prolong", "tm_coarse_vcycle", "tm_transfer_displacement"]
+           "tm_coarse_cells", "tm_coarse_apply", "tm_coarse_restrict", "tm_coarse_prolong", "tm_coarse_vcycle", "tm_transfer_displacement", "tm_learn_input",
+           "tm_learn_guess", "tm_learn_output_grad", "tm_adam_step"]
 
 _lib = None
 
@@ -118,6 +119,10 @@ def load_library(path: str = LIB_PATH):
         "tm_coarse_prolong": [vp, vp, vp],
         "tm_coarse_vcycle": [vp, vp, vp, C.c_int],
         "tm_transfer_displacement": [vp, vp, i64, vp, vp],
+        "tm_learn_input": [vp, vp, vp, C.c_int, vp, C.POINTER(dbl)],
+        "tm_learn_guess": [vp, vp, dbl, C.c_int, vp],
+        "tm_learn_output_grad": [vp, vp, vp, dbl, C.c_int, vp],
+        "tm_adam_step": [vp, i64, vp, vp, vp, vp, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float],
         "tm_profile_read": [vp, C.POINTER(tm_profile_data)],
     }
     for name, args in sig.items():
@@ -163,6 +168,7 @@ class Ctx:
         self.device = device
         self.info = None
         self.coarse = None
+        self.mesh_desc = None
 
     def check(self, rc):
         if rc != TM_OK:
@@ -212,6 +218,8 @@ def tm_mesh_upload(ctx: Ctx, nx, ny, nz, max_level, h0, leaves, dirichlet_faces=
     info = tm_mesh_info()
     ctx.check(load_library().tm_mesh_upload(ctx.handle, C.byref(d), C.byref(info)))
     ctx.info = {k: getattr(info, k) for k, _ in tm_mesh_info._fields_}
+    ctx.mesh_desc = (int(nx), int(ny), int(nz), int(max_level))
+    ctx.coarse = None
     return ctx.info
 
 
@@ -616,3 +624,39 @@ def tm_transfer_displacement(ctx: Ctx, u_full, points, out):
     ctx.check(load_library().tm_transfer_displacement(ctx.handle, _vec(ctx, u_full, torch.float64, "u_full"), n,
                                                       _ptr(points, torch.int32, 3 * n, "points"),
                                                       _ptr(out, torch.float64, 3 * n, "out")))
+
+
+# ---------------------------------------------------------------- learned initial guess
+def _voxels(ctx: Ctx, g: int) -> int:
+    i = ctx.mesh_desc
+    return (i[0] << g) * (i[1] << g) * (i[2] << g)
+
+
+def tm_learn_input(ctx: Ctx, rho, f, g, x) -> float:
+    """Network input (4 channels on the level-g voxel grid) into x; returns the load scale s."""
+    import torch
+    s = C.c_double()
+    ctx.check(load_library().tm_learn_input(ctx.handle, _elem(ctx, rho, "rho"), _vec(ctx, f, torch.float64, "f"),
+                                            int(g), _ptr(x, torch.float32, 4 * _voxels(ctx, g), "x"), C.byref(s)))
+    return s.value
+
+
+def tm_learn_guess(ctx: Ctx, out, s, g, u0):
+    import torch
+    ctx.check(load_library().tm_learn_guess(ctx.handle, _ptr(out, torch.float32, 3 * _voxels(ctx, g), "out"),
+                                            float(s), int(g), _vec(ctx, u0, torch.float64, "u0")))
+
+
+def tm_learn_output_grad(ctx: Ctx, au0, f, s, g, dout):
+    import torch
+    ctx.check(load_library().tm_learn_output_grad(ctx.handle, _vec(ctx, au0, torch.float64, "au0"),
+                                                  _vec(ctx, f, torch.float64, "f"), float(s), int(g),
+                                                  _ptr(dout, torch.float32, 3 * _voxels(ctx, g), "dout")))
+
+
+def tm_adam_step(ctx: Ctx, params, grads, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    import torch
+    n = params.numel()
+    ctx.check(load_library().tm_adam_step(ctx.handle, n, _ptr(params, torch.float32, n, "params"),
+                                          _ptr(grads, torch.float32, n, "grads"), _ptr(m, torch.float32, n, "m"),
+                                          _ptr(v, torch.float32, n, "v"), int(step), lr, beta1, beta2, eps))
