@@ -19,6 +19,10 @@ Modules
             leaf set with density transfer (Sec. 4, 6) and Eq. 10.
 ``learn``   the learned initial guess (no paper counterpart): grid transfers,
             a 3D U-Net and its energy loss.
+``coarse``  the two-level preconditioner (no paper counterpart): Galerkin coarse
+            space on the base-grid lattice and its l1-Jacobi V-cycle.
+``cpcg``    loader of ``pcg_omp.c``, Jacobi-PCG in C with OpenMP: the timed CPU
+            baseline of the benchmark.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against something other than itself (closed forms, exact rational
