@@ -11,9 +11,13 @@ smooth part of the error is removed by a projection onto a fixed coarse space.  
 below is a reading made for it:
 
 * **Levels.**  Level 0 is the vertex lattice of the base grid: ``(nx+1)(ny+1)(nz+1)`` nodes at
-  the base-cell corners, cell side ``h0``.  Level l+1 halves every dimension of level l; a
-  level is added while all three cell counts of the current level are even and it has more
-  than 64 cells.  The last level is the coarsest.
+  the base-cell corners, cell side ``h0``.  Level l+1 has ``ceil(n / 2)`` cells per axis for the
+  ``n`` of level l, cells of twice the side anchored at the origin; a level is added while the
+  current one has more than 64 cells.  With an odd count the last coarse cell overhangs the box;
+  the coarse functions restricted to the box stay trilinear on every finer cell, so the levels
+  stay nested.  An axis whose upper face is clamped is halved only while its count is even (the
+  clamped face must stay a lattice plane); an odd count there ends the hierarchy.  The last
+  level is the coarsest.
 * **Unknowns.**  Three displacement components per lattice node (DOF ``3 I + c``, nodes
   numbered with x fastest); nodes on a clamped face (the mesh's Dirichlet faces) carry none.
 * **Fine -> level 0 (P0).**  The trilinear interpolant of the lattice values, evaluated at the
@@ -47,14 +51,16 @@ from .mesh import Mesh
 
 
 # ---------------------------------------------------------------- lattices
-def level_shapes(mesh: Mesh):
+def level_shapes(mesh: Mesh, dirichlet_faces: int = 1):
     """Cell counts (X, Y, Z) of the levels 0, 1, ... (rule in the module docstring)."""
     shapes = [(mesh.nx, mesh.ny, mesh.nz)]
     while True:
-        X, Y, Z = shapes[-1]
-        if X % 2 or Y % 2 or Z % 2 or X * Y * Z <= 64:
+        cur = shapes[-1]
+        if cur[0] * cur[1] * cur[2] <= 64:
             return shapes
-        shapes.append((X // 2, Y // 2, Z // 2))
+        if any(cur[a] % 2 and (dirichlet_faces >> (2 * a + 1)) & 1 for a in range(3)):
+            return shapes
+        shapes.append(tuple((n + 1) // 2 for n in cur))
 
 
 def lattice_nodes(shape):
@@ -111,7 +117,7 @@ def level_prolongation(shape, dirichlet_faces: int = 1) -> sp.csr_matrix:
     """P (free DOFs of the level with `shape` cells x free DOFs of the next, halved level):
     nodal interpolation between nested lattices."""
     X, Y, Z = shape
-    Xc, Yc, Zc = X // 2, Y // 2, Z // 2
+    Xc, Yc, Zc = (X + 1) // 2, (Y + 1) // 2, (Z + 1) // 2
     p = lattice_nodes(shape)
 
     def axis(i):
@@ -145,7 +151,7 @@ class Hierarchy:
     """Galerkin operators of all levels for the reduced matrix A of `mesh`."""
 
     def __init__(self, mesh: Mesh, A: sp.spmatrix, dirichlet_faces: int = 1):
-        self.shapes = level_shapes(mesh)
+        self.shapes = level_shapes(mesh, dirichlet_faces)
         self.P0 = fine_prolongation(mesh, dirichlet_faces)
         self.A = [(self.P0.T @ A @ self.P0).tocsr()]
         self.P = []
@@ -192,13 +198,14 @@ def twolevel_pcg(mesh: Mesh, A: sp.spmatrix, f, u0=None, rtol=1e-8, nu: int = 2,
 
 
 # ---------------------------------------------------------------- independent check
-def quadrature_cell_matrices(mesh: Mesh, rho, level: int = 0, E0=1.0, Emin=1e-9, nu=0.3, penal=3.0):
+def quadrature_cell_matrices(mesh: Mesh, rho, level: int = 0, E0=1.0, Emin=1e-9, nu=0.3, penal=3.0,
+                             dirichlet_faces: int = 1):
     """(cells, 24, 24): the stiffness of the level's trilinear cell basis with the mesh's
     piecewise-constant Young's modulus, K_C = sum over leaves e in C of E_e * integral over e of
     B_C^T D B_C, each integral by 2x2x2 Gauss points of the leaf (exact: the integrand has
     degree <= 2 per axis).  A direct quadrature of the coarse basis, independent of K0, of the
     constraint map and of any prolongation; local DOF 3 k + c of cell corner k = i + 2j + 4m."""
-    X, Y, Z = level_shapes(mesh)[level]
+    X, Y, Z = level_shapes(mesh, dirichlet_faces)[level]
     S = (1 << mesh.L) << level                  # cell side in finest units
     H = mesh.h0 * (1 << level)
     D = F.elasticity_matrix(1.0, nu)

@@ -39,6 +39,10 @@ def test_level_shapes_follow_the_halving_rule():
                   np.zeros((1, 3), np.int64), np.zeros((1, 8), np.int64), {}, np.zeros(1, bool))
     assert CO.level_shapes(fake) == [(48, 24, 24), (24, 12, 12), (12, 6, 6), (6, 3, 3)]
     assert dom.nx == 48
+    odd = M.Mesh(18, 9, 9, 0, 1.0, fake.leaves, fake.perm, fake.nodes, fake.conn, {}, fake.dirichlet)
+    assert CO.level_shapes(odd) == [(18, 9, 9), (9, 5, 5), (5, 3, 3)]
+    # an odd count on an axis with a clamped upper face ends the hierarchy
+    assert CO.level_shapes(odd, dirichlet_faces=1 | 8) == [(18, 9, 9)]
 
 
 def test_fine_prolongation_reproduces_linear_fields_at_free_nodes():
@@ -163,3 +167,28 @@ def test_twolevel_pcg_reaches_the_direct_solution_in_fewer_iterations(name, make
     e = u - ud
     assert np.sqrt(e @ (A @ e) / (ud @ (A @ ud))) <= 1e-6
     assert factor * it2 <= it1
+
+
+def test_odd_base_grid_coarsens_with_overhanging_cells():
+    """A 10x5x5 base (odd y and z counts): the level-1 cells overhang the box; the Galerkin
+    operators still equal the quadrature of the coarse basis over the box, the coarse space stays
+    in the finite-element space, and the two-level PCG reaches the direct solution in a fraction
+    of Jacobi's iterations."""
+    dom = W.Domain(10, 5, 5, 1, 0.2)
+    w = W.truss_mesh("truss_10x5x5_L1", dom, 3, r0=0.06)
+    m, rho, A, f, C = _system(w)
+    assert CO.level_shapes(m) == [(10, 5, 5), (5, 3, 3)]
+    H = CO.Hierarchy(m, A)
+    for level, shape in enumerate(H.shapes):
+        K = CO.quadrature_cell_matrices(m, rho, level, w.E0, w.Emin, w.nu, w.penal)
+        Aq = CO.assemble_cells(shape, K)
+        assert abs(H.A[level] - Aq).max() <= 1e-12 * abs(Aq).max()
+    # linear fields: the level prolongation with an overhanging cell stays exact
+    P = CO.level_prolongation((10, 5, 5), dirichlet_faces=0)
+    fine = A_LIN + CO.lattice_nodes((10, 5, 5)).astype(np.float64) @ B_LIN.T
+    coarse = A_LIN + (2 * CO.lattice_nodes((5, 3, 3))).astype(np.float64) @ B_LIN.T
+    np.testing.assert_allclose(P @ coarse.ravel(), fine.ravel(), rtol=1e-13, atol=1e-13)
+    u, it2, _ = CO.twolevel_pcg(m, A, f, rtol=1e-8, nu=2)
+    it1 = S.jacobi_pcg(A, f, rtol=1e-8)[1]
+    assert np.linalg.norm(f - A @ u) <= 1.01e-8 * np.linalg.norm(f)
+    assert 3 * it2 <= it1
