@@ -287,9 +287,9 @@ def run_gpu(args):
 
     if rank != 0:
         return
-    solver = dict(precond=precond, smooth_sweeps=args.nu)
+    solver = dict(precond=precond, smooth_sweeps=args.nu, check_every=args.check_every)
     precision = precision_report(P, ctx, rho_first, f, u_first, u64, solver) if args.reports else None
-    batch = batch_report(P, W) if (args.batch and args.reports) else None
+    batch = batch_report(P, W, solver) if (args.batch and args.reports) else None
     adapt = adaptation_timing(P, ctx, cur, d, Ne, dev) if args.reports else None
     adaptive = (adaptive_report(P, W, w, solver, args.adaptive_iters, args.remesh_every)
                 if (args.reports and args.adaptive_iters > 0) else None)
@@ -370,10 +370,11 @@ def precision_report(P, ctx, rho, f, u0, u64, solver):
     return out
 
 
-def batch_report(P, W):
+def batch_report(P, W, solver):
     """Sixteen independent designs of 50k-500k leaves (two-level truss cantilevers, seeds
-    100-115), mixed solves from zero to 1e-8: one after another on one stream each, then all
-    at once through tm_pcg_solve_batch.  Throughput = sum of unknowns x iterations / wall time."""
+    100-115), solves with the chosen solver from zero to 1e-8: one after another on one stream
+    each, then all at once through tm_pcg_solve_batch.  Throughput = sum of unknowns x iterations
+    / wall time."""
     import torch
     works = W.batch_designs()
     items = []
@@ -397,9 +398,9 @@ def batch_report(P, W):
         t0 = time.perf_counter()
         if batched:
             sts = P.tm_pcg_solve_batch([it[0] for it in items], [it[1] for it in items], [it[2] for it in items], us,
-                                       rtol=1e-8, max_iter=200000, precision=P.TM_PREC_MIXED)
+                                       rtol=1e-8, max_iter=200000, precision=P.TM_PREC_MIXED, **solver)
         else:
-            sts = [P.tm_pcg_solve(c, rho, f, u, rtol=1e-8, max_iter=200000, precision=P.TM_PREC_MIXED)
+            sts = [P.tm_pcg_solve(c, rho, f, u, rtol=1e-8, max_iter=200000, precision=P.TM_PREC_MIXED, **solver)
                    for (c, rho, f, _), u in zip(items, us)]
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0

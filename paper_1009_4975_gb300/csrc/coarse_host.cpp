@@ -10,18 +10,24 @@
 
 namespace amr {
 
-// Level 0 is the base grid; a level is added while all three cell counts are even and the
-// current level has more than 64 cells.
+// Level 0 is the base grid; level l+1 has ceil(n / 2) cells per axis for the n of level l (a
+// coarse cell may overhang the box: the coarse functions restricted to the box stay nested),
+// added while level l has more than 64 cells.  An axis whose upper face is clamped is halved
+// only while its count is even (the clamped face stays a lattice plane).
 std::string coarse_shapes(const HostMesh &m, std::vector<int> &shapes) {
   shapes.clear();
   if (m.L > 9) return "node positions in a base cell need max_level <= 9";
-  int X = m.nx, Y = m.ny, Z = m.nz;
-  shapes.insert(shapes.end(), {X, Y, Z});
-  while (!(X % 2 || Y % 2 || Z % 2 || (int64_t)X * Y * Z <= 64)) {
-    X /= 2; Y /= 2; Z /= 2;
-    shapes.insert(shapes.end(), {X, Y, Z});
-    if ((int)shapes.size() / 3 >= kMaxCoarseLevels) break;
+  int d[3] = {m.nx, m.ny, m.nz};
+  shapes.insert(shapes.end(), {d[0], d[1], d[2]});
+  while ((int64_t)d[0] * d[1] * d[2] > 64 && (int)shapes.size() / 3 < kMaxCoarseLevels) {
+    bool stop = false;
+    for (int a = 0; a < 3; ++a)
+      if ((d[a] % 2) && ((m.dirichlet_faces >> (2 * a + 1)) & 1u)) stop = true;
+    if (stop) break;
+    for (int a = 0; a < 3; ++a) d[a] = (d[a] + 1) / 2;
+    shapes.insert(shapes.end(), {d[0], d[1], d[2]});
   }
+  int X, Y, Z;
   const int n = (int)shapes.size() / 3;
   X = shapes[3 * (n - 1)]; Y = shapes[3 * (n - 1) + 1]; Z = shapes[3 * (n - 1) + 2];
   const int64_t dofs = 3 * (int64_t)(X + 1) * (Y + 1) * (Z + 1);

@@ -92,19 +92,20 @@ __global__ void moments0_kernel(const int32_t *cell_elem, const int32_t *leaf, c
     for (int q = 0; q < 27; ++q) mom[27 * (int64_t)warp + q] = m[q];
 }
 
-// Parent moments from the 8 children (the finer level has 2X x 2Y x 2Z cells): per axis, a child
-// with offset o (-1 lower, +1 upper) has s_parent = (s_child + o) / 2, so
+// Parent moments from the <= 8 children (the finer level has Xc x Yc x Zc cells, X = ceil(Xc / 2);
+// children beyond the finer level's extent lie outside the box and carry nothing): per axis, a
+// child with offset o (-1 lower, +1 upper) has s_parent = (s_child + o) / 2, so
 //   m0' = m0,  m1' = (m1 + o m0) / 2,  m2' = (m2 + 2 o m1 + m0) / 4.
-__global__ void moments_up_kernel(const double *mc, int X, int Y, int Z, double *mp) {
+__global__ void moments_up_kernel(const double *mc, int Xc, int Yc, int Zc, int X, int Y, int Z, double *mp) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= X * Y * Z) return;
   const int px = p % X, py = (p / X) % Y, pz = p / (X * Y);
-  const int Xc = 2 * X, Yc = 2 * Y;
   double acc[27];
 #pragma unroll
   for (int q = 0; q < 27; ++q) acc[q] = 0.0;
   for (int ch = 0; ch < 8; ++ch) {
     const int ox = ch & 1, oy = (ch >> 1) & 1, oz = ch >> 2;
+    if (2 * px + ox >= Xc || 2 * py + oy >= Yc || 2 * pz + oz >= Zc) continue;
     const int c = (2 * px + ox) + Xc * ((2 * py + oy) + Yc * (2 * pz + oz));
     double t[27];
 #pragma unroll
@@ -243,12 +244,12 @@ __global__ void __launch_bounds__(kT) level_apply_kernel(const float *K, const f
   out[t] = mode == 0 ? r : fmaf(dinv[t], r, x[t]);
 }
 
-// Restriction of a level-l vector to level l+1 (X, Y, Z: the coarse level's cells): the
+// Restriction of a level-l vector (Xf x Yf x Zf cells) to level l+1 (X, Y, Z cells): the
 // transpose of nodal interpolation, weights 1 / 0.5 per axis.  With dinv: also x = dinv b
 // (the first l1-Jacobi sweep from zero).
-__global__ void __launch_bounds__(kT) level_restrict_kernel(const float *t_f, int X, int Y, int Z, unsigned faces,
-                                                            float *b_c, const float *dinv_c, float *x_c,
-                                                            const int *done) {
+__global__ void __launch_bounds__(kT) level_restrict_kernel(const float *t_f, int Xf, int Yf, int Zf, int X, int Y,
+                                                            int Z, unsigned faces, float *b_c, const float *dinv_c,
+                                                            float *x_c, const int *done) {
   if (done_set(done)) return;
   const int nodes = (X + 1) * (Y + 1) * (Z + 1);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -257,7 +258,6 @@ __global__ void __launch_bounds__(kT) level_restrict_kernel(const float *t_f, in
   const int i = J % (X + 1), j = (J / (X + 1)) % (Y + 1), k = J / ((X + 1) * (Y + 1));
   float s = 0.f;
   if (!lattice_fixed(i, j, k, X, Y, Z, faces)) {
-    const int Xf = 2 * X, Yf = 2 * Y, Zf = 2 * Z;
     for (int dz = -1; dz <= 1; ++dz) {
       const int fz = 2 * k + dz;
       if (fz < 0 || fz > Zf) continue;
@@ -277,9 +277,10 @@ __global__ void __launch_bounds__(kT) level_restrict_kernel(const float *t_f, in
   if (x_c) x_c[t] = dinv_c[t] * s;
 }
 
-// x_f += P x_c (X, Y, Z: the fine level's cells): nodal interpolation from the halved lattice.
-__global__ void __launch_bounds__(kT) level_prolong_kernel(const float *x_c, int X, int Y, int Z, unsigned faces,
-                                                           float *x_f, const int *done) {
+// x_f += P x_c (X, Y, Z: the fine level's cells; Xc, Yc: the coarse level's): nodal
+// interpolation from the halved lattice.
+__global__ void __launch_bounds__(kT) level_prolong_kernel(const float *x_c, int Xc, int Yc, int X, int Y, int Z,
+                                                           unsigned faces, float *x_f, const int *done) {
   if (done_set(done)) return;
   const int nodes = (X + 1) * (Y + 1) * (Z + 1);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -287,7 +288,6 @@ __global__ void __launch_bounds__(kT) level_prolong_kernel(const float *x_c, int
   const int I = t / 3, c = t % 3;
   const int i = I % (X + 1), j = (I / (X + 1)) % (Y + 1), k = I / ((X + 1) * (Y + 1));
   if (lattice_fixed(i, j, k, X, Y, Z, faces)) return;
-  const int Xc = X / 2, Yc = Y / 2;
   float s = 0.f;
   for (int bz = 0; bz <= (k & 1); ++bz)
     for (int by = 0; by <= (j & 1); ++by)
@@ -508,7 +508,8 @@ cudaError_t coarse_setup_launch(const DeviceMesh &m, CoarseHierarchy &h, const d
   if (e != cudaSuccess) return e;
   for (int l = 1; l < h.nlev; ++l) {
     const CoarseLevel &c = h.lev[l];
-    moments_up_kernel<<<grid_for((int64_t)c.X * c.Y * c.Z), kT, 0, s>>>(h.lev[l - 1].mom, c.X, c.Y, c.Z, c.mom);
+    const CoarseLevel &f = h.lev[l - 1];
+    moments_up_kernel<<<grid_for((int64_t)c.X * c.Y * c.Z), kT, 0, s>>>(f.mom, f.X, f.Y, f.Z, c.X, c.Y, c.Z, c.mom);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   for (int l = 0; l < h.nlev; ++l) {
@@ -564,13 +565,13 @@ static cudaError_t vcycle_from(const CoarseHierarchy &h, int l, int nu, const in
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const CoarseLevel &n = h.lev[l + 1];
   const bool sweep = l + 1 < h.nlev - 1;
-  level_restrict_kernel<<<grid_for(3 * (int64_t)n.nodes), kT, 0, s>>>(c.t, n.X, n.Y, n.Z, h.faces, n.b,
+  level_restrict_kernel<<<grid_for(3 * (int64_t)n.nodes), kT, 0, s>>>(c.t, c.X, c.Y, c.Z, n.X, n.Y, n.Z, h.faces, n.b,
                                                                        sweep ? n.dinv : nullptr, sweep ? n.x2 : nullptr,
                                                                        done);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *launches += 2;
   if ((e = vcycle_from(h, l + 1, nu, done, s, launches)) != cudaSuccess) return e;
-  level_prolong_kernel<<<grid_for(n3), kT, 0, s>>>(n.x, c.X, c.Y, c.Z, h.faces, cur, done);
+  level_prolong_kernel<<<grid_for(n3), kT, 0, s>>>(n.x, n.X, n.Y, c.X, c.Y, c.Z, h.faces, cur, done);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *launches += 1;
   for (int k = 0; k < nu; ++k) {

@@ -329,7 +329,8 @@ def tm_pcg_solve(ctx: Ctx, rho, f, u, rtol=1e-8, max_iter=100000, precision=TM_P
 
 
 def tm_pcg_solve_batch(ctxs, rhos, fs, us, rtol=1e-8, max_iter=100000, precision=TM_PREC_FP64, inner_rtol=0.1,
-                       check_every=64, raise_on_error=True, graphs=True) -> list:
+                       check_every=64, raise_on_error=True, graphs=True, precond=TM_PRECOND_JACOBI,
+                       smooth_sweeps=1) -> list:
     """Independent solves on distinct contexts, run concurrently (include/tm.h)."""
     import torch
     n = len(ctxs)
@@ -339,7 +340,7 @@ def tm_pcg_solve_batch(ctxs, rhos, fs, us, rtol=1e-8, max_iter=100000, precision
     rp = (C.c_void_p * n)(*[_elem(c, r, "rho").value for c, r in zip(ctxs, rhos)])
     fp = (C.c_void_p * n)(*[_vec(c, f, torch.float64, "f").value for c, f in zip(ctxs, fs)])
     up = (C.c_void_p * n)(*[_vec(c, u, torch.float64, "u").value for c, u in zip(ctxs, us)])
-    o = tm_solve_opts(rtol, max_iter, precision, inner_rtol, check_every, 0 if graphs else 1)
+    o = tm_solve_opts(rtol, max_iter, precision, inner_rtol, check_every, 0 if graphs else 1, precond, smooth_sweeps)
     st = (tm_solve_stats * n)()
     status = (C.c_int * n)()
     rc = load_library().tm_pcg_solve_batch(n, hs, rp, fp, up, C.byref(o), st, status)

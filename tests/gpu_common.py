@@ -69,5 +69,6 @@ class Case:
 
 @functools.lru_cache(maxsize=None)
 def case(name):
-    makers = {"config1": W.config1, "config1b": W.config1b, "small_truss": W.small_truss}
+    makers = {"config1": W.config1, "config1b": W.config1b, "small_truss": W.small_truss,
+              "truss_10x5x5_L1": lambda: W.truss_mesh("truss_10x5x5_L1", W.Domain(10, 5, 5, 1, 0.2), 3, r0=0.06)}
     return Case(makers[name]())

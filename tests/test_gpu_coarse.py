@@ -41,7 +41,7 @@ def _embed(shape, v):
     return out
 
 
-@pytest.mark.parametrize("name", ["config1b", "small_truss"])
+@pytest.mark.parametrize("name", ["config1b", "small_truss", "truss_10x5x5_L1"])
 def test_level_operators_match_the_oracle_galerkin_products(name):
     import torch
     c, rho, info, H = _setup(name)
@@ -60,7 +60,7 @@ def test_level_operators_match_the_oracle_galerkin_products(name):
         assert np.allclose(Kh, Kh.transpose(0, 2, 1))
 
 
-@pytest.mark.parametrize("name", ["config1b", "small_truss"])
+@pytest.mark.parametrize("name", ["config1b", "small_truss", "truss_10x5x5_L1"])
 def test_restriction_prolongation_and_level_products_match_the_oracle(name):
     import torch
     c, rho, info, H = _setup(name)
@@ -111,7 +111,7 @@ def test_restriction_prolongation_and_level_products_match_the_oracle(name):
         assert np.all(g[fixed] == 0.0)
 
 
-@pytest.mark.parametrize("name", ["config1b", "small_truss"])
+@pytest.mark.parametrize("name", ["config1b", "small_truss", "truss_10x5x5_L1"])
 @pytest.mark.parametrize("nu", [1, 2])
 def test_vcycle_matches_the_oracle(name, nu):
     import torch
@@ -133,7 +133,7 @@ def test_vcycle_matches_the_oracle(name, nu):
         assert np.all(got[fixed] == 0.0)
 
 
-@pytest.mark.parametrize("name,factor", [("config1b", 2.5), ("small_truss", 5.0)])
+@pytest.mark.parametrize("name,factor", [("config1b", 2.5), ("small_truss", 5.0), ("truss_10x5x5_L1", 2.5)])
 def test_twolevel_solve_reaches_the_tolerance_in_fewer_iterations(name, factor):
     import torch
     P = tm()
