@@ -290,6 +290,7 @@ def run_gpu(args):
     solver = dict(precond=precond, smooth_sweeps=args.nu, check_every=args.check_every)
     precision = precision_report(P, ctx, rho_first, f, u_first, u64, solver) if args.reports else None
     batch = batch_report(P, W, solver) if (args.batch and args.reports) else None
+    multi = multi_load_report(P, W, ctx, w, rho_first, Nn, solver) if (args.batch and args.reports) else None
     adapt = adaptation_timing(P, ctx, cur, d, Ne, dev) if args.reports else None
     adaptive = (adaptive_report(P, W, w, solver, args.adaptive_iters, args.remesh_every)
                 if (args.reports and args.adaptive_iters > 0) else None)
@@ -317,6 +318,7 @@ def run_gpu(args):
         "fp64_pcg": fp64,
         "precision": precision,
         "batch": batch,
+        "multi_load": multi,
         "adaptation": adapt,
         "adaptive_loop": adaptive,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -418,6 +420,41 @@ def batch_report(P, W, solver):
             "sequential_s": seq_s, "batched_s": bat_s,
             "sequential_gdof_iter_per_s": seq_work / seq_s / 1e9, "batched_gdof_iter_per_s": bat_work / bat_s / 1e9,
             "speedup": seq_s / bat_s}
+
+
+def multi_load_report(P, W, ctx, w, rho, Nn, solver):
+    """Config-4 load cases on the benchmark design: 8 seeded load cases (point loads and face
+    tractions on the face x = 2, seeds 10-17) solved from zero to 1e-8 with the chosen solver one
+    after another, then in lockstep through tm_pcg_solve_multi (one operator pass, update and
+    coarse step for all cases per iteration, CUDA-graph batches)."""
+    import torch
+    cases = W.load_cases(w.dom, 8, 10)
+    dev = rho.device
+    F = torch.zeros((len(cases), 3 * Nn), dtype=torch.float64, device=dev)
+    for r, (nd, comp, val) in enumerate(cases):
+        f = torch.zeros(3 * Nn, dtype=torch.float64, device=dev)
+        P.tm_build_rhs(ctx, nd, comp, val, f)
+        F[r] = f
+    kw = dict(rtol=1e-8, max_iter=200000, precond=solver["precond"], smooth_sweeps=solver["smooth_sweeps"],
+              check_every=solver["check_every"])
+
+    def seq():
+        its = []
+        for r in range(len(cases)):
+            u = torch.zeros(3 * Nn, dtype=torch.float64, device=dev)
+            its.append(P.tm_pcg_solve(ctx, rho, F[r].contiguous(), u, precision=P.TM_PREC_MIXED, **kw)["iterations"])
+        return its
+
+    def lock():
+        U = torch.zeros_like(F)
+        return [st["iterations"] for st in P.tm_pcg_solve_multi(ctx, rho, F, U, **kw)]
+
+    seq(); lock()                          # warm-up: set-up paths and graphs built once
+    torch.cuda.synchronize()
+    t0 = time.perf_counter(); it_s = seq(); torch.cuda.synchronize(); seq_s = time.perf_counter() - t0
+    t0 = time.perf_counter(); it_l = lock(); torch.cuda.synchronize(); lock_s = time.perf_counter() - t0
+    return {"load_cases": len(cases), "iterations": it_l, "same_iterations_as_sequential": it_l == it_s,
+            "sequential_s": seq_s, "lockstep_s": lock_s, "speedup": seq_s / lock_s}
 
 
 def adaptation_timing(P, ctx, rho, d, Ne, dev):

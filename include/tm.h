@@ -219,7 +219,7 @@ int tm_apply_K(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double *
  * of TM_PREC_MIXED). */
 int tm_apply_K_f32(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float *y_dev);
 
-/* The FP32 operator on nrhs vectors at once (1 <= nrhs <= 4; several load cases of one
+/* The FP32 operator on nrhs vectors at once (1 <= nrhs <= 8; several load cases of one
  * design): y_dev[r] = C^T K(rho) C x_dev[r] (Eq. 6-9), x_dev and y_dev each nrhs
  * consecutive A-space vectors of 3 * Nn floats (device).  Each y_dev[r] is the result
  * of tm_apply_K_f32 on x_dev[r] bit for bit; the operator tables are staged once per
@@ -275,14 +275,18 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
 int tm_pcg_solve_batch(int n, tm_ctx *const *ctxs, const double *const *rho_dev, const double *const *f_dev,
                        double *const *u_dev, const tm_solve_opts *opts, tm_solve_stats *stats, int *status);
 
-/* Several load cases of one design at once (1 <= nrhs <= 4; TM_PREC_MIXED only):
+/* Several load cases of one design at once (1 <= nrhs <= 8; TM_PREC_MIXED only):
  * f_dev and u_dev hold nrhs consecutive A-space vectors (device), u_dev the warm starts
  * on entry.  The load cases iterate in lockstep; each has its own CG scalars and
  * reliable updates, and gets the same u and iteration count as tm_pcg_solve with the
- * same options, bit for bit.  They share one operator pass per iteration
- * (tm_apply_K_f32_multi).  Plain kernel launches, no CUDA graphs.  stats: nrhs entries
- * (may be NULL); their seconds field is the time of the whole call.  Work buffers for 4
- * load cases are allocated on the first call for the uploaded mesh. */
+ * same options, bit for bit.  Per iteration one operator pass serves all cases
+ * (tm_apply_K_f32_multi), one launch updates all cases and, with TM_PRECOND_TWOLEVEL, one
+ * launch sequence applies the coarse correction of all cases (the level matrices are read
+ * once for all); cases that reached their stopping point skip the work.  Unless
+ * opts->no_graphs, each batch of check_every lockstep iterations is a CUDA graph replayed on
+ * a library stream.  stats: nrhs entries (may be NULL); their seconds field is the time of the
+ * whole call.  Work buffers for 8 load cases are allocated on the first call for the
+ * uploaded mesh. */
 int tm_pcg_solve_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const double *f_dev, double *u_dev,
                        const tm_solve_opts *opts, tm_solve_stats *stats);
 

@@ -290,16 +290,16 @@ int ensure_coarse(tm_ctx *ctx) {
     TM_CUDA(ctx, alloc(o, B, &c.mom, 27 * cells));
     TM_CUDA(ctx, alloc(o, B, &c.K, 576 * cells));
     TM_CUDA(ctx, alloc(o, B, &c.dinv, n3));
-    TM_CUDA(ctx, alloc(o, B, &c.b, n3));
-    TM_CUDA(ctx, alloc(o, B, &c.x, n3));
-    TM_CUDA(ctx, alloc(o, B, &c.x2, n3));
-    TM_CUDA(ctx, alloc(o, B, &c.t, n3));
+    TM_CUDA(ctx, alloc(o, B, &c.b, kMaxRhs * n3));
+    TM_CUDA(ctx, alloc(o, B, &c.x, kMaxRhs * n3));
+    TM_CUDA(ctx, alloc(o, B, &c.x2, kMaxRhs * n3));
+    TM_CUDA(ctx, alloc(o, B, &c.t, kMaxRhs * n3));
   }
   const CoarseLevel &cl = h.lev[nlev - 1];
   const size_t nc = 3 * (size_t)cl.nodes;
   TM_CUDA(ctx, alloc(o, B, &h.Kc64, 576 * (size_t)cl.X * cl.Y * cl.Z));
   TM_CUDA(ctx, alloc(o, B, &h.Ainv, nc * nc));
-  TM_CUDA(ctx, alloc(o, B, &h.part, 24 * (size_t)h.nseg));
+  TM_CUDA(ctx, alloc(o, B, &h.part, kMaxRhs * 24 * (size_t)h.nseg));
   h.faces = hm.dirichlet_faces;
   h.nlev = nlev;
   return TM_OK;
@@ -329,19 +329,26 @@ int coarse_setup(tm_ctx *ctx, const double *rho, double *seconds) {
   return TM_OK;
 }
 
-// The two-level part of one preconditioner application on the FP32 residual r: P0^T r, the
-// V-cycle, the CG scalars (mode: 0 iteration, 1 start, 2 residual replacement; finish_kernel)
-// and the search direction p from z = D^-1 r + P0 V(P0^T r).
-int enqueue_twolevel(tm_ctx *ctx, int mode, const float *r, float *p, const float *dinv, int nu) {
+// The two-level part of one preconditioner application on FP32 residuals: P0^T r, the V-cycle,
+// the CG scalars (mode: 0 iteration, 1 start, 2 residual replacement; finish_kernel) and the
+// search directions p from z = D^-1 r + P0 V(P0^T r), for load cases c0 .. c0 + nv - 1 (fine
+// vectors ld apart, scalars sc[case], finish partials pstride apart, tickets[case]).
+int enqueue_twolevel_cases(tm_ctx *ctx, int mode, const float *r, float *p, int64_t ld, const float *dinv, int nu,
+                           SolveScalars *sc, int c0, int nv, double *partials, int pstride, unsigned int *tickets) {
   const CoarseHierarchy &h = ctx->coarse;
-  SolveScalars *sc = solve_scalars(ctx);
-  TM_CUDA(ctx, coarse_restrict_launch(ctx->dm, h, r, true, &sc->done, ctx->stream));
+  TM_CUDA(ctx, coarse_restrict_launch(ctx->dm, h, r, ld, true, sc, c0, nv, ctx->stream));
   int nl = 0;
-  TM_CUDA(ctx, coarse_vcycle_launch(h, nu, &sc->done, ctx->stream, &nl));
-  TM_CUDA(ctx, coarse_finish_launch(h, mode, sc, ctx->w.red, ctx->w.ticket + 8, ctx->stream));
-  TM_CUDA(ctx, coarse_pupdate_launch(ctx->dm, h, p, r, dinv, mode, sc, ctx->stream));
+  TM_CUDA(ctx, coarse_vcycle_launch(h, nu, sc, c0, nv, ctx->stream, &nl));
+  TM_CUDA(ctx, coarse_finish_launch(h, mode, sc, c0, nv, partials, pstride, tickets, ctx->stream));
+  TM_CUDA(ctx, coarse_pupdate_launch(ctx->dm, h, p, r, ld, dinv, mode, sc, c0, nv, ctx->stream));
   ctx->launches += 4 + nl;
   return TM_OK;
+}
+
+// One load case on the context's single-solve vectors and scalars.
+int enqueue_twolevel(tm_ctx *ctx, int mode, const float *r, float *p, const float *dinv, int nu) {
+  return enqueue_twolevel_cases(ctx, mode, r, p, 3 * ctx->dm.Nn, dinv, nu, solve_scalars(ctx), 0, 1, ctx->w.red,
+                                4 * device_sms(), ctx->w.ticket + 8);
 }
 
 }  // namespace
@@ -1173,34 +1180,47 @@ int tm_pcg_solve_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const doubl
   if (!rho_dev || !f_dev || !u_dev || !opts) return fail(ctx, TM_EINVAL, "null pointer");
   if (nrhs < 1 || nrhs > kMaxRhs) return fail(ctx, TM_EINVAL, "nrhs must be in [1, " + std::to_string(kMaxRhs) + "]");
   if (opts->precision != TM_PREC_MIXED) return fail(ctx, TM_EINVAL, "multi-load solves are TM_PREC_MIXED only");
-  if (opts->precond != TM_PRECOND_JACOBI) return fail(ctx, TM_EINVAL, "multi-load solves use the Jacobi preconditioner");
+  if (opts->precond != TM_PRECOND_JACOBI && opts->precond != TM_PRECOND_TWOLEVEL)
+    return fail(ctx, TM_EINVAL, "unknown preconditioner");
   if (!(opts->rtol > 0) || opts->max_iter < 1) return fail(ctx, TM_EINVAL, "need rtol > 0 and max_iter >= 1");
+  const bool twolevel = opts->precond == TM_PRECOND_TWOLEVEL;
+  const int nu = opts->smooth_sweeps > 0 ? opts->smooth_sweeps : 1;
+  const bool graphs = opts->no_graphs == 0;
   const DeviceMesh &m = ctx->dm;
   Work &w = ctx->w;
   cudaStream_t st = ctx->stream;
   const int64_t n = 3 * m.Nn;
   const int check = opts->check_every > 0 ? opts->check_every : 32;
   const double delta = opts->inner_rtol > 0 ? opts->inner_rtol : 0.1;
+  const int pstride = 16 * device_sms();   // reduction partials per load case
   if (!w.mvec) {
     TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.mvec, (size_t)kMaxRhs * 4 * n));
     TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.mr64, (size_t)kMaxRhs * n));
     TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.msc, (size_t)kMaxRhs));
     TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.mdotp, (size_t)kMaxRhs * std::max(m.nblk, 1)));
+    TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.mred, (size_t)kMaxRhs * pstride));
+    TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.mticket, (size_t)4 * kMaxRhs));
   }
   if (!w.part_multi) TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.part_multi, (size_t)kMaxRhs * 3 * m.nslot));
   // kind-major: the p (q) vectors of the load cases are consecutive, as the operator reads them
   auto vec = [&](int r, int k) { return w.mvec + ((size_t)k * kMaxRhs + r) * n; };   // k: 0 x, 1 r, 2 p, 3 q
   auto scal = [&](int r) { return w.msc + r; };
+  unsigned int *t_apply = w.mticket, *t_update = w.mticket + kMaxRhs, *t_finish = w.mticket + 2 * kMaxRhs;
   std::vector<tm_solve_stats> out(nrhs);
   std::memset(out.data(), 0, nrhs * sizeof(tm_solve_stats));
   TM_CUDA(ctx, cudaEventRecord(ctx->ev0, st));
   TM_CUDA(ctx, launch_coeff(m, w, rho_dev, st));
   TM_CUDA(ctx, launch_diag(m, w.ce64, nullptr, w.dinv, w.dinv32, st));
   ctx->launches += 2;
+  double setup_s = 0;
+  int rc;
+  if (twolevel) {
+    rc = coarse_setup(ctx, rho_dev, &setup_s);
+    if (rc) return rc;
+  }
   double *rr_dev = scal_at(ctx, 81), *ff_dev = scal_at(ctx, 82);
   std::vector<double> ff(nrhs), scale_old(nrhs, 0.0), rel(nrhs, 0.0);
   std::vector<int> left(nrhs, opts->max_iter), active(nrhs, 1), first(nrhs, 1);
-  int rc;
   // FP64 true residual of load case r into mr64[r]; returns ||r||^2 in *rr
   auto residual = [&](int r, double *rr) -> int {
     int rc2 = timed_apply<double>(ctx, w.ce64, u_dev + (size_t)r * n, w.q, w.part64, nullptr, nullptr, true, nullptr);
@@ -1227,11 +1247,21 @@ int tm_pcg_solve_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const doubl
       TM_CUDA(ctx, launch_start<float>(w.mr64 + (size_t)r * n, nullptr, scale, vec(r, 1), vec(r, 2), w.dinv32, n,
                                        scal(r), w.red, w.ticket + 2, st));
       TM_CUDA(ctx, cudaStreamSynchronize(st));   // sc0 lives on the host stack
+      if (twolevel) {
+        rc = enqueue_twolevel_cases(ctx, 1, vec(0, 1), vec(0, 2), n, w.dinv32, nu, w.msc, r, 1, w.mred, pstride,
+                                    t_finish);
+        if (rc) return rc;
+      }
       first[r] = 0;
     } else {
       TM_CUDA(ctx, launch_replace(w.mr64 + (size_t)r * n, scale, scale / scale_old[r], vec(r, 1), vec(r, 2), w.dinv32,
-                                  n, abs_stop, left[r], scal(r), w.red, w.ticket + 2, st));
-      ctx->launches += 1;
+                                  n, abs_stop, left[r], scal(r), w.red, w.ticket + 2, st, twolevel));
+      ctx->launches += twolevel ? 0 : 1;
+      if (twolevel) {
+        rc = enqueue_twolevel_cases(ctx, 2, vec(0, 1), vec(0, 2), n, w.dinv32, nu, w.msc, r, 1, w.mred, pstride,
+                                    t_finish);
+        if (rc) return rc;
+      }
     }
     ctx->launches += 1;
     scale_old[r] = scale;
@@ -1267,6 +1297,56 @@ int tm_pcg_solve_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const doubl
       TM_CUDA(ctx, cudaMemcpyAsync(&scal(r)->done, &one, sizeof(int), cudaMemcpyHostToDevice, st));
       TM_CUDA(ctx, cudaStreamSynchronize(st));
     }
+  // one lockstep iteration for all cases: the multi-vector operator pass, the update of every case
+  // in one launch, then (two-level) the coarse step of every case in one launch sequence or
+  // (Jacobi) each case's p update; cases whose run is done return at once
+  auto iteration = [&]() -> int {
+    TM_CUDA(ctx, launch_apply_multi(m, nrhs, w.ce32, vec(0, 2), vec(0, 3), w.part_multi, w.mdotp, scal(0), t_apply,
+                                    ctx->stream));
+    TM_CUDA(ctx, launch_update_nodes_cases(nrhs, vec(0, 0), vec(0, 2), vec(0, 3), vec(0, 1), n, w.dinv32, m.Nn,
+                                           m.sh_of_node, m.sh_ptr, w.part_multi, 3 * m.nslot, w.msc, w.mred,
+                                           t_update, ctx->stream, twolevel));
+    ctx->launches += 2;
+    if (twolevel)
+      return enqueue_twolevel_cases(ctx, 0, vec(0, 1), vec(0, 2), n, w.dinv32, nu, w.msc, 0, nrhs, w.mred, pstride,
+                                    t_finish);
+    for (int r = 0; r < nrhs; ++r) {
+      TM_CUDA(ctx, launch_pupdate<float>(vec(r, 2), vec(r, 1), w.dinv32, n, scal(r), ctx->stream));
+      ctx->launches += 1;
+    }
+    return TM_OK;
+  };
+  cudaGraphExec_t exec = nullptr;
+  int graph_launches = 0;
+  if (graphs) {
+    // a batch of `check` lockstep iterations captured once on the library stream and replayed
+    cudaStream_t user = ctx->stream;
+    ctx->stream = ctx->gstream;
+    const int64_t l0 = ctx->launches;
+    cudaError_t e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal);
+    rc = TM_OK;
+    for (int k = 0; k < check && e == cudaSuccess && rc == TM_OK; ++k) rc = iteration();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(ctx->gstream, &graph);
+    ctx->stream = user;
+    graph_launches = (int)(ctx->launches - l0);
+    ctx->launches = l0;
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(ctx, TM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    if (rc) {
+      cudaGraphDestroy(graph);
+      return rc;
+    }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, TM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  struct GraphGuard {
+    cudaGraphExec_t g;
+    ~GraphGuard() { if (g) cudaGraphExecDestroy(g); }
+  } guard{exec};
   std::vector<SolveScalars> hs(nrhs);
   auto any_active = [&] {
     for (int r = 0; r < nrhs; ++r)
@@ -1274,17 +1354,17 @@ int tm_pcg_solve_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const doubl
     return false;
   };
   while (any_active()) {
-    for (int k = 0; k < check; ++k) {
-      TM_CUDA(ctx, launch_apply_multi(m, nrhs, w.ce32, vec(0, 2), vec(0, 3), w.part_multi, w.mdotp, scal(0),
-                                      w.ticket + 7, st));
-      ctx->launches += 1;
-      for (int r = 0; r < nrhs; ++r) {
-        if (!active[r]) continue;
-        TM_CUDA(ctx, launch_update_nodes<float, float>(vec(r, 0), vec(r, 2), vec(r, 3), vec(r, 1), w.dinv32, m.Nn,
-                                                       m.sh_of_node, m.sh_ptr, w.part_multi + (size_t)r * 3 * m.nslot,
-                                                       scal(r), w.red, w.ticket, st));
-        TM_CUDA(ctx, launch_pupdate<float>(vec(r, 2), vec(r, 1), w.dinv32, n, scal(r), st));
-        ctx->launches += 2;
+    if (exec) {
+      TM_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
+      TM_CUDA(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev_fork, 0));
+      TM_CUDA(ctx, cudaGraphLaunch(exec, ctx->gstream));
+      TM_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->gstream));
+      TM_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+      ctx->launches += graph_launches;
+    } else {
+      for (int k = 0; k < check; ++k) {
+        rc = iteration();
+        if (rc) return rc;
       }
     }
     for (int r = 0; r < nrhs; ++r)
@@ -1322,6 +1402,8 @@ int tm_pcg_solve_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const doubl
   for (int r = 0; r < nrhs; ++r) {
     out[r].rel_residual = rel[r];
     out[r].seconds = ms * 1e-3;
+    out[r].setup_seconds = setup_s;
+    out[r].coarse_levels = twolevel ? ctx->coarse.nlev : 0;
     if (rel[r] > opts->rtol) status = TM_ENOTCONVERGED;
   }
   if (stats) std::memcpy(stats, out.data(), nrhs * sizeof(tm_solve_stats));
@@ -1425,7 +1507,7 @@ int tm_coarse_restrict(tm_ctx *ctx, const float *r_dev, float *b0_dev) {
   TM_CHECK_COARSE(ctx);
   if (!r_dev || !b0_dev) return fail(ctx, TM_EINVAL, "null pointer");
   const CoarseHierarchy &h = ctx->coarse;
-  TM_CUDA(ctx, coarse_restrict_launch(ctx->dm, h, r_dev, false, nullptr, ctx->stream));
+  TM_CUDA(ctx, coarse_restrict_launch(ctx->dm, h, r_dev, 3 * ctx->dm.Nn, false, nullptr, 0, 1, ctx->stream));
   TM_CUDA(ctx, cudaMemcpyAsync(b0_dev, h.lev[0].b, 3 * (size_t)h.lev[0].nodes * sizeof(float),
                                cudaMemcpyDeviceToDevice, ctx->stream));
   ctx->launches += 2;
@@ -1452,7 +1534,7 @@ int tm_coarse_vcycle(tm_ctx *ctx, const float *b0_dev, float *x0_dev, int nu) {
   TM_CUDA(ctx, cudaMemcpyAsync(h.lev[0].b, b0_dev, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
   TM_CUDA(ctx, coarse_first_sweep_launch(h, ctx->stream));
   int nl = 0;
-  TM_CUDA(ctx, coarse_vcycle_launch(h, nu, nullptr, ctx->stream, &nl));
+  TM_CUDA(ctx, coarse_vcycle_launch(h, nu, nullptr, 0, 1, ctx->stream, &nl));
   TM_CUDA(ctx, cudaMemcpyAsync(x0_dev, h.lev[0].x, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
   ctx->launches += 1 + nl;
   return TM_OK;

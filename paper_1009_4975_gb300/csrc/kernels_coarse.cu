@@ -23,6 +23,9 @@
 // Layout: level l has X x Y x Z cells and (X+1)(Y+1)(Z+1) nodes, node I = i + (X+1)(j + (Y+1)k),
 // DOF 3 I + c; DOFs of nodes on clamped faces are kept at 0.  Cell matrices: [cell][24][24],
 // local DOF 3 q + c of corner q = a + 2b + 4c.  All summation orders are fixed (no atomics).
+// Several load cases run through one launch: grid dimension y (x for the coarsest solve) is the
+// case, each case with its own level vectors (consecutive, one level's length apart), its own
+// CG scalars and its own done flag; cases whose run is done return at once.
 #include <cuda_runtime.h>
 
 #include <utility>
@@ -37,7 +40,17 @@ namespace {
 
 constexpr int kT = 256;
 
-__device__ __forceinline__ bool done_set(const int *done) { return done && *(volatile const int *)done; }
+// The load cases of a launch: case c0 + (grid index); sc (may be NULL) holds every case's CG
+// scalars, and a case whose run is done is skipped.
+struct Cases {
+  const SolveScalars *sc;
+  int c0;
+};
+__device__ __forceinline__ int case_of(const Cases &cs, int g) { return cs.c0 + g; }
+__device__ __forceinline__ bool case_done(const Cases &cs, int c) {
+  return cs.sc && *(volatile const int *)&cs.sc[c].done;
+}
+__device__ __forceinline__ int64_t lattice_len(int X, int Y, int Z) { return 3 * (int64_t)(X + 1) * (Y + 1) * (Z + 1); }
 
 __device__ __forceinline__ bool lattice_fixed(int i, int j, int k, int X, int Y, int Z, unsigned faces) {
   return ((faces & 1u) && i == 0) || ((faces & 2u) && i == X) || ((faces & 4u) && j == 0) ||
@@ -224,8 +237,13 @@ __device__ __forceinline__ float cell_row_product(const float *K, const float *x
 // mode 2: out = A x (b unused).
 __global__ void __launch_bounds__(kT) level_apply_kernel(const float *K, const float *x, const float *b,
                                                          const float *dinv, float *out, int X, int Y, int Z,
-                                                         unsigned faces, int mode, const int *done) {
-  if (done_set(done)) return;
+                                                         unsigned faces, int mode, Cases cs) {
+  const int cc = case_of(cs, blockIdx.y);
+  if (case_done(cs, cc)) return;
+  const int64_t off = cc * lattice_len(X, Y, Z);
+  x += off;
+  out += off;
+  if (b) b += off;
   const int nodes = (X + 1) * (Y + 1) * (Z + 1);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * nodes) return;
@@ -249,8 +267,12 @@ __global__ void __launch_bounds__(kT) level_apply_kernel(const float *K, const f
 // (the first l1-Jacobi sweep from zero).
 __global__ void __launch_bounds__(kT) level_restrict_kernel(const float *t_f, int Xf, int Yf, int Zf, int X, int Y,
                                                             int Z, unsigned faces, float *b_c, const float *dinv_c,
-                                                            float *x_c, const int *done) {
-  if (done_set(done)) return;
+                                                            float *x_c, Cases cs) {
+  const int cc = case_of(cs, blockIdx.y);
+  if (case_done(cs, cc)) return;
+  t_f += cc * lattice_len(Xf, Yf, Zf);
+  b_c += cc * lattice_len(X, Y, Z);
+  if (x_c) x_c += cc * lattice_len(X, Y, Z);
   const int nodes = (X + 1) * (Y + 1) * (Z + 1);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * nodes) return;
@@ -279,9 +301,12 @@ __global__ void __launch_bounds__(kT) level_restrict_kernel(const float *t_f, in
 
 // x_f += P x_c (X, Y, Z: the fine level's cells; Xc, Yc: the coarse level's): nodal
 // interpolation from the halved lattice.
-__global__ void __launch_bounds__(kT) level_prolong_kernel(const float *x_c, int Xc, int Yc, int X, int Y, int Z,
-                                                           unsigned faces, float *x_f, const int *done) {
-  if (done_set(done)) return;
+__global__ void __launch_bounds__(kT) level_prolong_kernel(const float *x_c, int Xc, int Yc, int Zc, int X, int Y,
+                                                           int Z, unsigned faces, float *x_f, Cases cs) {
+  const int cc = case_of(cs, blockIdx.y);
+  if (case_done(cs, cc)) return;
+  x_c += cc * lattice_len(Xc, Yc, Zc);
+  x_f += cc * lattice_len(X, Y, Z);
   const int nodes = (X + 1) * (Y + 1) * (Z + 1);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * nodes) return;
@@ -302,8 +327,11 @@ __global__ void __launch_bounds__(kT) level_prolong_kernel(const float *x_c, int
 // Coarsest level: x = Ainv b over all of its DOFs (Ainv symmetric, zero rows and columns at
 // clamped DOFs).  One CTA; one warp per row (lanes stride the row, then a fixed shuffle tree).
 __global__ void __launch_bounds__(1024) dense_solve_kernel(const float *Ainv, const float *b, float *x, int n,
-                                                           const int *done) {
-  if (done_set(done)) return;
+                                                           Cases cs) {
+  const int cc = case_of(cs, blockIdx.x);
+  if (case_done(cs, cc)) return;
+  b += (int64_t)cc * n;
+  x += (int64_t)cc * n;
   extern __shared__ float sb[];
   for (int i = threadIdx.x; i < n; i += blockDim.x) sb[i] = b[i];
   __syncthreads();
@@ -333,9 +361,12 @@ __device__ __forceinline__ void trilinear8(uint32_t code, int L, float w[8]) {
 // Stage 1 of P0^T r: one warp per segment (a run of <= 64 nodes of one base cell) sums w_q r over
 // its nodes; a node belongs to the cell holding it in its half-open box, clamped at the upper
 // faces of the domain.  Lane sums, then a fixed shuffle tree.
-__global__ void fine_restrict_cells_kernel(const float *r, const int32_t *seg_ptr, const int32_t *cnode,
-                                           const uint32_t *code, int nseg, int L, float *part, const int *done) {
-  if (done_set(done)) return;
+__global__ void fine_restrict_cells_kernel(const float *r, int64_t r_ld, const int32_t *seg_ptr, const int32_t *cnode,
+                                           const uint32_t *code, int nseg, int L, float *part, Cases cs) {
+  const int cc = case_of(cs, blockIdx.y);
+  if (case_done(cs, cc)) return;
+  r += cc * r_ld;
+  part += (int64_t)cc * nseg * 24;
   const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (warp >= nseg) return;
@@ -373,10 +404,14 @@ __global__ void fine_restrict_cells_kernel(const float *r, const int32_t *seg_pt
 
 // Stage 2: each level-0 DOF sums the partials of its <= 8 cells' segments (fixed order); with dinv
 // also x = dinv b.
-__global__ void __launch_bounds__(kT) fine_restrict_nodes_kernel(const float *part, const int32_t *cseg, int X,
-                                                                 int Y, int Z, unsigned faces, float *b,
-                                                                 const float *dinv, float *x, const int *done) {
-  if (done_set(done)) return;
+__global__ void __launch_bounds__(kT) fine_restrict_nodes_kernel(const float *part, int nseg, const int32_t *cseg,
+                                                                 int X, int Y, int Z, unsigned faces, float *b,
+                                                                 const float *dinv, float *x, Cases cs) {
+  const int cc = case_of(cs, blockIdx.y);
+  if (case_done(cs, cc)) return;
+  part += (int64_t)cc * nseg * 24;
+  b += cc * lattice_len(X, Y, Z);
+  if (x) x += cc * lattice_len(X, Y, Z);
   const int nodes = (X + 1) * (Y + 1) * (Z + 1);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * nodes) return;
@@ -434,8 +469,15 @@ __global__ void fine_prolong_kernel(const float *v, const int32_t *ncell, const 
 // rz_jacobi = r^T D^-1 r is in scratch[0] (mode 0) or in rz (modes 1, 2); prev and r.p of a
 // replacement are in scratch[2] and scratch[3].
 __global__ void __launch_bounds__(kT) finish_kernel(const float *b0, const float *x0, int n, int mode,
-                                                    SolveScalars *sc, double *partials, unsigned int *ticket) {
+                                                    SolveScalars *sc_all, int c0, double *partials_all,
+                                                    int pstride, unsigned int *tickets) {
+  const int cc = c0 + blockIdx.y;
+  SolveScalars *sc = sc_all + cc;
   if (sc->done) return;
+  b0 += (int64_t)cc * n;
+  x0 += (int64_t)cc * n;
+  double *partials = partials_all + (int64_t)cc * pstride;
+  unsigned int *ticket = tickets + cc;
   DotAcc<float> acc;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc.add_prod(b0[i], x0[i]);
   const double v = block_sum<kT>(acc.value());
@@ -466,10 +508,16 @@ __global__ void __launch_bounds__(kT) finish_kernel(const float *b0, const float
 
 // The search direction with the two-level preconditioner, z = D^-1 r + P0 x0:
 //   mode 0: p = z + beta p;  mode 1: p = z;  mode 2: p = z + beta (p - gamma z).
-__global__ void __launch_bounds__(kT) pupdate2_kernel(float *p, const float *r, const float *dinv, const float *x0,
-                                                      const int32_t *ncell, const uint32_t *code, int64_t Nn, int L,
-                                                      int X, int Y, int mode, const SolveScalars *sc) {
+__global__ void __launch_bounds__(kT) pupdate2_kernel(float *p, const float *r, int64_t ld, const float *dinv,
+                                                      const float *x0, int64_t x0_ld, const int32_t *ncell,
+                                                      const uint32_t *code, int64_t Nn, int L, int X, int Y, int mode,
+                                                      const SolveScalars *sc_all, int c0) {
+  const int cc = c0 + blockIdx.y;
+  const SolveScalars *sc = sc_all + cc;
   if (sc->done) return;
+  p += cc * ld;
+  r += cc * ld;
+  x0 += cc * x0_ld;
   const float beta = (float)sc->beta, gamma = (float)sc->rp;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < Nn; n += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t cd = code[n];
@@ -525,57 +573,58 @@ cudaError_t coarse_setup_launch(const DeviceMesh &m, CoarseHierarchy &h, const d
   return cudaSuccess;
 }
 
-cudaError_t coarse_restrict_launch(const DeviceMesh &m, const CoarseHierarchy &h, const float *r, bool first_sweep,
-                                   const int *done, cudaStream_t s) {
+cudaError_t coarse_restrict_launch(const DeviceMesh &m, const CoarseHierarchy &h, const float *r, int64_t r_ld,
+                                   bool first_sweep, const SolveScalars *sc, int c0, int nv, cudaStream_t s) {
   const CoarseLevel &l0 = h.lev[0];
-  const int nc0 = l0.X * l0.Y * l0.Z;
-  fine_restrict_cells_kernel<<<grid_for(32 * (int64_t)h.nseg), kT, 0, s>>>(r, h.seg_ptr, h.cnode, h.code, h.nseg, m.L,
-                                                                           h.part, done);
+  const Cases cs{sc, c0};
+  const dim3 g1(grid_for(32 * (int64_t)h.nseg), nv);
+  fine_restrict_cells_kernel<<<g1, kT, 0, s>>>(r, r_ld, h.seg_ptr, h.cnode, h.code, h.nseg, m.L, h.part, cs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const bool sweep = first_sweep && h.nlev > 1;
-  fine_restrict_nodes_kernel<<<grid_for(3 * (int64_t)l0.nodes), kT, 0, s>>>(h.part, h.cseg, l0.X, l0.Y, l0.Z, h.faces,
-                                                                           l0.b,
-                                                                           sweep ? l0.dinv : nullptr,
-                                                                           sweep ? l0.x2 : nullptr, done);
+  const dim3 g2(grid_for(3 * (int64_t)l0.nodes), nv);
+  fine_restrict_nodes_kernel<<<g2, kT, 0, s>>>(h.part, h.nseg, h.cseg, l0.X, l0.Y, l0.Z, h.faces, l0.b,
+                                               sweep ? l0.dinv : nullptr, sweep ? l0.x2 : nullptr, cs);
   return cudaGetLastError();
 }
 
 // V-cycle from level l with b_l given and (l not coarsest) the first sweep x = dinv_l b_l
 // already in x2_l.  The remaining 2 nu - 1 sweeps alternate between x2 and x, so the result
 // ends in x_l, where the next finer level's prolongation (or the fine level) reads it.
-static cudaError_t vcycle_from(const CoarseHierarchy &h, int l, int nu, const int *done, cudaStream_t s, int *launches) {
+static cudaError_t vcycle_from(const CoarseHierarchy &h, int l, int nu, const Cases &cs, int nv, cudaStream_t s,
+                               int *launches) {
   cudaError_t e;
   const CoarseLevel &c = h.lev[l];
   if (l == h.nlev - 1) {
     const int n = 3 * c.nodes;
-    dense_solve_kernel<<<1, 1024, n * sizeof(float), s>>>(h.Ainv, c.b, c.x, n, done);
+    dense_solve_kernel<<<nv, 1024, n * sizeof(float), s>>>(h.Ainv, c.b, c.x, n, cs);
     *launches += 1;
     return cudaGetLastError();
   }
   const int n3 = 3 * c.nodes;
+  const dim3 gl(grid_for(n3), nv);
   float *cur = c.x2, *oth = c.x;
   for (int k = 1; k < nu; ++k) {           // remaining pre-smoothing sweeps
-    level_apply_kernel<<<grid_for(n3), kT, 0, s>>>(c.K, cur, c.b, c.dinv, oth, c.X, c.Y, c.Z, h.faces, 1, done);
+    level_apply_kernel<<<gl, kT, 0, s>>>(c.K, cur, c.b, c.dinv, oth, c.X, c.Y, c.Z, h.faces, 1, cs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     std::swap(cur, oth);
     *launches += 1;
   }
-  level_apply_kernel<<<grid_for(n3), kT, 0, s>>>(c.K, cur, c.b, c.dinv, c.t, c.X, c.Y, c.Z, h.faces, 0, done);
+  level_apply_kernel<<<gl, kT, 0, s>>>(c.K, cur, c.b, c.dinv, c.t, c.X, c.Y, c.Z, h.faces, 0, cs);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const CoarseLevel &n = h.lev[l + 1];
   const bool sweep = l + 1 < h.nlev - 1;
-  level_restrict_kernel<<<grid_for(3 * (int64_t)n.nodes), kT, 0, s>>>(c.t, c.X, c.Y, c.Z, n.X, n.Y, n.Z, h.faces, n.b,
-                                                                       sweep ? n.dinv : nullptr, sweep ? n.x2 : nullptr,
-                                                                       done);
+  const dim3 gn(grid_for(3 * (int64_t)n.nodes), nv);
+  level_restrict_kernel<<<gn, kT, 0, s>>>(c.t, c.X, c.Y, c.Z, n.X, n.Y, n.Z, h.faces, n.b, sweep ? n.dinv : nullptr,
+                                          sweep ? n.x2 : nullptr, cs);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *launches += 2;
-  if ((e = vcycle_from(h, l + 1, nu, done, s, launches)) != cudaSuccess) return e;
-  level_prolong_kernel<<<grid_for(n3), kT, 0, s>>>(n.x, n.X, n.Y, c.X, c.Y, c.Z, h.faces, cur, done);
+  if ((e = vcycle_from(h, l + 1, nu, cs, nv, s, launches)) != cudaSuccess) return e;
+  level_prolong_kernel<<<gl, kT, 0, s>>>(n.x, n.X, n.Y, n.Z, c.X, c.Y, c.Z, h.faces, cur, cs);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *launches += 1;
   for (int k = 0; k < nu; ++k) {
-    level_apply_kernel<<<grid_for(n3), kT, 0, s>>>(c.K, cur, c.b, c.dinv, oth, c.X, c.Y, c.Z, h.faces, 1, done);
+    level_apply_kernel<<<gl, kT, 0, s>>>(c.K, cur, c.b, c.dinv, oth, c.X, c.Y, c.Z, h.faces, 1, cs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     std::swap(cur, oth);
     *launches += 1;
@@ -583,25 +632,28 @@ static cudaError_t vcycle_from(const CoarseHierarchy &h, int l, int nu, const in
   return cur == c.x ? cudaSuccess : cudaErrorInvalidValue;   // 2 nu - 1 sweeps: always x
 }
 
-cudaError_t coarse_vcycle_launch(const CoarseHierarchy &h, int nu, const int *done, cudaStream_t s, int *launches) {
-  return vcycle_from(h, 0, nu, done, s, launches);
+cudaError_t coarse_vcycle_launch(const CoarseHierarchy &h, int nu, const SolveScalars *sc, int c0, int nv,
+                                 cudaStream_t s, int *launches) {
+  return vcycle_from(h, 0, nu, Cases{sc, c0}, nv, s, launches);
 }
 
-cudaError_t coarse_finish_launch(const CoarseHierarchy &h, int mode, SolveScalars *sc, double *partials,
-                                 unsigned int *ticket, cudaStream_t s) {
+cudaError_t coarse_finish_launch(const CoarseHierarchy &h, int mode, SolveScalars *sc, int c0, int nv,
+                                 double *partials, int pstride, unsigned int *tickets, cudaStream_t s) {
   const int n = 3 * h.lev[0].nodes;
   int g = grid_for(n);
-  if (g > 4 * device_sms()) g = 4 * device_sms();
-  finish_kernel<<<g, kT, 0, s>>>(h.lev[0].b, h.lev[0].x, n, mode, sc, partials, ticket);
+  if (g > 4 * device_sms()) g = 4 * device_sms();   // one grid for every caller: the same reduction order
+  if (g > pstride) return cudaErrorInvalidValue;
+  finish_kernel<<<dim3(g, nv), kT, 0, s>>>(h.lev[0].b, h.lev[0].x, n, mode, sc, c0, partials, pstride, tickets);
   return cudaGetLastError();
 }
 
 cudaError_t coarse_pupdate_launch(const DeviceMesh &m, const CoarseHierarchy &h, float *p, const float *r,
-                                  const float *dinv, int mode, const SolveScalars *sc, cudaStream_t s) {
+                                  int64_t ld, const float *dinv, int mode, const SolveScalars *sc, int c0, int nv,
+                                  cudaStream_t s) {
   int g = grid_for(m.Nn);
   if (g > 8 * device_sms()) g = 8 * device_sms();
-  pupdate2_kernel<<<g, kT, 0, s>>>(p, r, dinv, h.lev[0].x, h.ncell, h.code, m.Nn, m.L, h.lev[0].X, h.lev[0].Y, mode,
-                                    sc);
+  pupdate2_kernel<<<dim3(g, nv), kT, 0, s>>>(p, r, ld, dinv, h.lev[0].x, 3 * (int64_t)h.lev[0].nodes, h.ncell, h.code,
+                                             m.Nn, m.L, h.lev[0].X, h.lev[0].Y, mode, sc, c0);
   return cudaGetLastError();
 }
 
@@ -624,7 +676,7 @@ cudaError_t coarse_first_sweep_launch(const CoarseHierarchy &h, cudaStream_t s) 
 cudaError_t coarse_level_apply_launch(const CoarseHierarchy &h, int l, const float *x, float *y, cudaStream_t s) {
   const CoarseLevel &c = h.lev[l];
   level_apply_kernel<<<grid_for(3 * (int64_t)c.nodes), kT, 0, s>>>(c.K, x, nullptr, c.dinv, y, c.X, c.Y, c.Z, h.faces,
-                                                                    2, nullptr);
+                                                                    2, Cases{nullptr, 0});
   return cudaGetLastError();
 }
 

@@ -76,8 +76,17 @@ __global__ void __launch_bounds__(kVecThreads) update_nodes_kernel(TX *x, const 
                                                                    int64_t Nn, const int32_t *sh_of_node,
                                                                    const int32_t *sh_ptr, const T *part,
                                                                    SolveScalars *sc, double *partials,
-                                                                   unsigned int *ticket, int twolevel) {
+                                                                   unsigned int *ticket, int twolevel, int64_t vst,
+                                                                   int64_t pst, int pstride) {
+  // load case blockIdx.y: its vectors vst apart, its partial sums pst apart, its own scalars,
+  // reduction partials and ticket
+  const int cs = blockIdx.y;
+  sc += cs;
   if (sc->done) return;
+  x += cs * vst; p += cs * vst; q += cs * vst; r += cs * vst;
+  part += cs * pst;
+  partials += (int64_t)cs * pstride;
+  ticket += cs;
   const double alpha = sc->alpha;
   const T a = (T)alpha;
   DotAcc<T> arz, arr;
@@ -317,7 +326,7 @@ cudaError_t launch_update_nodes(TX *x, const T *p, const T *q, T *r, const T *di
                                 const int32_t *sh_of_node, const int32_t *sh_ptr, const T *part, SolveScalars *sc,
                                 double *partials, unsigned int *ticket, cudaStream_t s, bool twolevel) {
   update_nodes_kernel<TX, T><<<vec_grid(Nn), kVecThreads, 0, s>>>(x, p, q, r, dinv, Nn, sh_of_node, sh_ptr, part, sc,
-                                                                   partials, ticket, twolevel ? 1 : 0);
+                                                                   partials, ticket, twolevel ? 1 : 0, 0, 0, 0);
   return cudaGetLastError();
 }
 template cudaError_t launch_update_nodes<double, double>(double *, const double *, const double *, double *,
@@ -327,6 +336,17 @@ template cudaError_t launch_update_nodes<double, double>(double *, const double 
 template cudaError_t launch_update_nodes<float, float>(float *, const float *, const float *, float *, const float *,
                                                        int64_t, const int32_t *, const int32_t *, const float *,
                                                        SolveScalars *, double *, unsigned int *, cudaStream_t, bool);
+
+cudaError_t launch_update_nodes_cases(int nv, float *x, const float *p, const float *q, float *r, int64_t vst,
+                                      const float *dinv, int64_t Nn, const int32_t *sh_of_node, const int32_t *sh_ptr,
+                                      const float *part, int64_t pst, SolveScalars *sc, double *partials,
+                                      unsigned int *tickets, cudaStream_t s, bool twolevel) {
+  const int g = vec_grid(Nn);
+  update_nodes_kernel<float, float><<<dim3(g, nv), kVecThreads, 0, s>>>(x, p, q, r, dinv, Nn, sh_of_node, sh_ptr, part,
+                                                                        sc, partials, tickets, twolevel ? 1 : 0, vst,
+                                                                        pst, 2 * g);
+  return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_pupdate(T *p, const T *r, const T *dinv, int64_t n, SolveScalars *sc, cudaStream_t s) {

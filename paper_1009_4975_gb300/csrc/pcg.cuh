@@ -26,6 +26,12 @@ template <typename TX, typename T>
 cudaError_t launch_update_nodes(TX *x, const T *p, const T *q, T *r, const T *dinv, int64_t Nn,
                                 const int32_t *sh_of_node, const int32_t *sh_ptr, const T *part, SolveScalars *sc,
                                 double *partials, unsigned int *ticket, cudaStream_t s, bool twolevel = false);
+// The FP32 update for nv load cases in one launch (grid y = case): vectors vst apart, shared-node
+// partials pst apart, scalars sc[case], reduction partials 2 * grid apart, tickets[case].
+cudaError_t launch_update_nodes_cases(int nv, float *x, const float *p, const float *q, float *r, int64_t vst,
+                                      const float *dinv, int64_t Nn, const int32_t *sh_of_node, const int32_t *sh_ptr,
+                                      const float *part, int64_t pst, SolveScalars *sc, double *partials,
+                                      unsigned int *tickets, cudaStream_t s, bool twolevel);
 template <typename T>
 cudaError_t launch_pupdate(T *p, const T *r, const T *dinv, int64_t n, SolveScalars *sc, cudaStream_t s);
 template <typename T>

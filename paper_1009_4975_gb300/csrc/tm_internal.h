@@ -143,7 +143,7 @@ struct CoarseLevel {
   double *mom = nullptr;                 // cells x 27 moments of E (FP64)
   float *K = nullptr;                    // cells x 24 x 24 cell matrices
   float *dinv = nullptr;                 // 3 * nodes: inverse l1 row sums (0 at clamped nodes)
-  float *b = nullptr, *x = nullptr, *x2 = nullptr, *t = nullptr;   // 3 * nodes each
+  float *b = nullptr, *x = nullptr, *x2 = nullptr, *t = nullptr;   // kMaxRhs cases x 3 * nodes each
 };
 struct CoarseHierarchy {
   int nlev = 0;
@@ -158,7 +158,7 @@ struct CoarseHierarchy {
   int32_t *ncell = nullptr;              // per mesh node: its base cell
   uint32_t *code = nullptr;              // per mesh node: position in the cell, bit 31 = no unknowns
   double *Q = nullptr;                   // 27 x 576: moment -> cell-matrix coefficients
-  float *part = nullptr;                 // segments x 24: partial restrictions
+  float *part = nullptr;                 // kMaxRhs cases x segments x 24: partial restrictions
   double *Kc64 = nullptr;                // coarsest level's cell matrices in FP64
   float *Ainv = nullptr;                 // coarsest level: dense inverse over all its DOFs
   std::vector<double> Kc_host;           // host copy of Kc64 (inverse formed on the host)
@@ -177,13 +177,17 @@ void coarse_moment_matrices(double nu, std::vector<double> &Q);
 std::string coarse_dense_inverse(const std::vector<double> &Kc, int X, int Y, int Z, unsigned faces,
                                  std::vector<float> &Ainv);
 cudaError_t coarse_setup_launch(const DeviceMesh &m, CoarseHierarchy &h, const double *rho, cudaStream_t s);
-cudaError_t coarse_restrict_launch(const DeviceMesh &m, const CoarseHierarchy &h, const float *r, bool first_sweep,
-                                   const int *done, cudaStream_t s);
-cudaError_t coarse_vcycle_launch(const CoarseHierarchy &h, int nu, const int *done, cudaStream_t s, int *launches);
-cudaError_t coarse_finish_launch(const CoarseHierarchy &h, int mode, struct SolveScalars *sc, double *partials,
-                                 unsigned int *ticket, cudaStream_t s);
+// Load cases c0 .. c0 + nv - 1 per launch (sc: all cases' CG scalars, may be NULL outside a solve);
+// fine vectors of consecutive cases are r_ld (ld) floats apart.
+cudaError_t coarse_restrict_launch(const DeviceMesh &m, const CoarseHierarchy &h, const float *r, int64_t r_ld,
+                                   bool first_sweep, const struct SolveScalars *sc, int c0, int nv, cudaStream_t s);
+cudaError_t coarse_vcycle_launch(const CoarseHierarchy &h, int nu, const struct SolveScalars *sc, int c0, int nv,
+                                 cudaStream_t s, int *launches);
+cudaError_t coarse_finish_launch(const CoarseHierarchy &h, int mode, struct SolveScalars *sc, int c0, int nv,
+                                 double *partials, int pstride, unsigned int *tickets, cudaStream_t s);
 cudaError_t coarse_pupdate_launch(const DeviceMesh &m, const CoarseHierarchy &h, float *p, const float *r,
-                                  const float *dinv, int mode, const struct SolveScalars *sc, cudaStream_t s);
+                                  int64_t ld, const float *dinv, int mode, const struct SolveScalars *sc, int c0,
+                                  int nv, cudaStream_t s);
 cudaError_t coarse_prolong_launch(const DeviceMesh &m, const CoarseHierarchy &h, const float *v, float *y,
                                   cudaStream_t s);
 cudaError_t coarse_level_apply_launch(const CoarseHierarchy &h, int l, const float *x, float *y, cudaStream_t s);
@@ -226,6 +230,8 @@ struct Work {
   double *mr64 = nullptr;      // kMaxRhs * 3 Nn
   struct SolveScalars *msc = nullptr;   // kMaxRhs
   double *mdotp = nullptr;     // kMaxRhs * nblk
+  double *mred = nullptr;      // kMaxRhs x 16 SMs: per-case reduction partials
+  unsigned int *mticket = nullptr;   // 4 x kMaxRhs: per-case last-CTA tickets
   // solver vectors (3 * Nn)
   double *r = nullptr, *p = nullptr, *q = nullptr, *dinv = nullptr, *d = nullptr;
   float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *dinv32 = nullptr, *x32 = nullptr;
@@ -319,7 +325,7 @@ cudaError_t unet_gather8(const float *in, float *out, int64_t NC, int X, int Y, 
 cudaError_t unet_channels_copy(const float *src, int Cs, int sc0, float *dst, int Cd, int dc0, int nc, int N,
                                int64_t S, bool accumulate, cudaStream_t s);
 // several vectors at once (kernels_multi.cu)
-constexpr int kMaxRhs = 4;
+constexpr int kMaxRhs = 8;
 size_t apply_multi_smem_bytes(const DeviceMesh &m, int nr);
 struct SolveScalars;
 cudaError_t launch_apply_multi(const DeviceMesh &m, int nr, const float *ce, const float *x, float *y, float *part,

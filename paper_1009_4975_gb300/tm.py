@@ -356,13 +356,14 @@ def tm_pcg_solve_batch(ctxs, rhos, fs, us, rtol=1e-8, max_iter=100000, precision
 
 
 def tm_pcg_solve_multi(ctx: Ctx, rho, F, U, rtol=1e-8, max_iter=100000, inner_rtol=0.1, check_every=64,
-                       raise_on_error=True) -> list:
+                       raise_on_error=True, graphs=True, precond=TM_PRECOND_JACOBI, smooth_sweeps=1) -> list:
     """Mixed solves of the load cases in the rows of F (nrhs, 3 Nn) into U, in lockstep; see include/tm.h."""
     import torch
     if F.dim() != 2 or F.shape != U.shape or F.shape[1] != 3 * ctx.info["Nn"]:
         raise ValueError("F and U must be (nrhs, 3 Nn)")
     nr = F.shape[0]
-    o = tm_solve_opts(rtol, max_iter, TM_PREC_MIXED, inner_rtol, check_every, 1)
+    o = tm_solve_opts(rtol, max_iter, TM_PREC_MIXED, inner_rtol, check_every, 0 if graphs else 1, precond,
+                      smooth_sweeps)
     st = (tm_solve_stats * nr)()
     rc = load_library().tm_pcg_solve_multi(ctx.handle, nr, _elem(ctx, rho, "rho"), _ptr(F, torch.float64, None, "F"),
                                            _ptr(U, torch.float64, None, "U"), C.byref(o), st)

@@ -9,7 +9,8 @@ from tests.gpu_common import U32, case, ctx, tm
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("name,nrhs", [("config1", 1), ("config1b", 3), ("config1b", 4), ("small_truss", 4)])
+@pytest.mark.parametrize("name,nrhs", [("config1", 1), ("config1b", 3), ("config1b", 4), ("small_truss", 4),
+                                       ("config1b", 8)])
 def test_multi_vector_operator(name, nrhs):
     import torch
     P = tm()
@@ -38,22 +39,36 @@ def test_multi_vector_operator_rejects_too_many_vectors():
     P = tm()
     c = case("config1")
     c.upload()
-    X = torch.zeros((5, 3 * c.m.Nn), dtype=torch.float32, device=c.dev)
+    X = torch.zeros((9, 3 * c.m.Nn), dtype=torch.float32, device=c.dev)
     with pytest.raises(P.TmError):
         P.tm_apply_K_f32_multi(ctx(), c.t(c.rho), X, torch.zeros_like(X))
 
 
-def test_multi_load_solve_matches_single_solves():
-    """Three load cases of one design solved in lockstep: every u and iteration count equals
-    the single mixed solve of that case bit for bit, and meets the solve parity criterion."""
+def _loads(c, k):
+    """k load cases: point loads at the load node in each direction and combinations, then point
+    loads at nodes on the tip face."""
+    node = c.w.load_nodes
+    loads = [(node, [2], [-1.0]), (node, [1], [-1.0]), (np.concatenate([node, node]), [0, 2], [1.0, -0.5])]
+    tip = c.m.nodes[c.m.nodes[:, 0] == c.m.nodes[:, 0].max()]
+    rng = np.random.default_rng(17)
+    while len(loads) < k:
+        p = tip[rng.integers(len(tip))][None]
+        loads.append((p, [int(rng.integers(3))], [float(rng.choice([-1.0, 1.0]))]))
+    return loads[:k]
+
+
+@pytest.mark.parametrize("precond,nrhs,graphs", [(0, 3, False), (0, 8, True), (1, 3, False), (1, 8, True)])
+def test_multi_load_solve_matches_single_solves(precond, nrhs, graphs):
+    """Load cases of one design solved in lockstep, with the Jacobi and the two-level
+    preconditioner, plain launches or graph batches: every u and iteration count equals the
+    single mixed solve of that case bit for bit, and meets the solve parity criterion."""
     import torch
     from oracle import fem as F
     P = tm()
     c = case("config1b")
     c.upload()
     n3 = 3 * c.m.Nn
-    node = c.w.load_nodes
-    loads = [(node, [2], [-1.0]), (node, [1], [-1.0]), (np.concatenate([node, node]), [0, 2], [1.0, -0.5])]
+    loads = _loads(c, nrhs)
     Fd = torch.zeros((len(loads), n3), dtype=torch.float64, device=c.dev)
     for r, (nd, comp, val) in enumerate(loads):
         f = torch.zeros(n3, dtype=torch.float64, device=c.dev)
@@ -61,12 +76,13 @@ def test_multi_load_solve_matches_single_solves():
         Fd[r] = f
     rho = c.t(c.rho)
     U = torch.zeros_like(Fd)
-    stats = P.tm_pcg_solve_multi(ctx(), rho, Fd, U, rtol=1e-8, max_iter=200000)
+    stats = P.tm_pcg_solve_multi(ctx(), rho, Fd, U, rtol=1e-8, max_iter=200000, graphs=graphs, precond=precond,
+                                 check_every=16)
     torch.cuda.synchronize()
     for r, (nd, comp, val) in enumerate(loads):
         u1 = torch.zeros(n3, dtype=torch.float64, device=c.dev)
         st1 = P.tm_pcg_solve(ctx(), rho, Fd[r].contiguous(), u1, rtol=1e-8, max_iter=200000,
-                             precision=P.TM_PREC_MIXED)
+                             precision=P.TM_PREC_MIXED, precond=precond, check_every=16)
         torch.cuda.synchronize()
         assert stats[r]["iterations"] == st1["iterations"]
         assert U[r].cpu().numpy().tobytes() == u1.cpu().numpy().tobytes()

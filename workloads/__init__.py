@@ -28,6 +28,9 @@ Recipes (seeded; the shapes follow the paper's 3D cantilever workloads):
   paper's refinement criterion (solid elements and a layer around them).
 * ``batch_designs`` -- sixteen truss designs with two levels on bases of 2k x k x k cells
   (about 50k to 500k leaves), seeds 100-115, for batched solves.
+* ``load_cases`` -- seeded load cases on the face x = 2 of a box (point loads and uniform face
+  tractions at base-lattice points, which are nodes of every mesh of that box), for multi-load
+  solves.
 * ``unet_init`` -- seeded initial parameters of a network given by its parameter shapes.
 """
 from __future__ import annotations
@@ -40,7 +43,7 @@ from scipy import ndimage
 __all__ = [
     "Domain", "Workload", "uniform_leaves", "refine", "balance", "level_map",
     "smoothed_field", "random_field_mesh", "truss_mesh", "config1", "config1b",
-    "config2", "small_truss", "load_at", "batch_designs", "unet_init",
+    "config2", "small_truss", "load_at", "batch_designs", "unet_init", "load_cases",
 ]
 
 
@@ -295,6 +298,30 @@ def batch_designs(n: int = 16, seed0: int = 100):
     ks = np.linspace(9, 26, n).round().astype(int)
     return [truss_mesh(f"cantilever_{2 * k}x{k}x{k}_L2_truss_s{seed0 + i}", Domain(2 * k, k, k, 2, 1.0 / k),
                        seed0 + i, r0=0.045) for i, k in enumerate(ks)]
+
+
+def load_cases(dom: Domain, n: int = 8, seed0: int = 10):
+    """n load cases [(node_xyz (k, 3), comp (k,), val (k,))] with seeds seed0, seed0 + 1, ...:
+    even cases a unit point load at a random base-lattice point of the face x = 2 in a random
+    direction and sign; odd cases a uniform traction of total -1 in a random direction over all
+    base-lattice points of that face (corner, edge and interior points weighted 1/4, 1/2, 1)."""
+    s = 1 << dom.L
+    X = dom.nx * s
+    jj, kk = np.meshgrid(np.arange(dom.ny + 1) * s, np.arange(dom.nz + 1) * s, indexing="ij")
+    face = np.stack([np.full(jj.size, X), jj.ravel(), kk.ravel()], 1).astype(np.int64)
+    wy = np.where((jj.ravel() == 0) | (jj.ravel() == dom.ny * s), 0.5, 1.0)
+    wz = np.where((kk.ravel() == 0) | (kk.ravel() == dom.nz * s), 0.5, 1.0)
+    w = wy * wz
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng(seed0 + i)
+        comp = int(rng.integers(3))
+        if i % 2 == 0:
+            p = face[rng.integers(len(face))][None]
+            out.append((p, np.array([comp]), np.array([float(rng.choice([-1.0, 1.0]))])))
+        else:
+            out.append((face, np.full(len(face), comp), -w / w.sum()))
+    return out
 
 
 def unet_init(shapes, seed: int = 0):
