@@ -291,6 +291,7 @@ def run_gpu(args):
     precision = precision_report(P, ctx, rho_first, f, u_first, u64, solver) if args.reports else None
     batch = batch_report(P, W, solver) if (args.batch and args.reports) else None
     multi = multi_load_report(P, W, ctx, w, rho_first, Nn, solver) if (args.batch and args.reports) else None
+    tuned = autotune_report(P, W, ctx, w, rho_first, f, u_first, Nn) if (args.batch and args.reports) else None
     adapt = adaptation_timing(P, ctx, cur, d, Ne, dev) if args.reports else None
     adaptive = (adaptive_report(P, W, w, solver, args.adaptive_iters, args.remesh_every)
                 if (args.reports and args.adaptive_iters > 0) else None)
@@ -319,6 +320,7 @@ def run_gpu(args):
         "precision": precision,
         "batch": batch,
         "multi_load": multi,
+        "autotune": tuned,
         "adaptation": adapt,
         "adaptive_loop": adaptive,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -457,6 +459,24 @@ def multi_load_report(P, W, ctx, w, rho, Nn, solver):
             "sequential_s": seq_s, "lockstep_s": lock_s, "speedup": seq_s / lock_s}
 
 
+def autotune_report(P, W, ctx, w, rho, f, u0, Nn):
+    """The autotuner's choices for the benchmark system (check_every x smooth_sweeps of the
+    two-level solve from the first timed step's warm start) and for the 8 load cases (lockstep
+    group size); the bench itself runs the fixed defaults."""
+    import torch
+    from paper_1009_4975_gb300 import autotune as AT
+    best = AT.tune_solve(ctx, rho, f, u0, check_every=(8, 16, 32), smooth_sweeps=(1, 2), repeats=3)
+    cases = W.load_cases(w.dom, 8, 10)
+    F = torch.zeros((len(cases), 3 * Nn), dtype=torch.float64, device=rho.device)
+    for r, (nd, comp, val) in enumerate(cases):
+        fr = torch.zeros(3 * Nn, dtype=torch.float64, device=rho.device)
+        P.tm_build_rhs(ctx, nd, comp, val, fr)
+        F[r] = fr
+    bm = AT.tune_multi(ctx, rho, F, groups=(8, 4, 2), repeats=1, precond=P.TM_PRECOND_TWOLEVEL,
+                       smooth_sweeps=best["smooth_sweeps"], check_every=best["check_every"])
+    return {"solve": best, "multi_load": bm}
+
+
 def adaptation_timing(P, ctx, rho, d, Ne, dev):
     """Adaptation step on the benchmark mesh after the timed region (not part of a step): marks
     and both sweeps on the device (CUDA events), the new leaf set on the host, and Eq. 10 between
@@ -575,12 +595,15 @@ def run_profile_apply(args):
     perm = P.tm_mesh_tables(ctx)["perm"]
     rho = torch.as_tensor(w.rho[perm], device="cuda")
     gen = torch.Generator(device="cuda").manual_seed(7)
-    x = torch.randn(3 * info["Nn"], dtype=torch.float32, device="cuda", generator=gen)
+    dt = torch.float64 if args.profile_prec == 64 else torch.float32
+    x = torch.randn(3 * info["Nn"], dtype=dt, device="cuda", generator=gen)
     y = torch.zeros_like(x)
+    apply = P.tm_apply_K if args.profile_prec == 64 else P.tm_apply_K_f32
     for _ in range(args.profile_apply):
-        P.tm_apply_K_f32(ctx, rho, x, y)
+        apply(ctx, rho, x, y)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_apply": args.profile_apply, "elements": info["Ne"]}), flush=True)
+    print(json.dumps({"profile_apply": args.profile_apply, "precision": args.profile_prec, "elements": info["Ne"]}),
+          flush=True)
 
 
 def _sample_workload(w=None):
@@ -678,7 +701,9 @@ def main():
     ap.add_argument("--no-graphs", action="store_true",
                     help="plain kernel launches instead of CUDA-graph batches (for launch-list profiling)")
     ap.add_argument("--profile-apply", type=int, default=0,
-                    help="profiling workload: K FP32 operator applications on the benchmark mesh, no timing")
+                    help="profiling workload: K operator applications on the benchmark mesh, no timing")
+    ap.add_argument("--profile-prec", type=int, default=32, choices=[32, 64],
+                    help="profiling workload: FP32 (tm_apply_K_f32) or FP64 (tm_apply_K) operator")
     args = ap.parse_args()
     if args.profile_apply > 0:
         run_profile_apply(args)

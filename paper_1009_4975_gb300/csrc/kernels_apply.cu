@@ -102,19 +102,19 @@ __device__ __forceinline__ void issue_record(const uint4 *brec, const int32_t *r
   cp_async_commit();
 }
 
-// Node values of the block whose record is in `rec` into `R`.
+// Node values of the block whose record is in `rec` into `R`: consecutive threads copy
+// consecutive words (word w is component w % 3 of local node w / 3), so a run of consecutive node
+// ids is read with contiguous, coalesced requests.
 template <typename T>
 __device__ __forceinline__ void issue_values(const uint4 *rec, const T *x, T *R, bool valid) {
   if (valid) {
     const int *hdr = reinterpret_cast<const int *>(rec);
     const int nreg = hdr[2];
     const uint32_t *lnode = reinterpret_cast<const uint32_t *>(reinterpret_cast<const unsigned char *>(rec) + hdr[11]);
-    for (int i = threadIdx.x; i < nreg; i += kApplyThreads) {
+    for (int wd = threadIdx.x; wd < 3 * nreg; wd += kApplyThreads) {
+      const int i = wd / 3, c = wd - 3 * i;
       const uint32_t gw = lnode[i];
-      const bool fixed = gw >> 31;
-      const T *src = x + 3 * (size_t)(gw & 0x7FFFFFFFu);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) cp_async_small<sizeof(T)>(R + 3 * i + c, src + c, fixed);
+      cp_async_small<sizeof(T)>(R + wd, x + 3 * (size_t)(gw & 0x7FFFFFFFu) + c, (gw >> 31) != 0);
     }
   }
   cp_async_commit();
