@@ -350,8 +350,11 @@ int tm_filter(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double rm
               double *out_dev);
 
 /* Optimality-criteria update (Sec. 3): rho_new = clamp(rho (max(-dc,0)/(lambda V_e))^eta,
- * max(rho_min, rho - move), min(1, rho + move)) with lambda bisected until
- * sum rho_new V_e = volfrac * |Omega| (relative lambda bracket 1e-12).
+ * max(rho_min, rho - move), min(1, rho + move)) with lambda such that
+ * sum rho_new V_e = volfrac * |Omega|: found on the device by a safeguarded Newton search on
+ * the volume (a piecewise linear function of lambda^-eta), each step bracketing the root,
+ * until the relative lambda bracket is below 1e-12 (lambda is the bracket's midpoint) or a
+ * step hits the target volume exactly.
  * *change_out (host, may be NULL) receives max |rho_new - rho|. */
 int tm_oc_update(tm_ctx *ctx, const double *rho_dev, const double *dc_dev, double volfrac, double move,
                  double eta, double rho_min, double *rho_new_dev, double *change_out);

@@ -78,6 +78,7 @@ void release(std::vector<void *> &owned) {
 // concurrently (one stream).
 constexpr int kScalDoubles = 128;
 SolveScalars *solve_scalars(tm_ctx *c) { return reinterpret_cast<SolveScalars *>(c->w.scal); }
+static_assert(sizeof(OcState) <= 16 * sizeof(double), "the OC state must end before scalar 80");
 OcState *oc_state(tm_ctx *c) { return reinterpret_cast<OcState *>(c->w.scal + 64); }
 double *scal_at(tm_ctx *c, int i) { return c->w.scal + i; }
 
@@ -480,7 +481,7 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
   std::vector<void *> &wo = w.owned;
   int64_t &WB = w.bytes;
   const size_t nv = 3 * (size_t)m.Nn;
-  w.nred = (int64_t)m.nblk + (m.nsh + m.nh + 255) / 256 + 4 * 8 * (int64_t)device_sms() + 64;
+  w.nred = (int64_t)m.nblk + (m.nsh + m.nh + 255) / 256 + 8 * 8 * (int64_t)device_sms() + 64;
   TM_CUDA(ctx, alloc(wo, WB, &w.part64, 3 * (size_t)m.nslot));
   TM_CUDA(ctx, alloc(wo, WB, &w.part32, 3 * (size_t)m.nslot));
   TM_CUDA(ctx, alloc(wo, WB, &w.ce64, (size_t)m.Ne));
@@ -1447,9 +1448,25 @@ int tm_oc_update(tm_ctx *ctx, const double *rho_dev, const double *dc_dev, doubl
   s.target = volfrac * ctx->dm.volume;
   s.tol = 1e-12;
   TM_CUDA(ctx, cudaMemcpyAsync(oc_state(ctx), &s, sizeof(s), cudaMemcpyHostToDevice, ctx->stream));
-  TM_CUDA(ctx, launch_oc(ctx->dm, rho_dev, dc_dev, eta, move, rho_min, rho_new_dev, ctx->w.red, ctx->w.ticket + 4,
-                         oc_state(ctx), 200, ctx->stream));
-  ctx->launches += 202;
+  if (!ctx->w.octab) TM_CUDA(ctx, alloc(ctx->w.owned, ctx->w.bytes, &ctx->w.octab, (size_t)ctx->dm.Ne));
+  const DeviceMesh &m = ctx->dm;
+  double *part = ctx->w.red;
+  unsigned int *tk = ctx->w.ticket + 4;
+  TM_CUDA(ctx, launch_oc_init(m, rho_dev, dc_dev, eta, move, rho_min, ctx->w.octab, part, tk, oc_state(ctx),
+                              ctx->stream));
+  // the search usually ends within 10 launches; the state is read back between rounds of launches
+  // so that few launches run after it has ended (at most 64 in all)
+  int launched = 0;
+  for (int round = 0; round < 8; ++round) {
+    const int n = round == 0 ? 10 : 6;
+    TM_CUDA(ctx, launch_oc_search(m, eta, ctx->w.octab, part, tk, oc_state(ctx), n, ctx->stream));
+    launched += n;
+    TM_CUDA(ctx, cudaMemcpyAsync(&s, oc_state(ctx), sizeof(s), cudaMemcpyDeviceToHost, ctx->stream));
+    TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (s.done || launched >= 64) break;
+  }
+  TM_CUDA(ctx, launch_oc_final(m, rho_dev, eta, ctx->w.octab, rho_new_dev, part, tk, oc_state(ctx), ctx->stream));
+  ctx->launches += launched + 2;
   if (change_out) return read_scalar(ctx, &oc_state(ctx)->change, change_out);
   TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return TM_OK;

@@ -201,40 +201,32 @@ __global__ void l1diag_kernel(const float *K, int X, int Y, int Z, unsigned face
 }
 
 // ---------------------------------------------------------------- cycle
-// (A x) at DOF (I, c) from the <= 8 cells around node I; x is 0 at clamped nodes.
-__device__ __forceinline__ float cell_row_product(const float *K, const float *x, int i, int j, int k, int c, int X,
-                                                  int Y, int Z) {
+// Row (3 qi + c) of cell (cx, cy, cz) times the cell's x values: the part of (A x) at DOF (I, c)
+// that the cell contributes, qi being node I's corner in the cell; x is 0 at clamped nodes.
+__device__ __forceinline__ float cell_row_part(const float *K, const float *x, int cx, int cy, int cz, int qi, int c,
+                                               int X, int Y) {
+  const float4 *row = reinterpret_cast<const float4 *>(K + 576 * (int64_t)(cx + X * (cy + Y * cz)) + 24 * (3 * qi + c));
+  float v[24];
+#pragma unroll
+  for (int w = 0; w < 6; ++w) {
+    const float4 r4 = __ldg(row + w);
+    v[4 * w] = r4.x; v[4 * w + 1] = r4.y; v[4 * w + 2] = r4.z; v[4 * w + 3] = r4.w;
+  }
   float acc = 0.f;
-  for (int cz = k - 1; cz <= k; ++cz) {
-    if (cz < 0 || cz >= Z) continue;
-    for (int cy = j - 1; cy <= j; ++cy) {
-      if (cy < 0 || cy >= Y) continue;
-      for (int cx = i - 1; cx <= i; ++cx) {
-        if (cx < 0 || cx >= X) continue;
-        const int qi = (i - cx) + 2 * (j - cy) + 4 * (k - cz);
-        const float4 *row = reinterpret_cast<const float4 *>(K + 576 * (int64_t)(cx + X * (cy + Y * cz)) +
-                                                             24 * (3 * qi + c));
-        float v[24];
 #pragma unroll
-        for (int w = 0; w < 6; ++w) {
-          const float4 r4 = __ldg(row + w);
-          v[4 * w] = r4.x; v[4 * w + 1] = r4.y; v[4 * w + 2] = r4.z; v[4 * w + 3] = r4.w;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int J = (cx + (q & 1)) + (X + 1) * ((cy + ((q >> 1) & 1)) + (Y + 1) * (cz + (q >> 2)));
-          acc = fmaf(v[3 * q], x[3 * J], acc);
-          acc = fmaf(v[3 * q + 1], x[3 * J + 1], acc);
-          acc = fmaf(v[3 * q + 2], x[3 * J + 2], acc);
-        }
-      }
-    }
+  for (int q = 0; q < 8; ++q) {
+    const int J = (cx + (q & 1)) + (X + 1) * ((cy + ((q >> 1) & 1)) + (Y + 1) * (cz + (q >> 2)));
+    acc = fmaf(v[3 * q], x[3 * J], acc);
+    acc = fmaf(v[3 * q + 1], x[3 * J + 1], acc);
+    acc = fmaf(v[3 * q + 2], x[3 * J + 2], acc);
   }
   return acc;
 }
 
 // mode 0: out = b - A x (residual).  mode 1: out = x + dinv (b - A x) (an l1-Jacobi sweep).
-// mode 2: out = A x (b unused).
+// mode 2: out = A x (b unused).  Eight threads per DOF, one per cell around its node (slot q:
+// cell (i - 1 + q_x, j - 1 + q_y, k - 1 + q_z)), summed by a fixed shuffle tree over the eight, so
+// that the small levels still spread over many SMs and every thread has one cell row to load.
 __global__ void __launch_bounds__(kT) level_apply_kernel(const float *K, const float *x, const float *b,
                                                          const float *dinv, float *out, int X, int Y, int Z,
                                                          unsigned faces, int mode, Cases cs) {
@@ -245,20 +237,32 @@ __global__ void __launch_bounds__(kT) level_apply_kernel(const float *K, const f
   out += off;
   if (b) b += off;
   const int nodes = (X + 1) * (Y + 1) * (Z + 1);
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * nodes) return;
-  const int I = t / 3, c = t % 3;
-  const int i = I % (X + 1), j = (I / (X + 1)) % (Y + 1), k = I / ((X + 1) * (Y + 1));
-  if (lattice_fixed(i, j, k, X, Y, Z, faces)) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int t = (int)(g >> 3), q = (int)(g & 7);
+  const bool live = t < 3 * nodes;
+  bool fixed = true;
+  float part = 0.f;
+  if (live) {
+    const int I = t / 3, c = t % 3;
+    const int i = I % (X + 1), j = (I / (X + 1)) % (Y + 1), k = I / ((X + 1) * (Y + 1));
+    fixed = lattice_fixed(i, j, k, X, Y, Z, faces);
+    const int cx = i - 1 + (q & 1), cy = j - 1 + ((q >> 1) & 1), cz = k - 1 + (q >> 2);
+    if (!fixed && cx >= 0 && cx < X && cy >= 0 && cy < Y && cz >= 0 && cz < Z)
+      part = cell_row_part(K, x, cx, cy, cz, (i - cx) + 2 * (j - cy) + 4 * (k - cz), c, X, Y);
+  }
+  part += __shfl_xor_sync(0xffffffffu, part, 1);
+  part += __shfl_xor_sync(0xffffffffu, part, 2);
+  part += __shfl_xor_sync(0xffffffffu, part, 4);
+  if (!live || q != 0) return;
+  if (fixed) {
     out[t] = 0.f;
     return;
   }
-  const float ax = cell_row_product(K, x, i, j, k, c, X, Y, Z);
   if (mode == 2) {
-    out[t] = ax;
+    out[t] = part;
     return;
   }
-  const float r = b[t] - ax;
+  const float r = b[t] - part;
   out[t] = mode == 0 ? r : fmaf(dinv[t], r, x[t]);
 }
 
@@ -325,18 +329,22 @@ __global__ void __launch_bounds__(kT) level_prolong_kernel(const float *x_c, int
 }
 
 // Coarsest level: x = Ainv b over all of its DOFs (Ainv symmetric, zero rows and columns at
-// clamped DOFs).  One CTA; one warp per row (lanes stride the row, then a fixed shuffle tree).
-__global__ void __launch_bounds__(1024) dense_solve_kernel(const float *Ainv, const float *b, float *x, int n,
-                                                           Cases cs) {
-  const int cc = case_of(cs, blockIdx.x);
+// clamped DOFs).  kDenseRows rows per CTA (grid x) and one CTA row per load case (grid y); one
+// warp per row (lanes stride the row, then a fixed shuffle tree).
+constexpr int kDenseRows = 8;
+__global__ void __launch_bounds__(32 * kDenseRows) dense_solve_kernel(const float *Ainv, const float *b, float *x,
+                                                                      int n, Cases cs) {
+  const int cc = case_of(cs, blockIdx.y);
   if (case_done(cs, cc)) return;
   b += (int64_t)cc * n;
   x += (int64_t)cc * n;
   extern __shared__ float sb[];
   for (int i = threadIdx.x; i < n; i += blockDim.x) sb[i] = b[i];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = warp; r < n; r += nw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  {
+    const int r = blockIdx.x * kDenseRows + warp;
+    if (r >= n) return;
     const float *row = Ainv + (int64_t)r * n;
     float s = 0.f;
     for (int j = lane; j < n; j += 32) s = fmaf(row[j], sb[j], s);
@@ -597,20 +605,21 @@ static cudaError_t vcycle_from(const CoarseHierarchy &h, int l, int nu, const Ca
   const CoarseLevel &c = h.lev[l];
   if (l == h.nlev - 1) {
     const int n = 3 * c.nodes;
-    dense_solve_kernel<<<nv, 1024, n * sizeof(float), s>>>(h.Ainv, c.b, c.x, n, cs);
+    dense_solve_kernel<<<dim3((n + kDenseRows - 1) / kDenseRows, nv), 32 * kDenseRows, n * sizeof(float), s>>>(
+        h.Ainv, c.b, c.x, n, cs);
     *launches += 1;
     return cudaGetLastError();
   }
   const int n3 = 3 * c.nodes;
-  const dim3 gl(grid_for(n3), nv);
+  const dim3 gl(grid_for(n3), nv), ga(grid_for(8 * (int64_t)n3), nv);
   float *cur = c.x2, *oth = c.x;
   for (int k = 1; k < nu; ++k) {           // remaining pre-smoothing sweeps
-    level_apply_kernel<<<gl, kT, 0, s>>>(c.K, cur, c.b, c.dinv, oth, c.X, c.Y, c.Z, h.faces, 1, cs);
+    level_apply_kernel<<<ga, kT, 0, s>>>(c.K, cur, c.b, c.dinv, oth, c.X, c.Y, c.Z, h.faces, 1, cs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     std::swap(cur, oth);
     *launches += 1;
   }
-  level_apply_kernel<<<gl, kT, 0, s>>>(c.K, cur, c.b, c.dinv, c.t, c.X, c.Y, c.Z, h.faces, 0, cs);
+  level_apply_kernel<<<ga, kT, 0, s>>>(c.K, cur, c.b, c.dinv, c.t, c.X, c.Y, c.Z, h.faces, 0, cs);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const CoarseLevel &n = h.lev[l + 1];
   const bool sweep = l + 1 < h.nlev - 1;
@@ -624,7 +633,7 @@ static cudaError_t vcycle_from(const CoarseHierarchy &h, int l, int nu, const Ca
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *launches += 1;
   for (int k = 0; k < nu; ++k) {
-    level_apply_kernel<<<gl, kT, 0, s>>>(c.K, cur, c.b, c.dinv, oth, c.X, c.Y, c.Z, h.faces, 1, cs);
+    level_apply_kernel<<<ga, kT, 0, s>>>(c.K, cur, c.b, c.dinv, oth, c.X, c.Y, c.Z, h.faces, 1, cs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     std::swap(cur, oth);
     *launches += 1;
@@ -675,7 +684,7 @@ cudaError_t coarse_first_sweep_launch(const CoarseHierarchy &h, cudaStream_t s) 
 
 cudaError_t coarse_level_apply_launch(const CoarseHierarchy &h, int l, const float *x, float *y, cudaStream_t s) {
   const CoarseLevel &c = h.lev[l];
-  level_apply_kernel<<<grid_for(3 * (int64_t)c.nodes), kT, 0, s>>>(c.K, x, nullptr, c.dinv, y, c.X, c.Y, c.Z, h.faces,
+  level_apply_kernel<<<grid_for(24 * (int64_t)c.nodes), kT, 0, s>>>(c.K, x, nullptr, c.dinv, y, c.X, c.Y, c.Z, h.faces,
                                                                     2, Cases{nullptr, 0});
   return cudaGetLastError();
 }

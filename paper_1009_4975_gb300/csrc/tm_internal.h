@@ -223,6 +223,7 @@ struct Work {
   unsigned int *ticket = nullptr;  // last-block counters
   int *status = nullptr;       // device status word
   int8_t *mark_tmp = nullptr;  // Ne, intermediate adaptation marks
+  double4_32a *octab = nullptr;    // Ne, the OC update's per-element table (on first use)
   float *part_multi = nullptr; // kMaxRhs * 3 * nslot, partials of the multi-vector operator (on first use)
   // multi-load CG (on first use): per load case x, r, p, q (FP32) and the FP64 residual,
   // CG scalars, element-energy partials
