@@ -49,7 +49,7 @@ def _peaks():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for f in ("kernels_apply.cu", "element.cuh"):
+    for f in ("kernels_apply.cu", "element.cuh", "brick.cuh"):
         with open(os.path.join(ROOT, "paper_1009_4975_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -325,8 +325,8 @@ def run_gpu(args):
         "adaptive_loop": adaptive,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
-        "roofline": {"bound": "hbm", "kernel": "apply_blocks_kernel<float> (operator block pass; the partial "
-                     "sums of block-shared nodes are read by the CG update)", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "apply_blocks_kernel<float> (the operator: record-driven blocks "
+                     "and 4x4x4 equal-level bricks; the partial sums of shared nodes are read by the CG update)", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes": algo, "avg_ms": a_ms,
                      "launches_timed": prof["apply32_count"]},

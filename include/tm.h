@@ -82,10 +82,10 @@ typedef struct {
   int64_t n_free;             /* unknowns: 3 * (nodes neither hanging nor clamped) */
   int32_t n_blocks;           /* element blocks of the operator kernel            */
   int32_t max_local;          /* largest local-node count of a block              */
-  int64_t n_shared;           /* nodes touched by more than one block             */
+  int64_t n_shared;           /* nodes touched by more than one block or brick    */
   int64_t device_bytes;       /* device memory held for this mesh                 */
   int32_t max_block_bytes;    /* table bytes of the largest block (shared memory) */
-  int32_t pad_;
+  int32_t n_bricks;           /* 4x4x4 equal-level bricks taken by the brick pass  */
 } tm_mesh_info;
 
 typedef struct {
@@ -170,16 +170,29 @@ int tm_tables_copy(const tm_tables *t, int64_t *perm, int32_t *node_xyz, int32_t
 void tm_tables_free(tm_tables *t);
 /* Host-only export of the operator's block tables, for checking them without a GPU:
  * rec_off[n_blocks + 1] (record ranges in 16-byte units), brec[*rec_bytes] (the
- * per-block records the operator kernel stages: a header of 12 int32 -- first
+ * per-block records the operator kernel stages: a header of 16 int32 -- first
  * element, elements, regular and shared local nodes, hanging local nodes, inverse
- * entries, byte offsets of the lslot, hent, iptr, inv, lcorner and lnode sections --
- * then those sections), modal[72] (the element matrix of the unit cube in the
+ * entries, byte offsets of the lslot, hent, iptr, inv, lcorner, lnode and elist sections,
+ * three zeros -- then those sections; elist names the block's elements, ascending, which
+ * are the elements outside the bricks (tm_tables_bricks) taken in order), modal[72] (the element matrix of the unit cube in the
  * symmetry-adapted basis: 8 blocks of 3 x 3, row-major, block s couples the modes
  * s^1, s^2, s^4 of components 0, 1, 2), sh_node[n_shared] and sh_ptr[n_shared + 1]
  * (block-shared nodes and the ranges of their partials).  Any pointer may be NULL;
  * call with brec NULL to learn *rec_bytes first. */
 int tm_tables_operator(const tm_tables *t, int32_t *rec_off, uint8_t *brec, double *modal, int32_t *sh_node,
                        int32_t *sh_ptr, int64_t *rec_bytes);
+/* Host-only export of the brick tables (info->n_bricks bricks; any pointer may be NULL).  A brick
+ * is an aligned cube of 4x4x4 elements of one level, 64 consecutive elements in the canonical
+ * (Morton) order, element e0[i] + morton(x, y, z) at cube position (x, y, z); the blocks hold the
+ * other elements.  Its 5x5x5 node lattice, node (a, b, c) at a + 5 b + 25 c: node[125 i + ...]
+ * (global node id, bit 31 set at Dirichlet nodes), hax[...] (0 for a regular node; for a hanging
+ * node the axes, bits 0-2, along which it interpolates its masters, the lattice nodes one step
+ * away), out[...] (-1: the node's result is written to y by this brick alone; >= 0: the position
+ * of its partial in the shared-node pass, as sh_ptr ranges; -2: hanging), fold[...] (for a regular
+ * node, the lattice neighbours that are hanging nodes it is a master of: bit 2 a + (step > 0) the
+ * neighbour one step along axis a, hanging along a; bit 6 + 4 p + 2 (step1 > 0) + (step0 > 0) the
+ * diagonal neighbour in coordinate plane p = (x, y), (x, z), (y, z), hanging in that plane). */
+int tm_tables_bricks(const tm_tables *t, int32_t *e0, int32_t *node, uint8_t *hax, int32_t *out, uint32_t *fold);
 
 /* Host-only evaluation of a finite-element field of the tables' mesh at integer points
  * (the warm start after remeshing: the old displacement at the new mesh's nodes, see

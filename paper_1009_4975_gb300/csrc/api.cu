@@ -435,7 +435,8 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
   m.k0diag = h.K0[0];
   m.volume = (double)h.nx * h.ny * h.nz * h.h0 * h.h0 * h.h0;
   m.n_free = 3 * h.n_free_nodes;
-  m.nslot = h.blk_slot.empty() ? 0 : h.blk_slot.back();
+  m.nslot = h.nslot;
+  m.nbrick = h.nbrick;
   std::vector<void *> &o = m.owned;
   int64_t &B = m.bytes;
   TM_CUDA(ctx, upload(o, B, &m.leaf, h.leaf));
@@ -463,6 +464,7 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
   }
   TM_CUDA(ctx, upload(o, B, &m.rec_off, h.rec_off));
   m.max_rec_bytes = h.max_rec_bytes;
+  TM_CUDA(ctx, upload(o, B, &m.brick_tab, h.brick_tab));
   TM_CUDA(ctx, apply_residency(m, &m.resident_cta32, &m.resident_cta64));
   TM_CUDA(ctx, upload(o, B, &m.sh_node, h.sh_node));
   TM_CUDA(ctx, upload(o, B, &m.sh_ptr, h.sh_ptr));
@@ -481,7 +483,7 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
   std::vector<void *> &wo = w.owned;
   int64_t &WB = w.bytes;
   const size_t nv = 3 * (size_t)m.Nn;
-  w.nred = (int64_t)m.nblk + (m.nsh + m.nh + 255) / 256 + 8 * 8 * (int64_t)device_sms() + 64;
+  w.nred = (int64_t)apply_ctas(m) + (m.nsh + m.nh + 255) / 256 + 8 * 8 * (int64_t)device_sms() + 64;
   TM_CUDA(ctx, alloc(wo, WB, &w.part64, 3 * (size_t)m.nslot));
   TM_CUDA(ctx, alloc(wo, WB, &w.part32, 3 * (size_t)m.nslot));
   TM_CUDA(ctx, alloc(wo, WB, &w.ce64, (size_t)m.Ne));
@@ -513,7 +515,7 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
     info->n_shared = m.nsh;
     info->device_bytes = m.bytes + w.bytes;
     info->max_block_bytes = h.max_rec_bytes;
-    info->pad_ = 0;
+    info->n_bricks = m.nbrick;
   }
   return TM_OK;
 }
@@ -1198,7 +1200,7 @@ int tm_pcg_solve_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const doubl
     TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.mvec, (size_t)kMaxRhs * 4 * n));
     TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.mr64, (size_t)kMaxRhs * n));
     TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.msc, (size_t)kMaxRhs));
-    TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.mdotp, (size_t)kMaxRhs * std::max(m.nblk, 1)));
+    TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.mdotp, (size_t)kMaxRhs * std::max(apply_ctas(m), 1)));
     TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.mred, (size_t)kMaxRhs * pstride));
     TM_CUDA(ctx, alloc(w.owned, w.bytes, &w.mticket, (size_t)4 * kMaxRhs));
   }

@@ -3,6 +3,7 @@
 // and the dense inverse of the coarsest level.  Integer work and small dense algebra only.
 #include <algorithm>
 #include <cmath>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -163,6 +164,34 @@ void coarse_moment_matrices(double nu, std::vector<double> &Q) {
 // Dense inverse of the coarsest level's matrix (assembled from its FP64 cell matrices over the
 // free DOFs) by Cholesky factorisation; returned over all 3 (X+1)(Y+1)(Z+1) DOFs, with zero rows
 // and columns at clamped nodes.
+// a . b over n entries with four interleaved partial sums (a fixed order the compiler can vectorize)
+static double dot4(const double *a, const double *b, int n) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int k = 0;
+  for (; k + 4 <= n; k += 4) {
+    s0 += a[k] * b[k];
+    s1 += a[k + 1] * b[k + 1];
+    s2 += a[k + 2] * b[k + 2];
+    s3 += a[k + 3] * b[k + 3];
+  }
+  for (; k < n; ++k) s0 += a[k] * b[k];
+  return (s0 + s1) + (s2 + s3);
+}
+
+// f(i) for i in [0, n) on up to 8 host threads, rows dealt out round robin (row costs fall with i)
+template <typename F>
+static void parallel_rows(int n, F f) {
+  const int hw = (int)std::thread::hardware_concurrency();
+  const int nt = std::max(1, std::min({8, hw > 0 ? hw : 1, n / 32}));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t)
+    pool.emplace_back([&, t] {
+      for (int i = t; i < n; i += nt) f(i);
+    });
+  for (int i = 0; i < n; i += nt) f(i);
+  for (auto &th : pool) th.join();
+}
+
 std::string coarse_dense_inverse(const std::vector<double> &Kc, int X, int Y, int Z, unsigned faces,
                                  std::vector<float> &Ainv) {
   const int nodes = (X + 1) * (Y + 1) * (Z + 1), n = 3 * nodes;
@@ -192,43 +221,37 @@ std::string coarse_dense_inverse(const std::vector<double> &Kc, int X, int Y, in
             for (int s = 0; s < 24; ++s)
               if (dof[s] >= 0) A[(size_t)dof[r] * nf + dof[s]] += K[r * 24 + s];
       }
-  // Cholesky A = L L^T (lower triangle in place)
+  // Cholesky A = L L^T (lower triangle in place), rows of L contiguous
   for (int j = 0; j < nf; ++j) {
-    double d = A[(size_t)j * nf + j];
-    for (int k = 0; k < j; ++k) d -= A[(size_t)j * nf + k] * A[(size_t)j * nf + k];
+    const double *lj = &A[(size_t)j * nf];
+    const double d = A[(size_t)j * nf + j] - dot4(lj, lj, j);
     if (!(d > 0)) return "the coarsest level's matrix is not positive definite";
     const double ljj = std::sqrt(d);
     A[(size_t)j * nf + j] = ljj;
     for (int i = j + 1; i < nf; ++i) {
-      double s = A[(size_t)i * nf + j];
-      for (int k = 0; k < j; ++k) s -= A[(size_t)i * nf + k] * A[(size_t)j * nf + k];
-      A[(size_t)i * nf + j] = s / ljj;
+      const double *li = &A[(size_t)i * nf];
+      A[(size_t)i * nf + j] = (A[(size_t)i * nf + j] - dot4(li, lj, j)) / ljj;
     }
   }
-  // Y = L^-1 (lower triangular), row by row: Y[i, :] = (e_i - sum_{k<i} L[i, k] Y[k, :]) / L[i, i];
-  // then A^-1 = Y^T Y, accumulated one row of Y at a time (contiguous inner loops).
-  std::vector<double> Yl((size_t)nf * nf, 0.0), inv((size_t)nf * nf, 0.0);
-  for (int i = 0; i < nf; ++i) {
-    double *yi = &Yl[(size_t)i * nf];
-    yi[i] = 1.0;
-    for (int k = 0; k < i; ++k) {
-      const double l = A[(size_t)i * nf + k];
-      if (l == 0.0) continue;
-      const double *yk = &Yl[(size_t)k * nf];
-      for (int c = 0; c <= k; ++c) yi[c] -= l * yk[c];
+  // Yt = (L^-1)^T, one column of L^-1 per row of Yt: forward substitution with e_c, entries
+  // below c only; then A^-1 = Yt Yt^T restricted to the lower triangle and mirrored.  The columns
+  // and the rows of the product are independent: they are spread over host threads, each entry
+  // computed by one thread in a fixed order (the result does not depend on the thread count).
+  std::vector<double> Yt((size_t)nf * nf, 0.0), inv((size_t)nf * nf, 0.0);
+  parallel_rows(nf, [&](int c) {
+    double *y = &Yt[(size_t)c * nf];
+    y[c] = 1.0 / A[(size_t)c * nf + c];
+    for (int i = c + 1; i < nf; ++i) {
+      const double *li = &A[(size_t)i * nf];
+      y[i] = -dot4(li + c, y + c, i - c) / li[i];
     }
-    const double d = 1.0 / A[(size_t)i * nf + i];
-    for (int c = 0; c <= i; ++c) yi[c] *= d;
-  }
-  for (int k = 0; k < nf; ++k) {
-    const double *yk = &Yl[(size_t)k * nf];
-    for (int r = 0; r <= k; ++r) {
-      const double a = yk[r];
-      if (a == 0.0) continue;
-      double *ir = &inv[(size_t)r * nf];
-      for (int c = 0; c <= k; ++c) ir[c] += a * yk[c];
-    }
-  }
+  });
+  parallel_rows(nf, [&](int r) {
+    const double *yr = &Yt[(size_t)r * nf];
+    for (int c = 0; c <= r; ++c) inv[(size_t)r * nf + c] = dot4(yr + r, &Yt[(size_t)c * nf] + r, nf - r);
+  });
+  for (int r = 0; r < nf; ++r)
+    for (int c = r + 1; c < nf; ++c) inv[(size_t)r * nf + c] = inv[(size_t)c * nf + r];
   Ainv.assign((size_t)n * n, 0.f);
   for (int r = 0; r < n; ++r)
     if (fmap[r] >= 0)

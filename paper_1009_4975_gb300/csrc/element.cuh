@@ -53,8 +53,101 @@ __device__ __forceinline__ void bwd_stage(T v[8], int bit) {
 // MODE 2: both, returning coef X^T K0 X (a sum of per-block quadratic forms of
 // positive semidefinite blocks, free of the cancellation of X . Y).
 constexpr int kOpApply = 0, kOpEnergy = 1, kOpBoth = 2;
+
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+// FP32: components 0 and 1 of every corner travel as one packed pair through the butterflies and
+// the coefficient scaling (add.rn.f32x2 / fma.rn.f32x2: each half rounds as its scalar
+// counterpart), component 2 as a scalar; the 3x3 blocks are scalar FMA chains.
+template <int MODE>
+__device__ __forceinline__ float element_op_f32x2(const float X[24], float Y[24], float coef,
+                                                  const ModalBlocks<float> &M) {
+  constexpr bool WANT_ENERGY = MODE != kOpApply;
+  constexpr bool WANT_Y = MODE != kOpEnergy;
+  const float2 neg1 = make_float2(-1.f, -1.f);
+  float2 p[8];
+  float z[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    p[k] = make_float2(X[3 * k], X[3 * k + 1]);
+    z[k] = X[3 * k + 2];
+  }
+#pragma unroll
+  for (int bit = 1; bit < 8; bit <<= 1)
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (!(k & bit)) {
+        const float2 a = p[k], b = p[k | bit];
+        p[k] = __fadd2_rn(a, b);
+        p[k | bit] = __ffma2_rn(a, neg1, b);     // b - a
+        const float c = z[k], d = z[k | bit];
+        z[k] = c + d;
+        z[k | bit] = d - c;
+      }
+  float2 qp[8];
+  float qz[8];
+  float energy = 0.f;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const float a0 = p[s ^ 1].x, a1 = p[s ^ 2].y, a2 = z[s ^ 4];
+    float r0, r1, r2;
+    if (s == 1) {        // component 0 of this block is a translation
+      r0 = 0.f;
+      r1 = fmaf(M.b[s][1][2], a2, M.b[s][1][1] * a1);
+      r2 = fmaf(M.b[s][2][2], a2, M.b[s][2][1] * a1);
+    } else if (s == 2) {
+      r0 = fmaf(M.b[s][0][2], a2, M.b[s][0][0] * a0);
+      r1 = 0.f;
+      r2 = fmaf(M.b[s][2][2], a2, M.b[s][2][0] * a0);
+    } else if (s == 4) {
+      r0 = fmaf(M.b[s][0][1], a1, M.b[s][0][0] * a0);
+      r1 = fmaf(M.b[s][1][1], a1, M.b[s][1][0] * a0);
+      r2 = 0.f;
+    } else {
+      r0 = fmaf(M.b[s][0][2], a2, fmaf(M.b[s][0][1], a1, M.b[s][0][0] * a0));
+      r1 = fmaf(M.b[s][1][2], a2, fmaf(M.b[s][1][1], a1, M.b[s][1][0] * a0));
+      r2 = fmaf(M.b[s][2][2], a2, fmaf(M.b[s][2][1], a1, M.b[s][2][0] * a0));
+    }
+    if (WANT_ENERGY) energy = fmaf(a2, r2, fmaf(a1, r1, fmaf(a0, r0, energy)));
+    if (WANT_Y) {
+      qp[s ^ 1].x = r0;
+      qp[s ^ 2].y = r1;
+      qz[s ^ 4] = r2;
+    }
+  }
+  if (!WANT_Y) return energy;
+  const float2 cc = make_float2(coef, coef);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    qp[k] = __fmul2_rn(qp[k], cc);
+    qz[k] *= coef;
+  }
+#pragma unroll
+  for (int bit = 1; bit < 8; bit <<= 1)
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (!(k & bit)) {
+        const float2 sv = qp[k], dv = qp[k | bit];
+        qp[k] = __ffma2_rn(dv, neg1, sv);       // s - d
+        qp[k | bit] = __fadd2_rn(sv, dv);
+        const float c = qz[k], d = qz[k | bit];
+        qz[k] = c - d;
+        qz[k | bit] = c + d;
+      }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    Y[3 * k] = qp[k].x;
+    Y[3 * k + 1] = qp[k].y;
+    Y[3 * k + 2] = qz[k];
+  }
+  return WANT_ENERGY ? coef * energy : 0.f;
+}
+#endif
+
 template <typename T, int MODE>
 __device__ __forceinline__ T element_op(const T X[24], T Y[24], T coef, const ModalBlocks<T> &M) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  if constexpr (sizeof(T) == 4) return element_op_f32x2<MODE>(X, Y, coef, M);
+#endif
   constexpr bool WANT_ENERGY = MODE != kOpApply;
   constexpr bool WANT_Y = MODE != kOpEnergy;
   T w[3][8];

@@ -30,8 +30,10 @@
 #include <atomic>
 #include <mutex>
 
+#include "brick.cuh"
 #include "element.cuh"
 #include "pcg.cuh"
+#include "pdl.cuh"
 #include "reduce.cuh"
 #include "tm_internal.h"
 
@@ -57,6 +59,7 @@ struct ApplyParams {
   int max_local;    // local nodes of the largest block
   int rec_bytes;    // record buffer size (largest record, multiple of 16)
   int ahead;        // CTAs resident on the GPU: block b prefetches the record of b + ahead into L2
+  BrickTables bricks;  // CTAs nblk .. take 4 bricks each (brick.cuh)
 };
 
 
@@ -71,7 +74,7 @@ __host__ __device__ __forceinline__ size_t xy_bytes() {
 }
 template <typename T>
 size_t apply_smem_bytes(int max_local, int rec_bytes) {
-  return xy_bytes<T>() + val_buf_bytes<T>(max_local) + (size_t)rec_bytes;
+  return std::max(xy_bytes<T>() + val_buf_bytes<T>(max_local) + (size_t)rec_bytes, brick_smem_bytes<T>());
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -123,8 +126,15 @@ __device__ __forceinline__ void issue_values(const uint4 *rec, const T *x, T *R,
 template <typename T>
 __global__ void __launch_bounds__(kApplyThreads, (sizeof(T) == 4 ? 4 : 2) * 256 / kApplyThreads)
     apply_blocks_kernel(ApplyParams<T> P) {
+  pdl_begin();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (P.done && *(volatile const int *)P.done) return;
+  double dot = 0.0;
+  if (blockIdx.x >= P.nblk) {
+    const int brick = (blockIdx.x - P.nblk) * kBricksPerCta + threadIdx.x / kBrickElems;
+    if (P.dotp) dot = brick_pass<T, true>(P.bricks, brick, P.ce, P.x, P.y, P.part, P.K, smem_raw);
+    else brick_pass<T, false>(P.bricks, brick, P.ce, P.x, P.y, P.part, P.K, smem_raw);
+  } else {
   T *XY = reinterpret_cast<T *>(smem_raw);
   T *R = reinterpret_cast<T *>(smem_raw + xy_bytes<T>());
   uint4 *rec = reinterpret_cast<uint4 *>(smem_raw + xy_bytes<T>() + val_buf_bytes<T>(P.max_local));
@@ -146,13 +156,14 @@ __global__ void __launch_bounds__(kApplyThreads, (sizeof(T) == 4 ? 4 : 2) * 256 
 
   const int *hdr = reinterpret_cast<const int *>(rec);
   const unsigned char *rb = reinterpret_cast<const unsigned char *>(rec);
-  const int e0 = hdr[0], ne = hdr[1], nreg = hdr[2], nshared = hdr[3], nhang = hdr[4];
+  const int ne = hdr[1], nreg = hdr[2], nshared = hdr[3], nhang = hdr[4];
   const int *lslot = reinterpret_cast<const int *>(rb + hdr[6]);
   const uint2 *hent = reinterpret_cast<const uint2 *>(rb + hdr[7]);
   const uint16_t *ip = reinterpret_cast<const uint16_t *>(rb + hdr[8]);
   const uint16_t *iv = reinterpret_cast<const uint16_t *>(rb + hdr[9]);
   const uint4 *lcorner = reinterpret_cast<const uint4 *>(rb + hdr[10]);
   const uint32_t *lnode = reinterpret_cast<const uint32_t *>(rb + hdr[11]);
+  const int *elist = reinterpret_cast<const int *>(rb + hdr[12]);
 
   // 1. hanging nodes: (bi)linear interpolation of their masters (C)
   for (int j = tid; j < nhang; j += kApplyThreads) {
@@ -172,7 +183,6 @@ __global__ void __launch_bounds__(kApplyThreads, (sizeof(T) == 4 ? 4 : 2) * 256 
   // 2. element operator: gather the 8 corners, results into the slots; x^T A x is
   // the sum of the element energies c_e X_e^T K0 X_e (C and the Dirichlet zeros are
   // already in X_e)
-  double dot = 0.0;
   if (tid < ne) {
     const uint4 cw = lcorner[tid];
     const int code[8] = {(int)(cw.x & 0xFFFF), (int)(cw.x >> 16), (int)(cw.y & 0xFFFF), (int)(cw.y >> 16),
@@ -184,8 +194,8 @@ __global__ void __launch_bounds__(kApplyThreads, (sizeof(T) == 4 ? 4 : 2) * 256 
       X[3 * k + 1] = R[3 * code[k] + 1];
       X[3 * k + 2] = R[3 * code[k] + 2];
     }
-    if (P.dotp) dot = (double)element_op<T, kOpBoth>(X, Y, P.ce[e0 + tid], P.K);
-    else element_op<T, kOpApply>(X, Y, P.ce[e0 + tid], P.K);
+    if (P.dotp) dot = (double)element_op<T, kOpBoth>(X, Y, P.ce[elist[tid]], P.K);
+    else element_op<T, kOpApply>(X, Y, P.ce[elist[tid]], P.K);
 #pragma unroll
     for (int j = 0; j < 24; ++j) XY[tid * kRow + j] = Y[j];
   }
@@ -227,12 +237,13 @@ __global__ void __launch_bounds__(kApplyThreads, (sizeof(T) == 4 ? 4 : 2) * 256 
       dst[0] = s0; dst[1] = s1; dst[2] = s2;
     }
   }
+  }
   if (P.dotp) {
     dot = block_sum<kApplyThreads>(dot);
-    if (tid == 0) P.dotp[b] = dot;
+    if (threadIdx.x == 0) P.dotp[blockIdx.x] = dot;
     if (P.sc && last_cta(P.ticket)) {
       const double pq = sum_partials<kApplyThreads>(P.dotp, gridDim.x);
-      if (tid == 0) {
+      if (threadIdx.x == 0) {
         P.sc->pq = pq;
         P.sc->alpha = P.sc->rz / pq;
         if (!isfinite(pq) || !isfinite(P.sc->alpha) || pq <= 0.0) {
@@ -251,6 +262,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) apply_shared_kernel(const int32_t *sh_node, const int32_t *sh_ptr, int64_t nsh,
                                                            const int32_t *hang_node, int64_t nh, const T *part, T *y,
                                                            const int *done) {
+  pdl_begin();
   if (done && *(volatile const int *)done) return;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < nsh) {
@@ -324,7 +336,8 @@ cudaError_t launch_apply_blocks(const DeviceMesh &m, const T *ce, const T *x, T 
   P.dotp = energy_partials; P.sc = sc; P.ticket = ticket; P.done = done; P.nblk = m.nblk;
   for (int i = 0; i < 72; ++i) (&P.K.b[0][0][0])[i] = (T)m.modal[i];
   P.max_local = m.max_local; P.rec_bytes = rec_bytes; P.ahead = ahead;
-  if (m.nblk > 0) apply_blocks_kernel<T><<<m.nblk, kApplyThreads, smem, s>>>(P);
+  P.bricks = BrickTables{m.brick_tab, m.nbrick};
+  if (apply_ctas(m) > 0) { const cudaError_t pe_ = launch_pdl(apply_blocks_kernel<T>, dim3(apply_ctas(m)), dim3(kApplyThreads), smem, s, P); if (pe_ != cudaSuccess) return pe_; }
   return cudaGetLastError();
 }
 
@@ -335,8 +348,8 @@ cudaError_t launch_apply(const DeviceMesh &m, const T *ce, const T *x, T *y, T *
   cudaError_t e = launch_apply_blocks<T>(m, ce, x, y, part, dot_partials, sc, ticket, done, s);
   if (e != cudaSuccess) return e;
   const int64_t items = m.nsh + (zero_hanging ? m.nh : 0);
-  apply_shared_kernel<T><<<item_grid(items), 256, 0, s>>>(m.sh_node, m.sh_ptr, m.nsh, m.hang_node,
-                                                          zero_hanging ? m.nh : 0, part, y, done);
+  { const cudaError_t pe_ = launch_pdl(apply_shared_kernel<T>, dim3(item_grid(items)), dim3(256), 0, s, m.sh_node, m.sh_ptr, m.nsh, m.hang_node,
+                                                          zero_hanging ? m.nh : 0, part, y, done); if (pe_ != cudaSuccess) return pe_; }
   return cudaGetLastError();
 }
 

@@ -31,6 +31,7 @@
 #include <utility>
 
 #include "pcg.cuh"
+#include "pdl.cuh"
 #include "reduce.cuh"
 #include "tm_internal.h"
 
@@ -230,6 +231,7 @@ __device__ __forceinline__ float cell_row_part(const float *K, const float *x, i
 __global__ void __launch_bounds__(kT) level_apply_kernel(const float *K, const float *x, const float *b,
                                                          const float *dinv, float *out, int X, int Y, int Z,
                                                          unsigned faces, int mode, Cases cs) {
+  pdl_begin();
   const int cc = case_of(cs, blockIdx.y);
   if (case_done(cs, cc)) return;
   const int64_t off = cc * lattice_len(X, Y, Z);
@@ -272,6 +274,7 @@ __global__ void __launch_bounds__(kT) level_apply_kernel(const float *K, const f
 __global__ void __launch_bounds__(kT) level_restrict_kernel(const float *t_f, int Xf, int Yf, int Zf, int X, int Y,
                                                             int Z, unsigned faces, float *b_c, const float *dinv_c,
                                                             float *x_c, Cases cs) {
+  pdl_begin();
   const int cc = case_of(cs, blockIdx.y);
   if (case_done(cs, cc)) return;
   t_f += cc * lattice_len(Xf, Yf, Zf);
@@ -307,6 +310,7 @@ __global__ void __launch_bounds__(kT) level_restrict_kernel(const float *t_f, in
 // interpolation from the halved lattice.
 __global__ void __launch_bounds__(kT) level_prolong_kernel(const float *x_c, int Xc, int Yc, int Zc, int X, int Y,
                                                            int Z, unsigned faces, float *x_f, Cases cs) {
+  pdl_begin();
   const int cc = case_of(cs, blockIdx.y);
   if (case_done(cs, cc)) return;
   x_c += cc * lattice_len(Xc, Yc, Zc);
@@ -334,6 +338,7 @@ __global__ void __launch_bounds__(kT) level_prolong_kernel(const float *x_c, int
 constexpr int kDenseRows = 8;
 __global__ void __launch_bounds__(32 * kDenseRows) dense_solve_kernel(const float *Ainv, const float *b, float *x,
                                                                       int n, Cases cs) {
+  pdl_begin();
   const int cc = case_of(cs, blockIdx.y);
   if (case_done(cs, cc)) return;
   b += (int64_t)cc * n;
@@ -371,6 +376,7 @@ __device__ __forceinline__ void trilinear8(uint32_t code, int L, float w[8]) {
 // faces of the domain.  Lane sums, then a fixed shuffle tree.
 __global__ void fine_restrict_cells_kernel(const float *r, int64_t r_ld, const int32_t *seg_ptr, const int32_t *cnode,
                                            const uint32_t *code, int nseg, int L, float *part, Cases cs) {
+  pdl_begin();
   const int cc = case_of(cs, blockIdx.y);
   if (case_done(cs, cc)) return;
   r += cc * r_ld;
@@ -396,18 +402,23 @@ __global__ void fine_restrict_cells_kernel(const float *r, int64_t r_ld, const i
       acc[3 * q + 2] = fmaf(w[q], r2, acc[3 * q + 2]);
     }
   }
+  // reduce-scatter over the warp: at each halving step a lane keeps the half of its sums that its
+  // lane bit selects and adds its partner's copy of that half, so that lane l ends with the warp
+  // total of sum l (16 + 8 + 4 + 2 + 1 shuffles instead of 24 x 5; sums 24..31 are zero)
+  float v[32];
 #pragma unroll
-  for (int q = 0; q < 24; ++q) {
+  for (int q = 0; q < 32; ++q) v[q] = q < 24 ? acc[q] : 0.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+  for (int h = 16; h > 0; h >>= 1) {
+    const bool upper = (lane & h) != 0;
+#pragma unroll
+    for (int q = 0; q < h; ++q) {
+      const float keep = upper ? v[q + h] : v[q];
+      const float send = upper ? v[q] : v[q + h];
+      v[q] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
   }
-  if (lane < 24) {
-    float v = 0.f;
-#pragma unroll
-    for (int q = 0; q < 24; ++q)
-      if (q == lane) v = acc[q];
-    part[24 * (int64_t)warp + lane] = v;
-  }
+  if (lane < 24) part[24 * (int64_t)warp + lane] = v[0];
 }
 
 // Stage 2: each level-0 DOF sums the partials of its <= 8 cells' segments (fixed order); with dinv
@@ -415,6 +426,7 @@ __global__ void fine_restrict_cells_kernel(const float *r, int64_t r_ld, const i
 __global__ void __launch_bounds__(kT) fine_restrict_nodes_kernel(const float *part, int nseg, const int32_t *cseg,
                                                                  int X, int Y, int Z, unsigned faces, float *b,
                                                                  const float *dinv, float *x, Cases cs) {
+  pdl_begin();
   const int cc = case_of(cs, blockIdx.y);
   if (case_done(cs, cc)) return;
   part += (int64_t)cc * nseg * 24;
@@ -479,6 +491,7 @@ __global__ void fine_prolong_kernel(const float *v, const int32_t *ncell, const 
 __global__ void __launch_bounds__(kT) finish_kernel(const float *b0, const float *x0, int n, int mode,
                                                     SolveScalars *sc_all, int c0, double *partials_all,
                                                     int pstride, unsigned int *tickets) {
+  pdl_begin();
   const int cc = c0 + blockIdx.y;
   SolveScalars *sc = sc_all + cc;
   if (sc->done) return;
@@ -520,6 +533,7 @@ __global__ void __launch_bounds__(kT) pupdate2_kernel(float *p, const float *r, 
                                                       const float *x0, int64_t x0_ld, const int32_t *ncell,
                                                       const uint32_t *code, int64_t Nn, int L, int X, int Y, int mode,
                                                       const SolveScalars *sc_all, int c0) {
+  pdl_begin();
   const int cc = c0 + blockIdx.y;
   const SolveScalars *sc = sc_all + cc;
   if (sc->done) return;
@@ -586,13 +600,13 @@ cudaError_t coarse_restrict_launch(const DeviceMesh &m, const CoarseHierarchy &h
   const CoarseLevel &l0 = h.lev[0];
   const Cases cs{sc, c0};
   const dim3 g1(grid_for(32 * (int64_t)h.nseg), nv);
-  fine_restrict_cells_kernel<<<g1, kT, 0, s>>>(r, r_ld, h.seg_ptr, h.cnode, h.code, h.nseg, m.L, h.part, cs);
+  { const cudaError_t pe_ = launch_pdl(fine_restrict_cells_kernel, dim3(g1), dim3(kT), 0, s, r, r_ld, h.seg_ptr, h.cnode, h.code, h.nseg, m.L, h.part, cs); if (pe_ != cudaSuccess) return pe_; }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const bool sweep = first_sweep && h.nlev > 1;
   const dim3 g2(grid_for(3 * (int64_t)l0.nodes), nv);
-  fine_restrict_nodes_kernel<<<g2, kT, 0, s>>>(h.part, h.nseg, h.cseg, l0.X, l0.Y, l0.Z, h.faces, l0.b,
-                                               sweep ? l0.dinv : nullptr, sweep ? l0.x2 : nullptr, cs);
+  { const cudaError_t pe_ = launch_pdl(fine_restrict_nodes_kernel, dim3(g2), dim3(kT), 0, s, h.part, h.nseg, h.cseg, l0.X, l0.Y, l0.Z, h.faces, l0.b,
+                                               sweep ? l0.dinv : nullptr, sweep ? l0.x2 : nullptr, cs); if (pe_ != cudaSuccess) return pe_; }
   return cudaGetLastError();
 }
 
@@ -605,8 +619,8 @@ static cudaError_t vcycle_from(const CoarseHierarchy &h, int l, int nu, const Ca
   const CoarseLevel &c = h.lev[l];
   if (l == h.nlev - 1) {
     const int n = 3 * c.nodes;
-    dense_solve_kernel<<<dim3((n + kDenseRows - 1) / kDenseRows, nv), 32 * kDenseRows, n * sizeof(float), s>>>(
-        h.Ainv, c.b, c.x, n, cs);
+    { const cudaError_t pe_ = launch_pdl(dense_solve_kernel, dim3(dim3((n + kDenseRows - 1) / kDenseRows, nv)), dim3(32 * kDenseRows), n * sizeof(float), s, 
+        h.Ainv, c.b, c.x, n, cs); if (pe_ != cudaSuccess) return pe_; }
     *launches += 1;
     return cudaGetLastError();
   }
@@ -614,26 +628,26 @@ static cudaError_t vcycle_from(const CoarseHierarchy &h, int l, int nu, const Ca
   const dim3 gl(grid_for(n3), nv), ga(grid_for(8 * (int64_t)n3), nv);
   float *cur = c.x2, *oth = c.x;
   for (int k = 1; k < nu; ++k) {           // remaining pre-smoothing sweeps
-    level_apply_kernel<<<ga, kT, 0, s>>>(c.K, cur, c.b, c.dinv, oth, c.X, c.Y, c.Z, h.faces, 1, cs);
+    { const cudaError_t pe_ = launch_pdl(level_apply_kernel, dim3(ga), dim3(kT), 0, s, c.K, cur, c.b, c.dinv, oth, c.X, c.Y, c.Z, h.faces, 1, cs); if (pe_ != cudaSuccess) return pe_; }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     std::swap(cur, oth);
     *launches += 1;
   }
-  level_apply_kernel<<<ga, kT, 0, s>>>(c.K, cur, c.b, c.dinv, c.t, c.X, c.Y, c.Z, h.faces, 0, cs);
+  { const cudaError_t pe_ = launch_pdl(level_apply_kernel, dim3(ga), dim3(kT), 0, s, c.K, cur, c.b, c.dinv, c.t, c.X, c.Y, c.Z, h.faces, 0, cs); if (pe_ != cudaSuccess) return pe_; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const CoarseLevel &n = h.lev[l + 1];
   const bool sweep = l + 1 < h.nlev - 1;
   const dim3 gn(grid_for(3 * (int64_t)n.nodes), nv);
-  level_restrict_kernel<<<gn, kT, 0, s>>>(c.t, c.X, c.Y, c.Z, n.X, n.Y, n.Z, h.faces, n.b, sweep ? n.dinv : nullptr,
-                                          sweep ? n.x2 : nullptr, cs);
+  { const cudaError_t pe_ = launch_pdl(level_restrict_kernel, dim3(gn), dim3(kT), 0, s, c.t, c.X, c.Y, c.Z, n.X, n.Y, n.Z, h.faces, n.b, sweep ? n.dinv : nullptr,
+                                          sweep ? n.x2 : nullptr, cs); if (pe_ != cudaSuccess) return pe_; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *launches += 2;
   if ((e = vcycle_from(h, l + 1, nu, cs, nv, s, launches)) != cudaSuccess) return e;
-  level_prolong_kernel<<<gl, kT, 0, s>>>(n.x, n.X, n.Y, n.Z, c.X, c.Y, c.Z, h.faces, cur, cs);
+  { const cudaError_t pe_ = launch_pdl(level_prolong_kernel, dim3(gl), dim3(kT), 0, s, n.x, n.X, n.Y, n.Z, c.X, c.Y, c.Z, h.faces, cur, cs); if (pe_ != cudaSuccess) return pe_; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *launches += 1;
   for (int k = 0; k < nu; ++k) {
-    level_apply_kernel<<<ga, kT, 0, s>>>(c.K, cur, c.b, c.dinv, oth, c.X, c.Y, c.Z, h.faces, 1, cs);
+    { const cudaError_t pe_ = launch_pdl(level_apply_kernel, dim3(ga), dim3(kT), 0, s, c.K, cur, c.b, c.dinv, oth, c.X, c.Y, c.Z, h.faces, 1, cs); if (pe_ != cudaSuccess) return pe_; }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     std::swap(cur, oth);
     *launches += 1;
@@ -652,7 +666,7 @@ cudaError_t coarse_finish_launch(const CoarseHierarchy &h, int mode, SolveScalar
   int g = grid_for(n);
   if (g > 4 * device_sms()) g = 4 * device_sms();   // one grid for every caller: the same reduction order
   if (g > pstride) return cudaErrorInvalidValue;
-  finish_kernel<<<dim3(g, nv), kT, 0, s>>>(h.lev[0].b, h.lev[0].x, n, mode, sc, c0, partials, pstride, tickets);
+  { const cudaError_t pe_ = launch_pdl(finish_kernel, dim3(dim3(g, nv)), dim3(kT), 0, s, h.lev[0].b, h.lev[0].x, n, mode, sc, c0, partials, pstride, tickets); if (pe_ != cudaSuccess) return pe_; }
   return cudaGetLastError();
 }
 
@@ -661,8 +675,8 @@ cudaError_t coarse_pupdate_launch(const DeviceMesh &m, const CoarseHierarchy &h,
                                   cudaStream_t s) {
   int g = grid_for(m.Nn);
   if (g > 8 * device_sms()) g = 8 * device_sms();
-  pupdate2_kernel<<<dim3(g, nv), kT, 0, s>>>(p, r, ld, dinv, h.lev[0].x, 3 * (int64_t)h.lev[0].nodes, h.ncell, h.code,
-                                             m.Nn, m.L, h.lev[0].X, h.lev[0].Y, mode, sc, c0);
+  { const cudaError_t pe_ = launch_pdl(pupdate2_kernel, dim3(dim3(g, nv)), dim3(kT), 0, s, p, r, ld, dinv, h.lev[0].x, 3 * (int64_t)h.lev[0].nodes, h.ncell, h.code,
+                                             m.Nn, m.L, h.lev[0].X, h.lev[0].Y, mode, sc, c0); if (pe_ != cudaSuccess) return pe_; }
   return cudaGetLastError();
 }
 

@@ -11,8 +11,10 @@
 
 #include <mutex>
 
+#include "brick.cuh"
 #include "element.cuh"
 #include "pcg.cuh"
+#include "pdl.cuh"
 #include "reduce.cuh"
 #include "tm_internal.h"
 
@@ -55,9 +57,12 @@ struct MultiParams {
   unsigned int *ticket;
   ModalBlocks<float> K;
   int nr, max_local;
+  int nblk;             // CTAs nblk .. take 4 bricks each (brick.cuh), vector after vector
+  BrickTables bricks;
 };
 
 __global__ void __launch_bounds__(kThreads, 2) apply_blocks_multi_kernel(MultiParams P) {
+  pdl_begin();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float *XY = reinterpret_cast<float *>(smem_raw);
   const size_t vb = values_bytes(P.max_local);
@@ -65,6 +70,23 @@ __global__ void __launch_bounds__(kThreads, 2) apply_blocks_multi_kernel(MultiPa
   uint4 *rec = reinterpret_cast<uint4 *>(vals + (size_t)P.nr * vb);
   const int tid = threadIdx.x;
   const int b = blockIdx.x;
+  if (b >= P.nblk) {
+    const int brick = (b - P.nblk) * kBricksPerCta + tid / kBrickElems;
+    for (int r = 0; r < P.nr; ++r) {
+      if (P.sc && *(volatile const int *)&P.sc[r].done) continue;   // uniform over the CTA
+      const float *x = P.x + (size_t)r * P.ld;
+      float *y = P.y + (size_t)r * P.ld;
+      float *part = P.part + (size_t)r * 3 * P.nslot;
+      if (P.sc) {
+        double energy = brick_pass<float, true>(P.bricks, brick, P.ce, x, y, part, P.K, smem_raw);
+        energy = block_sum<kThreads>(energy);
+        if (tid == 0) P.dotp[(size_t)r * gridDim.x + b] = energy;
+      } else {
+        brick_pass<float, false>(P.bricks, brick, P.ce, x, y, part, P.K, smem_raw);
+      }
+      __syncthreads();   // the lattice buffers are reused by the next vector
+    }
+  } else {
   {
     const int r0 = P.rec_off[b], nrec = P.rec_off[b + 1] - r0;
     for (int i = tid; i < nrec; i += kThreads) copy16(rec + i, P.brec + r0 + i);
@@ -73,13 +95,14 @@ __global__ void __launch_bounds__(kThreads, 2) apply_blocks_multi_kernel(MultiPa
   }
   const int *hdr = reinterpret_cast<const int *>(rec);
   const unsigned char *rb = reinterpret_cast<const unsigned char *>(rec);
-  const int e0 = hdr[0], ne = hdr[1], nreg = hdr[2], nshared = hdr[3], nhang = hdr[4];
+  const int ne = hdr[1], nreg = hdr[2], nshared = hdr[3], nhang = hdr[4];
   const int *lslot = reinterpret_cast<const int *>(rb + hdr[6]);
   const uint2 *hent = reinterpret_cast<const uint2 *>(rb + hdr[7]);
   const uint16_t *ip = reinterpret_cast<const uint16_t *>(rb + hdr[8]);
   const uint16_t *iv = reinterpret_cast<const uint16_t *>(rb + hdr[9]);
   const uint4 *lcorner = reinterpret_cast<const uint4 *>(rb + hdr[10]);
   const uint32_t *lnode = reinterpret_cast<const uint32_t *>(rb + hdr[11]);
+  const int *elist = reinterpret_cast<const int *>(rb + hdr[12]);
   // node values of every vector (zero-filled at Dirichlet nodes), one stage
   for (int r = 0; r < P.nr; ++r) {
     float *R = reinterpret_cast<float *>(vals + (size_t)r * vb);
@@ -97,7 +120,7 @@ __global__ void __launch_bounds__(kThreads, 2) apply_blocks_multi_kernel(MultiPa
   float coef = 0.0f;
   uint4 cw = make_uint4(0, 0, 0, 0);
   if (tid < ne) {
-    coef = P.ce[e0 + tid];
+    coef = P.ce[elist[tid]];
     cw = lcorner[tid];
   }
   const int code[8] = {(int)(cw.x & 0xFFFF), (int)(cw.x >> 16), (int)(cw.y & 0xFFFF), (int)(cw.y >> 16),
@@ -176,6 +199,7 @@ __global__ void __launch_bounds__(kThreads, 2) apply_blocks_multi_kernel(MultiPa
     }
     __syncthreads();   // the slot buffer is reused by the next vector
   }
+  }
   // CG: the last CTA sums each running vector's energies: pq = p^T A p, alpha = rz / pq
   if (P.sc && last_cta(P.ticket)) {
     for (int r = 0; r < P.nr; ++r) {
@@ -200,6 +224,7 @@ __global__ void __launch_bounds__(kThreads, 2) apply_blocks_multi_kernel(MultiPa
 __global__ void __launch_bounds__(256) shared_multi_kernel(const int32_t *sh_node, const int32_t *sh_ptr, int64_t nsh,
                                                            const int32_t *hang_node, int64_t nh, const float *part,
                                                            int64_t nslot, float *y, int64_t ld, int nr) {
+  pdl_begin();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (r >= nr) return;
@@ -223,7 +248,7 @@ __global__ void __launch_bounds__(256) shared_multi_kernel(const int32_t *sh_nod
 
 size_t apply_multi_smem_bytes(const DeviceMesh &m, int nr) {
   const size_t rec_bytes = ((size_t)m.max_rec_bytes + 15) / 16 * 16;
-  return slot_bytes() + (size_t)nr * values_bytes(m.max_local) + rec_bytes;
+  return std::max(slot_bytes() + (size_t)nr * values_bytes(m.max_local) + rec_bytes, brick_smem_bytes<float>());
 }
 
 cudaError_t launch_apply_multi(const DeviceMesh &m, int nr, const float *ce, const float *x, float *y, float *part,
@@ -247,14 +272,16 @@ cudaError_t launch_apply_multi(const DeviceMesh &m, int nr, const float *ce, con
   P.brec = m.brec; P.rec_off = m.rec_off; P.ce = ce; P.x = x; P.y = y; P.part = part;
   P.ld = 3 * m.Nn; P.nslot = m.nslot; P.nr = nr; P.max_local = m.max_local;
   P.dotp = dotp; P.sc = sc; P.ticket = ticket;
+  P.nblk = m.nblk;
+  P.bricks = BrickTables{m.brick_tab, m.nbrick};
   for (int i = 0; i < 72; ++i) (&P.K.b[0][0][0])[i] = (float)m.modal[i];
-  if (m.nblk > 0) apply_blocks_multi_kernel<<<m.nblk, kThreads, smem, s>>>(P);
+  if (apply_ctas(m) > 0) { const cudaError_t pe_ = launch_pdl(apply_blocks_multi_kernel, dim3(apply_ctas(m)), dim3(kThreads), smem, s, P); if (pe_ != cudaSuccess) return pe_; }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || sc) return e;   // inside CG the update kernel sums the partials
   const int64_t items = m.nsh + m.nh;
   const dim3 grid((unsigned)std::max<int64_t>((items + 255) / 256, 1), (unsigned)nr);
-  shared_multi_kernel<<<grid, 256, 0, s>>>(m.sh_node, m.sh_ptr, m.nsh, m.hang_node, m.nh, part, m.nslot, y, 3 * m.Nn,
-                                           nr);
+  { const cudaError_t pe_ = launch_pdl(shared_multi_kernel, dim3(grid), dim3(256), 0, s, m.sh_node, m.sh_ptr, m.nsh, m.hang_node, m.nh, part, m.nslot, y, 3 * m.Nn,
+                                           nr); if (pe_ != cudaSuccess) return pe_; }
   return cudaGetLastError();
 }
 

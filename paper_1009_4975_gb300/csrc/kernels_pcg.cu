@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "pcg.cuh"
+#include "pdl.cuh"
 #include "reduce.cuh"
 #include "tm_internal.h"
 
@@ -26,6 +27,7 @@ template <typename TX, typename T>
 __global__ void __launch_bounds__(kVecThreads) update_kernel(TX *x, const T *p, const T *q, T *r, const T *dinv,
                                                              int64_t n, SolveScalars *sc, double *partials,
                                                              unsigned int *ticket) {
+  pdl_begin();
   if (sc->done) return;
   const double alpha = sc->alpha;
   const T a = (T)alpha;
@@ -78,6 +80,7 @@ __global__ void __launch_bounds__(kVecThreads) update_nodes_kernel(TX *x, const 
                                                                    SolveScalars *sc, double *partials,
                                                                    unsigned int *ticket, int twolevel, int64_t vst,
                                                                    int64_t pst, int pstride) {
+  pdl_begin();
   // load case blockIdx.y: its vectors vst apart, its partial sums pst apart, its own scalars,
   // reduction partials and ticket
   const int cs = blockIdx.y;
@@ -149,6 +152,7 @@ __global__ void __launch_bounds__(kVecThreads) update_nodes_kernel(TX *x, const 
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) pupdate_kernel(T *p, const T *r, const T *dinv, int64_t n,
                                                               SolveScalars *sc) {
+  pdl_begin();
   if (sc->done) return;
   const T beta = (T)sc->beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -312,7 +316,7 @@ int vec_grid(int64_t n) {
 template <typename TX, typename T>
 cudaError_t launch_update(TX *x, const T *p, const T *q, T *r, const T *dinv, int64_t n, SolveScalars *sc,
                           double *partials, unsigned int *ticket, cudaStream_t s) {
-  update_kernel<TX, T><<<vec_grid(n), kVecThreads, 0, s>>>(x, p, q, r, dinv, n, sc, partials, ticket);
+  { const cudaError_t pe_ = launch_pdl(update_kernel<TX, T>, dim3(vec_grid(n)), dim3(kVecThreads), 0, s, x, p, q, r, dinv, n, sc, partials, ticket); if (pe_ != cudaSuccess) return pe_; }
   return cudaGetLastError();
 }
 template cudaError_t launch_update<double, double>(double *, const double *, const double *, double *,
@@ -325,8 +329,8 @@ template <typename TX, typename T>
 cudaError_t launch_update_nodes(TX *x, const T *p, const T *q, T *r, const T *dinv, int64_t Nn,
                                 const int32_t *sh_of_node, const int32_t *sh_ptr, const T *part, SolveScalars *sc,
                                 double *partials, unsigned int *ticket, cudaStream_t s, bool twolevel) {
-  update_nodes_kernel<TX, T><<<vec_grid(Nn), kVecThreads, 0, s>>>(x, p, q, r, dinv, Nn, sh_of_node, sh_ptr, part, sc,
-                                                                   partials, ticket, twolevel ? 1 : 0, 0, 0, 0);
+  { const cudaError_t pe_ = launch_pdl(update_nodes_kernel<TX, T>, dim3(vec_grid(Nn)), dim3(kVecThreads), 0, s, x, p, q, r, dinv, Nn, sh_of_node, sh_ptr, part, sc,
+                                                                   partials, ticket, twolevel ? 1 : 0, 0, 0, 0); if (pe_ != cudaSuccess) return pe_; }
   return cudaGetLastError();
 }
 template cudaError_t launch_update_nodes<double, double>(double *, const double *, const double *, double *,
@@ -342,15 +346,15 @@ cudaError_t launch_update_nodes_cases(int nv, float *x, const float *p, const fl
                                       const float *part, int64_t pst, SolveScalars *sc, double *partials,
                                       unsigned int *tickets, cudaStream_t s, bool twolevel) {
   const int g = vec_grid(Nn);
-  update_nodes_kernel<float, float><<<dim3(g, nv), kVecThreads, 0, s>>>(x, p, q, r, dinv, Nn, sh_of_node, sh_ptr, part,
+  { const cudaError_t pe_ = launch_pdl(update_nodes_kernel<float, float>, dim3(dim3(g, nv)), dim3(kVecThreads), 0, s, x, p, q, r, dinv, Nn, sh_of_node, sh_ptr, part,
                                                                         sc, partials, tickets, twolevel ? 1 : 0, vst,
-                                                                        pst, 2 * g);
+                                                                        pst, 2 * g); if (pe_ != cudaSuccess) return pe_; }
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_pupdate(T *p, const T *r, const T *dinv, int64_t n, SolveScalars *sc, cudaStream_t s) {
-  pupdate_kernel<T><<<vec_grid(n), kVecThreads, 0, s>>>(p, r, dinv, n, sc);
+  { const cudaError_t pe_ = launch_pdl(pupdate_kernel<T>, dim3(vec_grid(n)), dim3(kVecThreads), 0, s, p, r, dinv, n, sc); if (pe_ != cudaSuccess) return pe_; }
   return cudaGetLastError();
 }
 template cudaError_t launch_pupdate<double>(double *, const double *, const double *, int64_t, SolveScalars *,

@@ -361,15 +361,143 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
   // corners it uses.  Elements address corners by local id; the hanging slots
   // are filled from their masters before the element pass and folded back into
   // them after it.
-  std::vector<int32_t> nblocks_of(Nn, 0);       // number of blocks touching a regular node
-  struct Blk { int64_t e0, e1; };
+  std::vector<int32_t> nblocks_of(Nn, 0);       // number of blocks and bricks touching a regular node
+  // ---- 6a. bricks: aligned 4x4x4 cubes of 64 equal-level elements (consecutive in the Morton
+  // order, element t of the brick at (i, j, k) with t = morton(i, j, k)) whose hanging corners --
+  // on faces and edges shared with coarser elements -- each have their masters at the lattice
+  // nodes next to them along the coarse edge or face.  The brick's nodes form a 5x5x5 lattice,
+  // node (a, b, c) at a + 5 b + 25 c; the brick pass addresses them implicitly.  Other elements
+  // form the blocks.
+  std::vector<uint8_t> in_brick(Ne, 0);
+  m.brick_e0.clear();
+  m.brick_node.clear();
+  m.brick_hax.clear();
+  m.brick_fold.clear();
+  {
+    auto demorton = [](int t, int &i, int &j, int &k) {
+      i = (t & 1) | ((t >> 2) & 2);
+      j = ((t >> 1) & 1) | ((t >> 3) & 2);
+      k = ((t >> 2) & 1) | ((t >> 4) & 2);
+    };
+    auto morton6 = [](int i, int j, int k) {
+      return (i & 1) | ((j & 1) << 1) | ((k & 1) << 2) | ((i & 2) << 2) | ((j & 2) << 3) | ((k & 2) << 4);
+    };
+    int32_t lat[125];
+    uint8_t hax[125];
+    for (int64_t e = 0; e + 64 <= Ne;) {
+      const int32_t *l0 = &m.leaf[4 * e];
+      const int32_t s = 1 << (L - l0[3]);
+      bool ok = l0[0] % (4 * s) == 0 && l0[1] % (4 * s) == 0 && l0[2] % (4 * s) == 0;
+      for (int t = 1; ok && t < 64; ++t) {
+        int i, j, k;
+        demorton(t, i, j, k);
+        const int32_t *lt = &m.leaf[4 * (e + t)];
+        ok = lt[3] == l0[3] && lt[0] == l0[0] + s * i && lt[1] == l0[1] + s * j && lt[2] == l0[2] + s * k;
+      }
+      if (ok) {
+        for (int c = 0; c < 5; ++c)
+          for (int b = 0; b < 5; ++b)
+            for (int a = 0; a < 5; ++a) {
+              const int ex = a < 4 ? a : 3, ey = b < 4 ? b : 3, ez = c < 4 ? c : 3;
+              const int q = (a - ex) + 2 * (b - ey) + 4 * (c - ez);
+              lat[a + 5 * b + 25 * c] = m.conn[8 * (e + morton6(ex, ey, ez)) + q];
+            }
+        for (int nd = 0; ok && nd < 125; ++nd) {
+          hax[nd] = 0;
+          const int32_t hi = m.hang_index[lat[nd]];
+          if (hi < 0) continue;
+          const int a = nd % 5, b = (nd / 5) % 5, c = nd / 25;
+          int nm = 0, dmask = 0;
+          int d[4][3];
+          for (int q = 0; q < 4; ++q) {
+            const int32_t mm = m.hang_master[4 * hi + q];
+            if (mm < 0) continue;
+            const int32_t *p = &m.node_xyz[3 * mm];
+            const int32_t rel[3] = {p[0] - l0[0] - s * a, p[1] - l0[1] - s * b, p[2] - l0[2] - s * c};
+            for (int ax = 0; ax < 3; ++ax) {
+              if (rel[ax] != 0 && rel[ax] != s && rel[ax] != -s) ok = false;
+              d[nm][ax] = rel[ax] / s;
+              if (rel[ax] != 0) dmask |= 1 << ax;
+            }
+            if (m.hang_index[mm] >= 0) ok = false;
+            ++nm;
+          }
+          const int naxes = (dmask & 1) + ((dmask >> 1) & 1) + ((dmask >> 2) & 1);
+          if (!ok || !((nm == 2 && naxes == 1) || (nm == 4 && naxes == 2))) { ok = false; break; }
+          // every master moves by exactly one lattice step along each interpolation axis, and
+          // the masters are distinct
+          for (int q = 0; q < nm && ok; ++q)
+            for (int ax = 0; ax < 3; ++ax)
+              if (((dmask >> ax) & 1) ? (d[q][ax] == 0) : (d[q][ax] != 0)) ok = false;
+          for (int q = 0; q < nm && ok; ++q)
+            for (int r = q + 1; r < nm; ++r)
+              if (d[q][0] == d[r][0] && d[q][1] == d[r][1] && d[q][2] == d[r][2]) ok = false;
+          for (int ax = 0; ax < 3 && ok; ++ax) {
+            const int pos = ax == 0 ? a : (ax == 1 ? b : c);
+            if (((dmask >> ax) & 1) && (pos == 0 || pos == 4)) ok = false;
+          }
+          hax[nd] = (uint8_t)dmask;
+        }
+      }
+      if (!ok) {
+        ++e;
+        continue;
+      }
+      m.brick_e0.push_back((int32_t)e);
+      // fold masks: which lattice neighbours of a regular node are hanging nodes it is a master
+      // of -- bits 2 ax + (step > 0): the neighbour one step along axis ax, edge-hanging along
+      // ax; bits 6 + 4 pl + 2 (step1 > 0) + (step0 > 0): the diagonal neighbour in coordinate
+      // plane pl ((x, y), (x, z), (y, z)), face-hanging in that plane
+      for (int nd = 0; nd < 125; ++nd) {
+        uint32_t fm = 0;
+        const int pos[3] = {nd % 5, (nd / 5) % 5, nd / 25}, nst[3] = {1, 5, 25};
+        if (!hax[nd]) {
+          for (int ax = 0; ax < 3; ++ax)
+            for (int sg = -1; sg <= 1; sg += 2) {
+              const int p = pos[ax] + sg;
+              if (p >= 0 && p <= 4 && hax[nd + sg * nst[ax]] == (1 << ax)) fm |= 1u << (2 * ax + (sg > 0));
+            }
+          for (int pl = 0; pl < 3; ++pl) {
+            const int ax0 = pl == 2 ? 1 : 0, ax1 = pl == 0 ? 1 : 2;
+            for (int s1g = -1; s1g <= 1; s1g += 2)
+              for (int s0g = -1; s0g <= 1; s0g += 2) {
+                const int p0 = pos[ax0] + s0g, p1 = pos[ax1] + s1g;
+                if (p0 < 0 || p0 > 4 || p1 < 0 || p1 > 4) continue;
+                if (hax[nd + s0g * nst[ax0] + s1g * nst[ax1]] == ((1 << ax0) | (1 << ax1)))
+                  fm |= 1u << (6 + 4 * pl + 2 * (s1g > 0) + (s0g > 0));
+              }
+          }
+        }
+        m.brick_fold.push_back(fm);
+      }
+      for (int nd = 0; nd < 125; ++nd) {
+        uint32_t g = (uint32_t)lat[nd];
+        if (m.nflag[lat[nd]] & 1) g |= 0x80000000u;
+        m.brick_node.push_back((int32_t)g);
+        m.brick_hax.push_back(hax[nd]);
+        if (!hax[nd]) nblocks_of[lat[nd]]++;
+      }
+      std::memset(&in_brick[e], 1, 64);
+      e += 64;
+    }
+    m.nbrick = (int32_t)m.brick_e0.size();
+  }
+  // blocks: consecutive runs of the non-brick elements in Morton order (gen), at most kBlockElems
+  // elements and kMaxLocal local nodes each; a block may span the bricks between its elements
+  std::vector<int32_t> &gen = m.gen_elem;
+  gen.clear();
+  for (int64_t e = 0; e < Ne; ++e)
+    if (!in_brick[e]) gen.push_back((int32_t)e);
+  const int64_t ngen = (int64_t)gen.size();
+  struct Blk { int64_t e0, e1; };   // range of gen
   std::vector<Blk> blks;
   {
     std::vector<int32_t> mark(Nn, -1);
-    auto count_local = [&](int64_t e0, int64_t e1, int tag) {
+    auto count_local = [&](int64_t u0, int64_t u1, int tag) {
       int cnt = 0;
-      for (int64_t e = e0; e < e1; ++e)
+      for (int64_t u = u0; u < u1; ++u)
         for (int k = 0; k < 8; ++k) {
+          const int64_t e = gen[u];
           const int32_t n = m.conn[8 * e + k];
           if (mark[n] != tag) { mark[n] = tag; ++cnt; }
           const int32_t h = m.hang_index[n];
@@ -382,13 +510,13 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
       return cnt;
     };
     int tag = 0;
-    int64_t e0 = 0;
-    while (e0 < Ne) {
-      int64_t len = std::min<int64_t>(kBlockElems, Ne - e0);
-      while (len > 1 && count_local(e0, e0 + len, tag++) > kMaxLocal) len = (len + 1) / 2;
-      if (count_local(e0, e0 + len, tag++) > kMaxLocal) return "block local-node limit exceeded";
-      blks.push_back({e0, e0 + len});
-      e0 += len;
+    int64_t u0 = 0;
+    while (u0 < ngen) {
+      int64_t len = std::min<int64_t>(kBlockElems, ngen - u0);
+      while (len > 1 && count_local(u0, u0 + len, tag++) > kMaxLocal) len = (len + 1) / 2;
+      if (count_local(u0, u0 + len, tag++) > kMaxLocal) return "block local-node limit exceeded";
+      blks.push_back({u0, u0 + len});
+      u0 += len;
     }
   }
   const int32_t nblk = (int32_t)blks.size();
@@ -404,9 +532,9 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
           v.push_back(n);
         }
       };
-      for (int64_t e = blks[b].e0; e < blks[b].e1; ++e)
+      for (int64_t u = blks[b].e0; u < blks[b].e1; ++u)
         for (int k = 0; k < 8; ++k) {
-          const int32_t n = m.conn[8 * e + k];
+          const int32_t n = m.conn[8 * (int64_t)gen[u] + k];
           const int32_t h = m.hang_index[n];
           if (h < 0) add(n);
           else
@@ -417,7 +545,7 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
       for (int32_t n : v) nblocks_of[n]++;
     }
   }
-  m.blk_elem.assign(nblk + 1, 0);
+  m.blk_elem.assign(2 * (size_t)nblk, 0);
   m.blk_node.assign(nblk + 1, 0);
   m.blk_shared.assign(nblk, 0);
   m.blk_slot.assign(nblk + 1, 0);
@@ -443,10 +571,10 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     m.lnode.insert(m.lnode.end(), order.begin(), order.end());
     // hanging nodes used by this block: local ids nreg, nreg+1, ... in first-use order
     std::vector<int32_t> used_h;
-    const int64_t e0 = blks[b].e0, e1 = blks[b].e1;
-    for (int64_t e = e0; e < e1; ++e)
+    const int64_t e0 = blks[b].e0, e1 = blks[b].e1;   // range of gen
+    for (int64_t u = e0; u < e1; ++u)
       for (int k = 0; k < 8; ++k) {
-        const int32_t n = m.conn[8 * e + k];
+        const int32_t n = m.conn[8 * (int64_t)gen[u] + k];
         if (m.hang_index[n] >= 0 && local_of[n] < 0) {
           local_of[n] = nreg + (int32_t)used_h.size();
           used_h.push_back(m.hang_index[n]);
@@ -456,14 +584,17 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     if (nloc > kMaxLocal) return "block local-node limit exceeded";
     max_local = std::max(max_local, nloc);
     m.blk_hang[b + 1] = m.blk_hang[b] + (int32_t)used_h.size();
-    for (int64_t e = e0; e < e1; ++e)
-      for (int k = 0; k < 8; ++k) m.lcorner[8 * e + k] = (uint16_t)local_of[m.conn[8 * e + k]];
+    for (int64_t u = e0; u < e1; ++u)
+      for (int k = 0; k < 8; ++k) {
+        const int64_t e = gen[u];
+        m.lcorner[8 * e + k] = (uint16_t)local_of[m.conn[8 * e + k]];
+      }
     // inverse lists, built as one block-local CSR: per local node its slots (element order),
     // then its fold entries (hanging order)
     if (used_h.size() >= (size_t)kQuarterBit) return "too many hanging nodes in a block";
     lcount.assign(nloc + 1, 0);
-    for (int64_t e = e0; e < e1; ++e)
-      for (int k = 0; k < 8; ++k) lcount[local_of[m.conn[8 * e + k]] + 1]++;
+    for (int64_t u = e0; u < e1; ++u)
+      for (int k = 0; k < 8; ++k) lcount[local_of[m.conn[8 * (int64_t)gen[u] + k]] + 1]++;
     for (size_t j = 0; j < used_h.size(); ++j)
       for (int q = 0; q < 4; ++q) {
         const int32_t mm = m.hang_master[4 * used_h[j] + q];
@@ -476,9 +607,9 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     const size_t inv0 = m.inv.size();
     m.inv.resize(inv0 + lcount[nloc]);
     lfill.assign(lcount.begin(), lcount.end() - 1);
-    for (int64_t e = e0; e < e1; ++e)
+    for (int64_t u = e0; u < e1; ++u)
       for (int k = 0; k < 8; ++k)   // the slot's offset in the block's per-element result buffer
-        m.inv[inv0 + lfill[local_of[m.conn[8 * e + k]]]++] = (uint16_t)((e - e0) * kSlotRow + 3 * k);
+        m.inv[inv0 + lfill[local_of[m.conn[8 * (int64_t)gen[u] + k]]]++] = (uint16_t)((u - e0) * kSlotRow + 3 * k);
     for (size_t j = 0; j < used_h.size(); ++j) {
       const int32_t h = used_h[j];
       const bool quarter = m.hang_master[4 * h + 2] >= 0;
@@ -490,7 +621,8 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
       }
     }
     for (int32_t i = 0; i <= nloc; ++i) m.iptr.push_back((uint16_t)lcount[i]);
-    m.blk_elem[b + 1] = (int32_t)e1;
+    m.blk_elem[2 * b] = (int32_t)e0;
+    m.blk_elem[2 * b + 1] = (int32_t)e1;
     for (int32_t n : order) local_of[n] = -1;
     for (int32_t h : used_h) local_of[m.hang_node[h]] = -1;
   }
@@ -501,9 +633,14 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
   // second pass streams them; each block writes its shared nodes' partials to
   // their CSR positions (lslot).
   {
+    // blocks first (ascending), then bricks (ascending): the order of a node's partials
     std::vector<int32_t> cnt(Nn + 1, 0);
     for (int32_t b = 0; b < nblk; ++b)
       for (int32_t i = 0; i < m.blk_shared[b]; ++i) cnt[m.lnode[m.blk_node[b] + i] + 1]++;
+    for (size_t i = 0; i < m.brick_node.size(); ++i) {
+      const int32_t n = m.brick_node[i] & 0x7FFFFFFF;
+      if (!m.brick_hax[i] && nblocks_of[n] > 1) cnt[n + 1]++;
+    }
     std::vector<int32_t> start(Nn + 1, 0);
     for (int64_t n = 0; n < Nn; ++n) start[n + 1] = start[n] + cnt[n + 1];
     std::vector<int32_t> fill(start.begin(), start.end() - 1);
@@ -513,6 +650,26 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
         const int32_t n = m.lnode[m.blk_node[b] + i];
         m.lslot[m.blk_slot[b] + i] = fill[n]++;
       }
+    m.brick_out.assign(m.brick_node.size(), -1);
+    for (size_t i = 0; i < m.brick_node.size(); ++i) {
+      const int32_t n = m.brick_node[i] & 0x7FFFFFFF;
+      if (m.brick_hax[i]) m.brick_out[i] = -2;
+      else if (nblocks_of[n] > 1) m.brick_out[i] = fill[n]++;
+    }
+    m.nslot = start[Nn];
+    // the brick pass's packed table: per brick 3 x 128 int32 -- node ids (125, then e0 at 125),
+    // output targets (125), fold mask | axes << 24 (125)
+    m.brick_tab.assign((size_t)384 * m.nbrick, 0);
+    for (int32_t bk = 0; bk < m.nbrick; ++bk) {
+      int32_t *t = &m.brick_tab[(size_t)384 * bk];
+      for (int nd = 0; nd < 125; ++nd) {
+        const size_t i = (size_t)125 * bk + nd;
+        t[nd] = m.brick_node[i];
+        t[128 + nd] = m.brick_out[i];
+        t[256 + nd] = (int32_t)(m.brick_fold[i] | ((uint32_t)m.brick_hax[i] << 24));
+      }
+      t[125] = m.brick_e0[bk];
+    }
     m.sh_ptr.push_back(0);
     m.sh_of_node.assign(Nn, -1);
     for (int64_t n = 0; n < Nn; ++n)
@@ -525,10 +682,11 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
 
   // ---- 7b. one contiguous record per block (16-byte aligned), staged into
   // shared memory by the operator kernel with coalesced 16-byte loads:
-  //   header (12 x i32: e0, ne, nreg, nshared, nhang, ninv, byte offsets of
-  //   lslot, hent, iptr, inv, lcorner, lnode), lcorner (8 x u16 per element: the
+  //   header (16 x i32: first element, ne, nreg, nshared, nhang, ninv, byte offsets of
+  //   lslot, hent, iptr, inv, lcorner, lnode, elist, 3 x 0), lcorner (8 x u16 per element: the
   //   local ids of its corners), lnode (i32, bit 31 = Dirichlet node), lslot
-  //   (i32), hent (4 x u16), iptr (u16), inv (u16).
+  //   (i32), hent (4 x u16), iptr (u16), inv (u16); elist (i32 per element: its canonical index)
+  //   follows lcorner.
   {
     m.rec_off.assign(nblk + 1, 0);
     m.max_rec_bytes = 0;
@@ -539,9 +697,10 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
       const int32_t nhang = m.blk_hang[b + 1] - m.blk_hang[b];
       const int32_t nloc = nreg + nhang;
       const int32_t ninv = m.iptr[m.blk_iptr[b] + nloc];
-      const int32_t ne = m.blk_elem[b + 1] - m.blk_elem[b];
-      size_t off = 48;
+      const int32_t ne = m.blk_elem[2 * b + 1] - m.blk_elem[2 * b];
+      size_t off = 64;
       const size_t o_lcorner = off; off += 16 * (size_t)ne;
+      const size_t o_elist = off; off += 4 * (size_t)ne;
       const size_t o_lnode = off; off += 4 * (size_t)nreg;
       const size_t o_lslot = off; off += 4 * (size_t)nshared;
       off = align(off, 8);
@@ -550,10 +709,13 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
       const size_t o_inv = off; off += 2 * (size_t)ninv;
       const size_t bytes = align(off, 16);
       std::vector<uint8_t> rec(bytes, 0);
-      int32_t hdr[12] = {m.blk_elem[b], ne, nreg, nshared, nhang, ninv, (int32_t)o_lslot, (int32_t)o_hent,
-                         (int32_t)o_iptr, (int32_t)o_inv, (int32_t)o_lcorner, (int32_t)o_lnode};
+      const int32_t *el = &gen[m.blk_elem[2 * b]];
+      int32_t hdr[16] = {el[0], ne, nreg, nshared, nhang, ninv, (int32_t)o_lslot, (int32_t)o_hent,
+                         (int32_t)o_iptr, (int32_t)o_inv, (int32_t)o_lcorner, (int32_t)o_lnode, (int32_t)o_elist,
+                         0, 0, 0};
       std::memcpy(rec.data(), hdr, sizeof(hdr));
-      std::memcpy(&rec[o_lcorner], &m.lcorner[8 * (size_t)m.blk_elem[b]], 16 * (size_t)ne);
+      for (int32_t t = 0; t < ne; ++t) std::memcpy(&rec[o_lcorner + 16 * (size_t)t], &m.lcorner[8 * (size_t)el[t]], 16);
+      std::memcpy(&rec[o_elist], el, 4 * (size_t)ne);
       for (int32_t i = 0; i < nreg; ++i) {
         uint32_t g = (uint32_t)m.lnode[m.blk_node[b] + i];
         if (m.nflag[g] & 1) g |= 0x80000000u;
@@ -721,7 +883,7 @@ int tm_tables_build(const tm_mesh_desc *d, tm_tables **out, tm_mesh_info *info, 
     info->n_shared = (int64_t)m.sh_node.size();
     info->device_bytes = 0;
     info->max_block_bytes = m.max_rec_bytes;
-    info->pad_ = 0;
+    info->n_bricks = m.nbrick;
   }
   *out = t;
   return TM_OK;
@@ -750,6 +912,17 @@ int tm_tables_operator(const tm_tables *t, int32_t *rec_off, uint8_t *brec, doub
   if (modal) std::memcpy(modal, h.modal.data(), 72 * sizeof(double));
   if (sh_node) std::memcpy(sh_node, h.sh_node.data(), h.sh_node.size() * sizeof(int32_t));
   if (sh_ptr) std::memcpy(sh_ptr, h.sh_ptr.data(), h.sh_ptr.size() * sizeof(int32_t));
+  return TM_OK;
+}
+
+int tm_tables_bricks(const tm_tables *t, int32_t *e0, int32_t *node, uint8_t *hax, int32_t *out, uint32_t *fold) {
+  if (!t) return TM_EINVAL;
+  const amr::HostMesh &h = t->m;
+  if (e0) std::memcpy(e0, h.brick_e0.data(), h.brick_e0.size() * sizeof(int32_t));
+  if (node) std::memcpy(node, h.brick_node.data(), h.brick_node.size() * sizeof(int32_t));
+  if (hax) std::memcpy(hax, h.brick_hax.data(), h.brick_hax.size());
+  if (out) std::memcpy(out, h.brick_out.data(), h.brick_out.size() * sizeof(int32_t));
+  if (fold) std::memcpy(fold, h.brick_fold.data(), h.brick_fold.size() * sizeof(uint32_t));
   return TM_OK;
 }
 

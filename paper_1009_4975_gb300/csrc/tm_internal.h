@@ -43,7 +43,7 @@ struct HostMesh {
   std::vector<int32_t> hang_index;    // node -> hanging index or -1
   int64_t n_dirichlet = 0, n_free_nodes = 0;
 
-  // operator blocks (consecutive canonical elements).  Local node ids of a
+  // operator blocks (runs of consecutive canonical elements outside the bricks).  Local node ids of a
   // block: regular nodes first (shared ones, then interior), then the hanging
   // nodes its elements use.  The inverse list of a local node names the
   // (element, corner) slots it fills -- entry e_local * kSlotRow + 3 k, the slot's
@@ -51,7 +51,8 @@ struct HostMesh {
   // the hanging nodes it is a master of -- entry kFoldBit | (kQuarterBit if the
   // hanging node has 4 masters) | hanging index.
   int32_t nblk = 0, max_local = 0;
-  std::vector<int32_t> blk_elem;      // nblk+1: element ranges
+  std::vector<int32_t> gen_elem;      // the elements outside the bricks, ascending
+  std::vector<int32_t> blk_elem;      // 2 per block: its range [u0, u1) of gen_elem
   std::vector<int32_t> blk_node;      // nblk+1: regular local node ranges in lnode
   std::vector<int32_t> blk_shared;    // nblk: regular local nodes [0, shared) are shared
   std::vector<int32_t> blk_slot;      // nblk+1: the block's shared nodes' range in lslot
@@ -67,6 +68,18 @@ struct HostMesh {
   std::vector<uint8_t> brec;          // per-block records (see mesh_host.cpp, 16-byte aligned)
   std::vector<int32_t> rec_off;       // nblk+1: record ranges in 16-byte units
   int32_t max_rec_bytes = 0;
+  // bricks (mesh_host.cpp, section 6a): aligned 4x4x4 runs of 64 equal-level elements taken by
+  // the brick pass; their 5x5x5 node lattice is node (a, b, c) at a + 5 b + 25 c
+  int32_t nbrick = 0;
+  std::vector<int32_t> brick_e0;      // first element of each brick
+  std::vector<int32_t> brick_node;    // 125 per brick: global node, bit 31 = Dirichlet
+  std::vector<uint8_t> brick_hax;     // 125 per brick: 0 regular, else the axes (bits 0-2) a hanging
+                                      // node interpolates along (masters one lattice step away)
+  std::vector<int32_t> brick_out;     // 125 per brick: -1 the brick owns the node, >= 0 its partial's
+                                      // position (node-major CSR), -2 hanging (folded into masters)
+  std::vector<uint32_t> brick_fold;   // 125 per brick: lattice neighbours folded into a regular node
+  std::vector<int32_t> brick_tab;     // 384 per brick: the device copy (brick.cuh)
+  int64_t nslot = 0;                  // partials of block- and brick-shared nodes
   // second pass over shared nodes
   std::vector<int32_t> sh_node;       // shared node ids
   std::vector<int32_t> sh_ptr;        // CSR: partials of shared node i are [sh_ptr[i], sh_ptr[i+1])
@@ -122,6 +135,8 @@ struct DeviceMesh {
   int32_t *rec_off = nullptr;
   int32_t max_rec_bytes = 0;
   int32_t resident_cta32 = 0, resident_cta64 = 0;  // block-pass CTAs resident on the GPU (record prefetch distance)
+  int32_t nbrick = 0;                 // bricks (HostMesh): CTAs nblk .. of the block pass take 4 each
+  int32_t *brick_tab = nullptr;       // 384 per brick (brick.cuh)
   int32_t *sh_node = nullptr, *sh_ptr = nullptr;
   int32_t *sh_of_node = nullptr;      // node -> shared-node index, -1 when one block owns it
   int32_t *dg_ptr = nullptr, *dg_elem = nullptr;
@@ -131,6 +146,9 @@ struct DeviceMesh {
   std::vector<void *> owned;
   int64_t bytes = 0;
 };
+
+// CTAs of the operator's block pass: the blocks, then the bricks four to a CTA
+inline int apply_ctas(const DeviceMesh &m) { return m.nblk + (m.nbrick + 3) / 4; }
 
 // Two-level preconditioner (kernels_coarse.cu): levels of the uniform vertex lattice, level 0
 // the base grid.  Lattice vectors hold 3 values per node, x fastest, clamped nodes at 0.

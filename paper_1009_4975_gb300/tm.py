@@ -39,7 +39,7 @@ class tm_mesh_info(C.Structure):
     _fields_ = [("Ne", C.c_int64), ("Nn", C.c_int64), ("n_hanging", C.c_int64), ("n_dirichlet", C.c_int64),
                 ("n_free", C.c_int64), ("n_blocks", C.c_int32), ("max_local", C.c_int32),
                 ("n_shared", C.c_int64), ("device_bytes", C.c_int64), ("max_block_bytes", C.c_int32),
-                ("pad_", C.c_int32)]
+                ("n_bricks", C.c_int32)]
 
 
 class tm_solve_opts(C.Structure):
@@ -67,7 +67,7 @@ class tm_profile_data(C.Structure):
 EXPORTS = ["tm_create", "tm_destroy", "tm_set_stream", "tm_last_error", "tm_mesh_upload", "tm_mesh_tables",
            "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_apply_K_f32_static", "tm_apply_K_f32_multi", "tm_jacobi_diag", "tm_pcg_solve", "tm_pcg_solve_batch", "tm_pcg_solve_multi", "tm_expand",
            "tm_sensitivity", "tm_filter", "tm_oc_update", "tm_amr_mark", "tm_amr_adapt", "tm_design_difference",
-           "tm_tables_adapt", "tm_tables_operator", "tm_tables_transfer", "tm_unet_param_count", "tm_unet_workspace_floats",
+           "tm_tables_adapt", "tm_tables_operator", "tm_tables_bricks", "tm_tables_transfer", "tm_unet_param_count", "tm_unet_workspace_floats",
            "tm_unet_forward", "tm_unet_backward", "tm_profile", "tm_profile_read", "tm_coarse_setup",
            "tm_coarse_cells", "tm_coarse_apply", "tm_coarse_restrict", "tm_coarse_prolong", "tm_coarse_vcycle", "tm_transfer_displacement", "tm_learn_input",
            "tm_learn_guess", "tm_learn_output_grad", "tm_adam_step"]
@@ -108,6 +108,7 @@ def load_library(path: str = LIB_PATH):
         "tm_design_difference": [vp, vp, i64, vp, vp, C.POINTER(dbl)],
         "tm_tables_adapt": [vp, vp, vp, i64, vp, vp, C.POINTER(i64)],
         "tm_tables_operator": [vp, vp, vp, vp, vp, vp, C.POINTER(i64)],
+        "tm_tables_bricks": [vp, vp, vp, vp, vp, vp],
         "tm_tables_transfer": [vp, vp, i64, vp, vp],
         "tm_unet_forward": [vp, C.POINTER(tm_unet_desc), vp, vp, vp, vp],
         "tm_unet_backward": [vp, C.POINTER(tm_unet_desc), vp, vp, vp, vp, vp, vp],
@@ -474,8 +475,9 @@ def tm_tables_adapt(nx, ny, nz, max_level, h0, leaves, mark, rho):
 
 
 def tm_tables_operator(nx, ny, nz, max_level, h0, leaves, dirichlet_faces=1):
-    """Host-only export of the operator's block tables (tm_tables_operator): dict with info,
-    rec_off, brec (uint8), modal (8, 3, 3), sh_node, sh_ptr."""
+    """Host-only export of the operator's block and brick tables (tm_tables_operator,
+    tm_tables_bricks): dict with info, rec_off, brec (uint8), modal (8, 3, 3), sh_node, sh_ptr,
+    brick_e0, brick_node, brick_hax, brick_out, brick_fold (bricks x 125)."""
     lib = load_library()
     lv = np.ascontiguousarray(np.asarray(leaves, np.int32).reshape(-1, 4))
     d = tm_mesh_desc(nx, ny, nz, max_level, h0, lv.shape[0], lv.ctypes.data_as(C.POINTER(C.c_int32)),
@@ -497,6 +499,14 @@ def tm_tables_operator(nx, ny, nz, max_level, h0, leaves, dirichlet_faces=1):
                                          ("rec_off", "brec", "modal", "sh_node", "sh_ptr")], C.byref(nb))
         if rc != TM_OK:
             raise TmError(rc, "tm_tables_operator failed")
+        nbk = info.n_bricks
+        out.update(brick_e0=np.zeros(nbk, np.int32), brick_node=np.zeros((nbk, 125), np.int32),
+                   brick_hax=np.zeros((nbk, 125), np.uint8), brick_out=np.zeros((nbk, 125), np.int32),
+                   brick_fold=np.zeros((nbk, 125), np.uint32))
+        rc = lib.tm_tables_bricks(h, *[C.c_void_p(out[k].ctypes.data) for k in
+                                       ("brick_e0", "brick_node", "brick_hax", "brick_out", "brick_fold")])
+        if rc != TM_OK:
+            raise TmError(rc, "tm_tables_bricks failed")
         return out
     finally:
         lib.tm_tables_free(h)
