@@ -306,27 +306,49 @@ int ensure_coarse(tm_ctx *ctx) {
   return TM_OK;
 }
 
-// Level operators, smoother diagonals and the coarsest inverse for the density rho.  Host time
-// in *seconds (may be NULL).
-int coarse_setup(tm_ctx *ctx, const double *rho, double *seconds) {
+// Level operators, smoother diagonals and the coarsest inverse for the density rho, in two
+// halves: coarse_setup_begin enqueues the device part and the copy of the coarsest level's cell
+// matrices to the host; coarse_setup_end inverts on the host and enqueues the inverse's upload.
+// Work the caller enqueues in between (the solver's first true residual) runs on the GPU while
+// the host inverts.  Host time of the two halves is added to *seconds (may be NULL).
+int coarse_setup_begin(tm_ctx *ctx, const double *rho, double *seconds) {
   const auto t0 = std::chrono::steady_clock::now();
   int rc = ensure_coarse(ctx);
   if (rc) return rc;
   CoarseHierarchy &h = ctx->coarse;
+  ctx->coarse_ready = false;
   TM_CUDA(ctx, coarse_setup_launch(ctx->dm, h, rho, ctx->stream));
   ctx->launches += 3 * (int64_t)h.nlev - 1;
   const CoarseLevel &cl = h.lev[h.nlev - 1];
   h.Kc_host.resize(576 * (size_t)cl.X * cl.Y * cl.Z);
   TM_CUDA(ctx, cudaMemcpyAsync(h.Kc_host.data(), h.Kc64, h.Kc_host.size() * sizeof(double), cudaMemcpyDeviceToHost,
                                ctx->stream));
-  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  std::vector<float> Ainv;
+  TM_CUDA(ctx, cudaEventRecord(ctx->ev_coarse, ctx->stream));
+  if (seconds) *seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return TM_OK;
+}
+
+int coarse_setup_end(tm_ctx *ctx, double *seconds) {
+  const auto t0 = std::chrono::steady_clock::now();
+  CoarseHierarchy &h = ctx->coarse;
+  const CoarseLevel &cl = h.lev[h.nlev - 1];
+  TM_CUDA(ctx, cudaEventSynchronize(ctx->ev_coarse));   // the cell matrices are on the host
+  std::vector<float> &Ainv = h.Ainv_host;
   std::string msg = coarse_dense_inverse(h.Kc_host, cl.X, cl.Y, cl.Z, h.faces, Ainv);
   if (!msg.empty()) return fail(ctx, TM_ENONFINITE, "two-level preconditioner: " + msg);
   TM_CUDA(ctx, cudaMemcpyAsync(h.Ainv, Ainv.data(), Ainv.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   ctx->coarse_ready = true;
-  if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (seconds) *seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return TM_OK;
+}
+
+int coarse_setup(tm_ctx *ctx, const double *rho, double *seconds) {
+  if (seconds) *seconds = 0.0;
+  int rc = coarse_setup_begin(ctx, rho, seconds);
+  if (rc) return rc;
+  rc = coarse_setup_end(ctx, seconds);
+  if (rc) return rc;
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return TM_OK;
 }
 
@@ -368,6 +390,7 @@ int tm_create(tm_ctx **out, int device, void *cuda_stream) {
   c->stream = (cudaStream_t)cuda_stream;
   if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_coarse, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess) {
     delete c;
@@ -393,6 +416,7 @@ int tm_destroy(tm_ctx *ctx) {
   }
   for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_coarse) cudaEventDestroy(ctx->ev_coarse);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -463,7 +487,9 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
     m.brec = reinterpret_cast<uint4 *>(rec);
   }
   TM_CUDA(ctx, upload(o, B, &m.rec_off, h.rec_off));
+  TM_CUDA(ctx, upload(o, B, &m.rec_skip, h.rec_skip));
   m.max_rec_bytes = h.max_rec_bytes;
+  m.max_rec_stage = h.max_rec_stage;
   TM_CUDA(ctx, upload(o, B, &m.brick_tab, h.brick_tab));
   TM_CUDA(ctx, apply_residency(m, &m.resident_cta32, &m.resident_cta64));
   TM_CUDA(ctx, upload(o, B, &m.sh_node, h.sh_node));
@@ -1106,8 +1132,8 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
     int left = opts->max_iter;
     double rel = 0, scale_old = 0;
     bool first = true;
-    if (twolevel) {
-      rc = coarse_setup(ctx, rho_dev, &out.setup_seconds);
+    if (twolevel) {   // finished below, while the first true residual is computed
+      rc = coarse_setup_begin(ctx, rho_dev, &out.setup_seconds);
       if (rc) return rc;
       out.coarse_levels = ctx->coarse.nlev;
     }
@@ -1119,6 +1145,10 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
       out.fp64_applies++;
       TM_CUDA(ctx, launch_residual64(f_dev, w.q, w.r, n, rr_dev, w.red, w.ticket + 1, st));
       ctx->launches += 1;
+      if (twolevel && sweep == 0) {
+        rc = coarse_setup_end(ctx, &out.setup_seconds);
+        if (rc) return rc;
+      }
       double rr = 0;
       rc = read_scalar(ctx, rr_dev, &rr);
       if (rc) return rc;

@@ -46,6 +46,7 @@ template <typename T>
 struct ApplyParams {
   const uint4 *brec;        // per-block records
   const int32_t *rec_off;   // record ranges in 16-byte units
+  const int32_t *rec_skip;  // per block: 16-byte units of lcorner and elist, read from global memory
   const T *ce;
   const T *x;
   T *y;
@@ -95,12 +96,15 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Record of block `blk` into `rec` (all threads; an empty group past the end).
-__device__ __forceinline__ void issue_record(const uint4 *brec, const int32_t *rec_off, int blk, int nblk,
-                                             uint4 *rec) {
+// Record of block `blk` into `rec` (all threads; an empty group past the end): its 64-byte header
+// and its sections from lnode on (lcorner and elist, read once per element, stay in global
+// memory), so that the sections after the header sit 16 * skip bytes below their record offsets.
+__device__ __forceinline__ void issue_record(const uint4 *brec, const int32_t *rec_off, const int32_t *rec_skip,
+                                             int blk, int nblk, uint4 *rec) {
   if (blk < nblk) {
-    const int r0 = rec_off[blk], nr = rec_off[blk + 1] - r0;
-    for (int i = threadIdx.x; i < nr; i += kApplyThreads) cp_async16(rec + i, brec + r0 + i);
+    const int r0 = rec_off[blk], nr = rec_off[blk + 1] - r0, skip = rec_skip[blk];
+    for (int i = threadIdx.x; i < nr - skip; i += kApplyThreads)
+      cp_async16(rec + i, brec + r0 + (i < 4 ? i : i + skip));
   }
   cp_async_commit();
 }
@@ -109,11 +113,12 @@ __device__ __forceinline__ void issue_record(const uint4 *brec, const int32_t *r
 // consecutive words (word w is component w % 3 of local node w / 3), so a run of consecutive node
 // ids is read with contiguous, coalesced requests.
 template <typename T>
-__device__ __forceinline__ void issue_values(const uint4 *rec, const T *x, T *R, bool valid) {
+__device__ __forceinline__ void issue_values(const uint4 *rec, int skip_bytes, const T *x, T *R, bool valid) {
   if (valid) {
     const int *hdr = reinterpret_cast<const int *>(rec);
     const int nreg = hdr[2];
-    const uint32_t *lnode = reinterpret_cast<const uint32_t *>(reinterpret_cast<const unsigned char *>(rec) + hdr[11]);
+    const uint32_t *lnode =
+        reinterpret_cast<const uint32_t *>(reinterpret_cast<const unsigned char *>(rec) + hdr[11] - skip_bytes);
     for (int wd = threadIdx.x; wd < 3 * nreg; wd += kApplyThreads) {
       const int i = wd / 3, c = wd - 3 * i;
       const uint32_t gw = lnode[i];
@@ -141,7 +146,9 @@ __global__ void __launch_bounds__(kApplyThreads, (sizeof(T) == 4 ? 4 : 2) * 256 
   const int tid = threadIdx.x;
   const int b = blockIdx.x;
   // record, then the node values it names: every copy of a stage in flight at once
-  issue_record(P.brec, P.rec_off, b, P.nblk, rec);
+  issue_record(P.brec, P.rec_off, P.rec_skip, b, P.nblk, rec);
+  const int skip_bytes = 16 * P.rec_skip[b];
+  const unsigned char *gb = reinterpret_cast<const unsigned char *>(P.brec + P.rec_off[b]);   // the record in global memory
   // the record of the block that starts about one resident wave later, into L2 (one bulk
   // prefetch; records are 16-byte aligned multiples of 16 bytes)
   if (tid == 0 && P.ahead > 0 && b + P.ahead < P.nblk) {
@@ -150,20 +157,28 @@ __global__ void __launch_bounds__(kApplyThreads, (sizeof(T) == 4 ? 4 : 2) * 256 
   }
   cp_async_wait<0>();
   __syncthreads();
-  issue_values<T>(rec, P.x, R, true);
+  // the element's corner codes and coefficient (global memory), in flight with the values
+  uint4 cw = make_uint4(0, 0, 0, 0);
+  T coef = T(0);
+  {
+    const int *h0 = reinterpret_cast<const int *>(rec);
+    if (tid < h0[1]) {
+      cw = reinterpret_cast<const uint4 *>(gb + h0[10])[tid];
+      coef = P.ce[reinterpret_cast<const int *>(gb + h0[12])[tid]];
+    }
+  }
+  issue_values<T>(rec, skip_bytes, P.x, R, true);
   cp_async_wait<0>();
   __syncthreads();
 
   const int *hdr = reinterpret_cast<const int *>(rec);
   const unsigned char *rb = reinterpret_cast<const unsigned char *>(rec);
   const int ne = hdr[1], nreg = hdr[2], nshared = hdr[3], nhang = hdr[4];
-  const int *lslot = reinterpret_cast<const int *>(rb + hdr[6]);
-  const uint2 *hent = reinterpret_cast<const uint2 *>(rb + hdr[7]);
-  const uint16_t *ip = reinterpret_cast<const uint16_t *>(rb + hdr[8]);
-  const uint16_t *iv = reinterpret_cast<const uint16_t *>(rb + hdr[9]);
-  const uint4 *lcorner = reinterpret_cast<const uint4 *>(rb + hdr[10]);
-  const uint32_t *lnode = reinterpret_cast<const uint32_t *>(rb + hdr[11]);
-  const int *elist = reinterpret_cast<const int *>(rb + hdr[12]);
+  const int *lslot = reinterpret_cast<const int *>(rb + hdr[6] - skip_bytes);
+  const uint2 *hent = reinterpret_cast<const uint2 *>(rb + hdr[7] - skip_bytes);
+  const uint16_t *ip = reinterpret_cast<const uint16_t *>(rb + hdr[8] - skip_bytes);
+  const uint16_t *iv = reinterpret_cast<const uint16_t *>(rb + hdr[9] - skip_bytes);
+  const uint32_t *lnode = reinterpret_cast<const uint32_t *>(rb + hdr[11] - skip_bytes);
 
   // 1. hanging nodes: (bi)linear interpolation of their masters (C)
   for (int j = tid; j < nhang; j += kApplyThreads) {
@@ -184,7 +199,6 @@ __global__ void __launch_bounds__(kApplyThreads, (sizeof(T) == 4 ? 4 : 2) * 256 
   // the sum of the element energies c_e X_e^T K0 X_e (C and the Dirichlet zeros are
   // already in X_e)
   if (tid < ne) {
-    const uint4 cw = lcorner[tid];
     const int code[8] = {(int)(cw.x & 0xFFFF), (int)(cw.x >> 16), (int)(cw.y & 0xFFFF), (int)(cw.y >> 16),
                          (int)(cw.z & 0xFFFF), (int)(cw.z >> 16), (int)(cw.w & 0xFFFF), (int)(cw.w >> 16)};
     T X[24], Y[24];
@@ -194,8 +208,8 @@ __global__ void __launch_bounds__(kApplyThreads, (sizeof(T) == 4 ? 4 : 2) * 256 
       X[3 * k + 1] = R[3 * code[k] + 1];
       X[3 * k + 2] = R[3 * code[k] + 2];
     }
-    if (P.dotp) dot = (double)element_op<T, kOpBoth>(X, Y, P.ce[elist[tid]], P.K);
-    else element_op<T, kOpApply>(X, Y, P.ce[elist[tid]], P.K);
+    if (P.dotp) dot = (double)element_op<T, kOpBoth>(X, Y, coef, P.K);
+    else element_op<T, kOpApply>(X, Y, coef, P.K);
 #pragma unroll
     for (int j = 0; j < 24; ++j) XY[tid * kRow + j] = Y[j];
   }
@@ -326,13 +340,13 @@ cudaError_t ensure_apply_smem(size_t smem) {
 template <typename T>
 cudaError_t launch_apply_blocks(const DeviceMesh &m, const T *ce, const T *x, T *y, T *part, double *energy_partials,
                                 SolveScalars *sc, unsigned int *ticket, const int *done, cudaStream_t s) {
-  const int rec_bytes = (m.max_rec_bytes + 15) / 16 * 16;
+  const int rec_bytes = (m.max_rec_stage + 15) / 16 * 16;
   const size_t smem = apply_smem_bytes<T>(m.max_local, rec_bytes);
   cudaError_t e = ensure_apply_smem<T>(smem);
   if (e != cudaSuccess) return e;
   const int ahead = sizeof(T) == 4 ? m.resident_cta32 : m.resident_cta64;
   ApplyParams<T> P;
-  P.brec = m.brec; P.rec_off = m.rec_off; P.ce = ce; P.x = x; P.y = y; P.part = part;
+  P.brec = m.brec; P.rec_off = m.rec_off; P.rec_skip = m.rec_skip; P.ce = ce; P.x = x; P.y = y; P.part = part;
   P.dotp = energy_partials; P.sc = sc; P.ticket = ticket; P.done = done; P.nblk = m.nblk;
   for (int i = 0; i < 72; ++i) (&P.K.b[0][0][0])[i] = (T)m.modal[i];
   P.max_local = m.max_local; P.rec_bytes = rec_bytes; P.ahead = ahead;
@@ -360,7 +374,7 @@ cudaError_t apply_residency(const DeviceMesh &m, int *resident32, int *resident6
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int rec_bytes = (m.max_rec_bytes + 15) / 16 * 16;
+  const int rec_bytes = (m.max_rec_stage + 15) / 16 * 16;
   const size_t s32 = apply_smem_bytes<float>(m.max_local, rec_bytes), s64 = apply_smem_bytes<double>(m.max_local, rec_bytes);
   e = ensure_apply_smem<float>(s32);
   if (e == cudaSuccess) e = ensure_apply_smem<double>(s64);

@@ -371,7 +371,7 @@ __device__ __forceinline__ void trilinear8(uint32_t code, int L, float w[8]) {
     w[q] = ((q & 1) ? tx : 1.f - tx) * ((q & 2) ? ty : 1.f - ty) * ((q & 4) ? tz : 1.f - tz);
 }
 
-// Stage 1 of P0^T r: one warp per segment (a run of <= 64 nodes of one base cell) sums w_q r over
+// Stage 1 of P0^T r: one warp per segment (a run of <= kSegNodes nodes of one base cell) sums w_q r over
 // its nodes; a node belongs to the cell holding it in its half-open box, clamped at the upper
 // faces of the domain.  Lane sums, then a fixed shuffle tree.
 __global__ void fine_restrict_cells_kernel(const float *r, int64_t r_ld, const int32_t *seg_ptr, const int32_t *cnode,

@@ -20,6 +20,7 @@
 #include <cstring>
 #include <map>
 #include <numeric>
+#include <thread>
 
 #include "tm_internal.h"
 
@@ -39,34 +40,77 @@ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
   return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
 }
 
+// the inverse of spread3: bits 0, 3, 6, ... of x packed together
+static inline uint32_t compact3(uint64_t x) {
+  x &= 0x1249249249249249ull;
+  x = (x | (x >> 2)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x >> 4)) & 0x100f00f00f00f00full;
+  x = (x | (x >> 8)) & 0x1f0000ff0000ffull;
+  x = (x | (x >> 16)) & 0x1f00000000ffffull;
+  x = (x | (x >> 32)) & 0x1fffffull;
+  return (uint32_t)x;
+}
+
 // LSD radix sort of keys, returning the permutation (stable).
 static_assert(kBlockElems * kSlotRow < kQuarterBit, "inverse-list slot offsets must stay below the fold bits");
 
-static std::vector<int64_t> radix_order(const std::vector<uint64_t> &key) {
+// Host threads for the table builds: up to 16, at most one per 64k items.
+static int host_threads(size_t n) {
+  const int hw = (int)std::thread::hardware_concurrency();
+  return (int)std::max<size_t>(1, std::min<size_t>({(size_t)16, (size_t)(hw > 0 ? hw : 1), n / 65536 + 1}));
+}
+
+// f(t, lo, hi) over nt contiguous chunks of [0, n), one host thread each.
+template <typename F>
+static void chunked(int nt, size_t n, F f) {
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back([&, t] { f(t, n * t / nt, n * (t + 1) / nt); });
+  f(0, 0, n / nt);
+  for (auto &th : pool) th.join();
+}
+
+// Each pass: per-chunk digit counts, then every chunk scatters its items in order to the positions
+// the counts of the lower digits and of the earlier chunks leave free -- the sequential stable
+// order, whatever the number of threads.
+static std::vector<int64_t> radix_order(const std::vector<uint64_t> &key, std::vector<uint64_t> *sorted = nullptr) {
   const size_t n = key.size();
   uint64_t mx = 0;
   for (uint64_t k : key) mx |= k;
   int bits = 0;
   while (bits < 64 && (mx >> bits)) ++bits;
   // keys travel with their indices, so every pass streams both arrays in order
-  std::vector<int64_t> idx(n), tmp(n);
+  std::vector<uint32_t> idx(n), tmp(n);
   std::vector<uint64_t> k(key), ktmp(n);
-  std::iota(idx.begin(), idx.end(), 0);
+  std::iota(idx.begin(), idx.end(), 0u);
   const int R = 11, B = 1 << R;
-  std::vector<size_t> cnt(B + 1);
+  const int nt = host_threads(n);
+  std::vector<size_t> cnt((size_t)nt * B);
   for (int sh = 0; sh < bits; sh += R) {
-    std::fill(cnt.begin(), cnt.end(), 0);
-    for (size_t i = 0; i < n; ++i) cnt[((k[i] >> sh) & (B - 1)) + 1]++;
-    for (int b = 0; b < B; ++b) cnt[b + 1] += cnt[b];
-    for (size_t i = 0; i < n; ++i) {
-      const size_t d = cnt[(k[i] >> sh) & (B - 1)]++;
-      tmp[d] = idx[i];
-      ktmp[d] = k[i];
-    }
+    chunked(nt, n, [&](int t, size_t lo, size_t hi) {
+      size_t *c = &cnt[(size_t)t * B];
+      std::fill(c, c + B, 0);
+      for (size_t i = lo; i < hi; ++i) c[(k[i] >> sh) & (B - 1)]++;
+    });
+    size_t run = 0;   // digit-major, chunk-minor exclusive prefix
+    for (int d = 0; d < B; ++d)
+      for (int t = 0; t < nt; ++t) {
+        const size_t v = cnt[(size_t)t * B + d];
+        cnt[(size_t)t * B + d] = run;
+        run += v;
+      }
+    chunked(nt, n, [&](int t, size_t lo, size_t hi) {
+      size_t *c = &cnt[(size_t)t * B];
+      for (size_t i = lo; i < hi; ++i) {
+        const size_t d = c[(k[i] >> sh) & (B - 1)]++;
+        tmp[d] = idx[i];
+        ktmp[d] = k[i];
+      }
+    });
     idx.swap(tmp);
     k.swap(ktmp);
   }
-  return idx;
+  if (sorted) sorted->swap(k);
+  return std::vector<int64_t>(idx.begin(), idx.end());
 }
 
 void reference_stiffness(double nu, double *K0) {
@@ -127,6 +171,7 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
   if (d.max_level < 0 || d.max_level > 12) return "max_level must be in [0, 12]";
   if (!(d.h0 > 0)) return "h0 must be positive";
   if (d.n_leaves < 1 || !d.leaves) return "no leaves";
+  if (d.n_leaves >= (int64_t)1 << 29) return "more than 2^29 - 1 leaves";   // 8 corners each, 32-bit sort indices
   if (!(d.nu > -1.0 && d.nu < 0.5)) return "Poisson ratio must be in (-1, 0.5)";
   if (!(d.E0 > d.Emin && d.Emin >= 0)) return "need E0 > Emin >= 0";
   if (!(d.penal >= 1)) return "penalty must be >= 1";
@@ -168,42 +213,46 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
   }
   if (covered != fx * fy * fz) return "leaves do not cover the domain";
 
-  // ---- 2. nodes
+  // ---- 2. nodes: the distinct corner keys in Morton order; conn and coordinates from them
   std::vector<uint64_t> ckey(8 * Ne);
-  for (int64_t e = 0; e < Ne; ++e) {
-    const int32_t *l = &m.leaf[4 * e];
-    const int32_t s = 1 << (L - l[3]);
-    for (int k = 0; k < 8; ++k)
-      ckey[8 * e + k] = morton3(l[0] + s * (k & 1), l[1] + s * ((k >> 1) & 1), l[2] + s * ((k >> 2) & 1));
-  }
+  chunked(host_threads(Ne), (size_t)Ne, [&](int, size_t lo, size_t hi) {
+    for (size_t e = lo; e < hi; ++e) {
+      const int32_t *l = &m.leaf[4 * e];
+      const int32_t s = 1 << (L - l[3]);
+      for (int k = 0; k < 8; ++k)
+        ckey[8 * e + k] = morton3(l[0] + s * (k & 1), l[1] + s * ((k >> 1) & 1), l[2] + s * ((k >> 2) & 1));
+    }
+  });
   {
-    std::vector<int64_t> ord = radix_order(ckey);
-    m.conn.resize(8 * Ne);
+    std::vector<uint64_t> sk;
+    const std::vector<int64_t> ord = radix_order(ckey, &sk);
+    std::vector<int32_t> nid(8 * Ne);
     int64_t nn = -1;
     uint64_t prev = ~0ull;
     for (int64_t i = 0; i < 8 * Ne; ++i) {
-      const uint64_t k = ckey[ord[i]];
-      if (k != prev) {
+      if (sk[i] != prev) {
         ++nn;
-        m.node_key.push_back(k);
-        prev = k;
+        m.node_key.push_back(sk[i]);
+        prev = sk[i];
       }
-      m.conn[ord[i]] = (int32_t)nn;
+      nid[i] = (int32_t)nn;
     }
     m.Nn = nn + 1;
+    m.conn.resize(8 * Ne);
+    chunked(host_threads(8 * Ne), (size_t)(8 * Ne), [&](int, size_t lo, size_t hi) {
+      for (size_t i = lo; i < hi; ++i) m.conn[ord[i]] = nid[i];
+    });
   }
   const int64_t Nn = m.Nn;
   m.node_xyz.resize(3 * Nn);
-  for (int64_t e = 0; e < Ne; ++e) {
-    const int32_t *l = &m.leaf[4 * e];
-    const int32_t s = 1 << (L - l[3]);
-    for (int k = 0; k < 8; ++k) {
-      const int32_t n = m.conn[8 * e + k];
-      m.node_xyz[3 * n] = l[0] + s * (k & 1);
-      m.node_xyz[3 * n + 1] = l[1] + s * ((k >> 1) & 1);
-      m.node_xyz[3 * n + 2] = l[2] + s * ((k >> 2) & 1);
+  chunked(host_threads(Nn), (size_t)Nn, [&](int, size_t lo, size_t hi) {
+    for (size_t n = lo; n < hi; ++n) {
+      const uint64_t k = m.node_key[n];
+      m.node_xyz[3 * n] = (int32_t)compact3(k);
+      m.node_xyz[3 * n + 1] = (int32_t)compact3(k >> 1);
+      m.node_xyz[3 * n + 2] = (int32_t)compact3(k >> 2);
     }
-  }
+  });
 
   // ---- 3. balance via a dense owner map of the finest cells
   {
@@ -240,42 +289,47 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
                                      {4, 6}, {5, 7}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
     static const int faces[6][4] = {{0, 2, 4, 6}, {1, 3, 5, 7}, {0, 1, 4, 5},
                                     {2, 3, 6, 7}, {0, 1, 2, 3}, {4, 5, 6, 7}};
-    for (int64_t e = 0; e < Ne; ++e) {
-      const int32_t *l = &m.leaf[4 * e];
-      const int32_t s = 1 << (L - l[3]);
-      if (s < 2) continue;
-      const int32_t *cn = &m.conn[8 * e];
-      auto probe = [&](const int *cs, int nc) -> std::string {
-        int64_t x = 0, y = 0, z = 0;
-        for (int i = 0; i < nc; ++i) {
-          x += m.node_xyz[3 * cn[cs[i]]];
-          y += m.node_xyz[3 * cn[cs[i]] + 1];
-          z += m.node_xyz[3 * cn[cs[i]] + 2];
-        }
-        x /= nc; y /= nc; z /= nc;
-        const int64_t n = find_key(m.node_key, morton3((uint32_t)x, (uint32_t)y, (uint32_t)z));
-        if (n < 0) return "";
-        std::array<int32_t, 4> ms = {-1, -1, -1, -1};
-        for (int i = 0; i < nc; ++i) ms[i] = cn[cs[i]];
-        std::sort(ms.begin(), ms.begin() + nc);
-        if (m.hang_index[n] < 0) {
-          m.hang_index[n] = (int32_t)masters.size();
-          masters.push_back(ms);
-          m.hang_node.push_back((int32_t)n);
-        } else if (masters[m.hang_index[n]] != ms) {
+    // probes in parallel over element chunks (edge midpoints and face centres that are nodes,
+    // with their sorted masters), merged in element order
+    struct Found { int32_t n; std::array<int32_t, 4> ms; };
+    const int nt = host_threads(Ne);
+    std::vector<std::vector<Found>> found(nt);
+    chunked(nt, (size_t)Ne, [&](int t, size_t lo, size_t hi) {
+      std::vector<Found> &out = found[t];
+      for (size_t e = lo; e < hi; ++e) {
+        const int32_t *l = &m.leaf[4 * e];
+        const int32_t s = 1 << (L - l[3]);
+        if (s < 2) continue;
+        const int32_t *cn = &m.conn[8 * e];
+        auto probe = [&](const int *cs, int nc) {
+          int64_t x = 0, y = 0, z = 0;
+          for (int i = 0; i < nc; ++i) {
+            x += m.node_xyz[3 * cn[cs[i]]];
+            y += m.node_xyz[3 * cn[cs[i]] + 1];
+            z += m.node_xyz[3 * cn[cs[i]] + 2];
+          }
+          x /= nc; y /= nc; z /= nc;
+          const int64_t n = find_key(m.node_key, morton3((uint32_t)x, (uint32_t)y, (uint32_t)z));
+          if (n < 0) return;
+          Found f{(int32_t)n, {-1, -1, -1, -1}};
+          for (int i = 0; i < nc; ++i) f.ms[i] = cn[cs[i]];
+          std::sort(f.ms.begin(), f.ms.begin() + nc);
+          out.push_back(f);
+        };
+        for (auto &ed : edges) probe(ed, 2);
+        for (auto &fc : faces) probe(fc, 4);
+      }
+    });
+    for (const auto &fv : found)
+      for (const Found &f : fv) {
+        if (m.hang_index[f.n] < 0) {
+          m.hang_index[f.n] = (int32_t)masters.size();
+          masters.push_back(f.ms);
+          m.hang_node.push_back(f.n);
+        } else if (masters[m.hang_index[f.n]] != f.ms) {
           return "inconsistent hanging-node constraints";
         }
-        return "";
-      };
-      for (auto &ed : edges) {
-        std::string r = probe(ed, 2);
-        if (!r.empty()) return r;
       }
-      for (auto &fc : faces) {
-        std::string r = probe(fc, 4);
-        if (!r.empty()) return r;
-      }
-    }
     // ascending node order
     std::vector<int32_t> ord(m.hang_node.size());
     std::iota(ord.begin(), ord.end(), 0);
@@ -689,7 +743,9 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
   //   follows lcorner.
   {
     m.rec_off.assign(nblk + 1, 0);
+    m.rec_skip.assign(nblk, 0);
     m.max_rec_bytes = 0;
+    m.max_rec_stage = 0;
     auto align = [](size_t v, size_t a) { return (v + a - 1) / a * a; };
     for (int32_t b = 0; b < nblk; ++b) {
       const int32_t nreg = m.blk_node[b + 1] - m.blk_node[b];
@@ -701,6 +757,7 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
       size_t off = 64;
       const size_t o_lcorner = off; off += 16 * (size_t)ne;
       const size_t o_elist = off; off += 4 * (size_t)ne;
+      off = align(off, 16);   // the sections from lnode on are staged into shared memory
       const size_t o_lnode = off; off += 4 * (size_t)nreg;
       const size_t o_lslot = off; off += 4 * (size_t)nshared;
       off = align(off, 8);
@@ -728,6 +785,8 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
       m.brec.insert(m.brec.end(), rec.begin(), rec.end());
       m.rec_off[b + 1] = (int32_t)(m.brec.size() / 16);
       m.max_rec_bytes = std::max<int32_t>(m.max_rec_bytes, (int32_t)bytes);
+      m.rec_skip[b] = (int32_t)((o_lnode - 64) / 16);
+      m.max_rec_stage = std::max<int32_t>(m.max_rec_stage, (int32_t)(bytes - (o_lnode - 64)));
     }
   }
 
@@ -742,64 +801,87 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
       tab_index[kq] = 0;
       m.dg_tab.insert(m.dg_tab.end(), {q, q, q});
     }
-    // pass 1: count the entries of every node; elements with hanging corners list their
-    // (node, coefficient triple) entries once, in element order, for pass 2
-    std::vector<int32_t> cnt(Nn + 1, 0);
-    std::vector<int32_t> ex_node;     // entries of elements with hanging corners
-    std::vector<uint16_t> ex_q;
-    std::vector<int32_t> ex_end(Ne, 0);   // prefix end of each element's entries (others: unchanged)
-    for (int64_t e = 0; e < Ne; ++e) {
-      bool plain = true;
-      for (int k = 0; k < 8; ++k) plain &= m.hang_index[m.conn[8 * e + k]] < 0;
-      if (plain) {
-        for (int k = 0; k < 8; ++k) cnt[m.conn[8 * e + k] + 1]++;
-        ex_end[e] = (int32_t)ex_node.size();
-        continue;
-      }
-      // corner expansion: (node, weight) pairs
-      int32_t nodes[32];
-      double wts[32];
-      int corner_of[32];
-      int np = 0;
-      for (int k = 0; k < 8; ++k) {
-        const int32_t n = m.conn[8 * e + k];
-        const int32_t h = m.hang_index[n];
-        if (h < 0) {
-          nodes[np] = n; wts[np] = 1.0; corner_of[np++] = k;
-        } else {
-          int nm = 0;
-          for (int j = 0; j < 4; ++j) nm += m.hang_master[4 * h + j] >= 0;
-          for (int j = 0; j < nm; ++j) {
-            nodes[np] = m.hang_master[4 * h + j]; wts[np] = 1.0 / nm; corner_of[np++] = k;
+    // pass 1 (in parallel over element chunks): elements with hanging corners list their
+    // (node, coefficient triple) entries in element order; every chunk numbers the distinct
+    // triples it meets in order of first appearance, and the chunks' numberings are merged in
+    // chunk order, so the table is the one an element-order pass would build
+    const int nt = host_threads(Ne);
+    std::vector<std::vector<int32_t>> cx_node(nt), cx_lq(nt);
+    std::vector<std::vector<std::array<double, 3>>> cx_tab(nt);
+    std::vector<int32_t> ex_end(Ne, 0);   // per element: end of its entries within its chunk's list
+    chunked(nt, (size_t)Ne, [&](int t, size_t lo, size_t hi) {
+      std::map<std::array<int64_t, 3>, int> local;
+      for (size_t e = lo; e < hi; ++e) {
+        bool plain = true;
+        for (int k = 0; k < 8; ++k) plain &= m.hang_index[m.conn[8 * e + k]] < 0;
+        if (plain) {
+          ex_end[e] = (int32_t)cx_node[t].size();
+          continue;
+        }
+        // corner expansion: (node, weight) pairs
+        int32_t nodes[32];
+        double wts[32];
+        int corner_of[32];
+        int np = 0;
+        for (int k = 0; k < 8; ++k) {
+          const int32_t n = m.conn[8 * e + k];
+          const int32_t h = m.hang_index[n];
+          if (h < 0) {
+            nodes[np] = n; wts[np] = 1.0; corner_of[np++] = k;
+          } else {
+            int nm = 0;
+            for (int j = 0; j < 4; ++j) nm += m.hang_master[4 * h + j] >= 0;
+            for (int j = 0; j < nm; ++j) {
+              nodes[np] = m.hang_master[4 * h + j]; wts[np] = 1.0 / nm; corner_of[np++] = k;
+            }
           }
         }
-      }
-      int32_t uniq[32];
-      int nu_ = 0;
-      for (int i = 0; i < np; ++i) {
-        bool seen = false;
-        for (int j = 0; j < nu_; ++j) seen |= uniq[j] == nodes[i];
-        if (!seen) uniq[nu_++] = nodes[i];
-      }
-      for (int u = 0; u < nu_; ++u) {
-        double v[8] = {};
-        for (int i = 0; i < np; ++i)
-          if (nodes[i] == uniq[u]) v[corner_of[i]] += wts[i];
-        // q_c = v^T K0_cc v over the corners where v is nonzero, in ascending corner order
-        // (the zero terms of the full double sum add nothing)
-        int nz[8], nnz = 0;
-        for (int a = 0; a < 8; ++a)
-          if (v[a] != 0.0) nz[nnz++] = a;
-        double q[3];
-        for (int c = 0; c < 3; ++c) {
-          double s = 0;
-          for (int ia = 0; ia < nnz; ++ia)
-            for (int ib = 0; ib < nnz; ++ib) {
-              const int a = nz[ia], b2 = nz[ib];
-              s += v[a] * v[b2] * m.K0[(3 * a + c) * 24 + 3 * b2 + c];
-            }
-          q[c] = s;
+        int32_t uniq[32];
+        int nu_ = 0;
+        for (int i = 0; i < np; ++i) {
+          bool seen = false;
+          for (int j = 0; j < nu_; ++j) seen |= uniq[j] == nodes[i];
+          if (!seen) uniq[nu_++] = nodes[i];
         }
+        for (int u = 0; u < nu_; ++u) {
+          double v[8] = {};
+          for (int i = 0; i < np; ++i)
+            if (nodes[i] == uniq[u]) v[corner_of[i]] += wts[i];
+          // q_c = v^T K0_cc v over the corners where v is nonzero, in ascending corner order
+          // (the zero terms of the full double sum add nothing)
+          int nz[8], nnz = 0;
+          for (int a = 0; a < 8; ++a)
+            if (v[a] != 0.0) nz[nnz++] = a;
+          std::array<double, 3> q;
+          for (int c = 0; c < 3; ++c) {
+            double s = 0;
+            for (int ia = 0; ia < nnz; ++ia)
+              for (int ib = 0; ib < nnz; ++ib) {
+                const int a = nz[ia], b2 = nz[ib];
+                s += v[a] * v[b2] * m.K0[(3 * a + c) * 24 + 3 * b2 + c];
+              }
+            q[c] = s;
+          }
+          std::array<int64_t, 3> kq;
+          for (int c = 0; c < 3; ++c) std::memcpy(&kq[c], &q[c], 8);
+          auto it = local.find(kq);
+          int li;
+          if (it == local.end()) {
+            li = (int)cx_tab[t].size();
+            local[kq] = li;
+            cx_tab[t].push_back(q);
+          } else {
+            li = it->second;
+          }
+          cx_node[t].push_back(uniq[u]);
+          cx_lq[t].push_back(li);
+        }
+        ex_end[e] = (int32_t)cx_node[t].size();
+      }
+    });
+    std::vector<std::vector<uint16_t>> l2g(nt);
+    for (int t = 0; t < nt; ++t)
+      for (const auto &q : cx_tab[t]) {
         std::array<int64_t, 3> kq;
         for (int c = 0; c < 3; ++c) std::memcpy(&kq[c], &q[c], 8);
         auto it = tab_index.find(kq);
@@ -808,15 +890,42 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
           qi = (int)tab_index.size();
           if (qi >= 65535) return "too many distinct diagonal coefficients";
           tab_index[kq] = qi;
-          m.dg_tab.insert(m.dg_tab.end(), q, q + 3);
+          m.dg_tab.insert(m.dg_tab.end(), q.begin(), q.end());
         } else {
           qi = it->second;
         }
-        ex_node.push_back(uniq[u]);
-        ex_q.push_back((uint16_t)qi);
-        cnt[uniq[u] + 1]++;
+        l2g[t].push_back((uint16_t)qi);
       }
-      ex_end[e] = (int32_t)ex_node.size();
+    // the entries in element order, and the count of every node
+    std::vector<int32_t> ex_node;
+    std::vector<uint16_t> ex_q;
+    std::vector<int64_t> chunk_base(nt + 1, 0);
+    for (int t = 0; t < nt; ++t) {
+      chunk_base[t + 1] = chunk_base[t] + (int64_t)cx_node[t].size();
+      for (size_t i = 0; i < cx_node[t].size(); ++i) {
+        ex_node.push_back(cx_node[t][i]);
+        ex_q.push_back(l2g[t][cx_lq[t][i]]);
+      }
+    }
+    for (int t = 0; t < nt; ++t) {   // ex_end relative to the whole list
+      const size_t lo = (size_t)Ne * t / nt, hi = (size_t)Ne * (t + 1) / nt;
+      for (size_t e = lo; e < hi; ++e) ex_end[e] += (int32_t)chunk_base[t];
+    }
+    std::vector<int32_t> cnt(Nn + 1, 0);
+    {
+      int32_t x0 = 0;
+      for (int64_t e = 0; e < Ne; ++e) {
+        if (ex_end[e] == x0) {
+          bool plain = true;
+          for (int k = 0; k < 8; ++k) plain &= m.hang_index[m.conn[8 * e + k]] < 0;
+          if (plain) {
+            for (int k = 0; k < 8; ++k) cnt[m.conn[8 * e + k] + 1]++;
+            continue;
+          }
+        }
+        for (int32_t i = x0; i < ex_end[e]; ++i) cnt[ex_node[i] + 1]++;
+        x0 = ex_end[e];
+      }
     }
     // pass 2: fill the node-major CSR in element order
     m.dg_ptr.assign(Nn + 1, 0);

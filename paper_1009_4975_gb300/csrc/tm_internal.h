@@ -67,7 +67,9 @@ struct HostMesh {
   std::vector<uint16_t> lcorner;      // 8 per element: local ids of its corners within its block
   std::vector<uint8_t> brec;          // per-block records (see mesh_host.cpp, 16-byte aligned)
   std::vector<int32_t> rec_off;       // nblk+1: record ranges in 16-byte units
+  std::vector<int32_t> rec_skip;      // nblk: 16-byte units of lcorner and elist (not staged)
   int32_t max_rec_bytes = 0;
+  int32_t max_rec_stage = 0;          // largest staged part: header + the sections from lnode on
   // bricks (mesh_host.cpp, section 6a): aligned 4x4x4 runs of 64 equal-level elements taken by
   // the brick pass; their 5x5x5 node lattice is node (a, b, c) at a + 5 b + 25 c
   int32_t nbrick = 0;
@@ -133,7 +135,8 @@ struct DeviceMesh {
   int32_t max_local = 0;
   uint4 *brec = nullptr;
   int32_t *rec_off = nullptr;
-  int32_t max_rec_bytes = 0;
+  int32_t *rec_skip = nullptr;
+  int32_t max_rec_bytes = 0, max_rec_stage = 0;
   int32_t resident_cta32 = 0, resident_cta64 = 0;  // block-pass CTAs resident on the GPU (record prefetch distance)
   int32_t nbrick = 0;                 // bricks (HostMesh): CTAs nblk .. of the block pass take 4 each
   int32_t *brick_tab = nullptr;       // 384 per brick (brick.cuh)
@@ -180,6 +183,7 @@ struct CoarseHierarchy {
   double *Kc64 = nullptr;                // coarsest level's cell matrices in FP64
   float *Ainv = nullptr;                 // coarsest level: dense inverse over all its DOFs
   std::vector<double> Kc_host;           // host copy of Kc64 (inverse formed on the host)
+  std::vector<float> Ainv_host;          // the inverse, kept until its upload has completed
   std::vector<void *> owned;
   int64_t bytes = 0;
 };
@@ -297,6 +301,7 @@ struct tm_ctx {
   std::deque<Graph> graphs;
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_coarse = nullptr;   // the coarsest level's cell matrices reached the host
   bool capturing = false;
 };
 
