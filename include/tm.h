@@ -251,8 +251,8 @@ int tm_apply_K_f32_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const flo
  * passes rho, x and y as for tm_apply_K_f32; the uploaded mesh must have at most
  * 2,097,152 elements and 2,097,152 shared-node partials, else TM_EINVAL names
  * the sizes.  The first call on a device looks up the array's device address
- * (module set-up, once per device, with that device current): make that first
- * call before any stream capture.  All calls share the one array and every call
+ * (module set-up, once per device under a lock, with that device current).  All
+ * calls share the one array and every call
  * overwrites all of it that it reads, so nothing carries over between calls;
  * calls that overlap on the GPU (other streams, other contexts of the same
  * device) race on it, so the caller serialises them.  tm_profile does not time
