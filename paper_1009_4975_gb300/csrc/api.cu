@@ -276,6 +276,11 @@ int ensure_coarse(tm_ctx *ctx) {
   TM_CUDA(ctx, upload(o, B, &h.cnode, cnode));
   TM_CUDA(ctx, upload(o, B, &h.ncell, ncell));
   TM_CUDA(ctx, upload(o, B, &h.code, code));
+  {
+    std::vector<uint32_t> ccode(cnode.size());   // the codes in cnode order
+    for (size_t p = 0; p < cnode.size(); ++p) ccode[p] = code[cnode[p]];
+    TM_CUDA(ctx, upload(o, B, &h.ccode, ccode));
+  }
   TM_CUDA(ctx, upload(o, B, &h.seg_ptr, seg_ptr));
   TM_CUDA(ctx, upload(o, B, &h.seg_cell, seg_cell));
   TM_CUDA(ctx, upload(o, B, &h.cseg, cseg));

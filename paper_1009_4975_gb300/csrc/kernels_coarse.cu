@@ -375,7 +375,7 @@ __device__ __forceinline__ void trilinear8(uint32_t code, int L, float w[8]) {
 // its nodes; a node belongs to the cell holding it in its half-open box, clamped at the upper
 // faces of the domain.  Lane sums, then a fixed shuffle tree.
 __global__ void fine_restrict_cells_kernel(const float *r, int64_t r_ld, const int32_t *seg_ptr, const int32_t *cnode,
-                                           const uint32_t *code, int nseg, int L, float *part, Cases cs) {
+                                           const uint32_t *ccode, int nseg, int L, float *part, Cases cs) {
   pdl_begin();
   const int cc = case_of(cs, blockIdx.y);
   if (case_done(cs, cc)) return;
@@ -390,7 +390,7 @@ __global__ void fine_restrict_cells_kernel(const float *r, int64_t r_ld, const i
   const int p1 = seg_ptr[warp + 1];
   for (int p = seg_ptr[warp] + lane; p < p1; p += 32) {
     const int n = cnode[p];
-    const uint32_t cd = code[n];
+    const uint32_t cd = ccode[p];   // loaded beside n, not after it
     if (cd >> 31) continue;
     float w[8];
     trilinear8(cd, L, w);
@@ -600,7 +600,7 @@ cudaError_t coarse_restrict_launch(const DeviceMesh &m, const CoarseHierarchy &h
   const CoarseLevel &l0 = h.lev[0];
   const Cases cs{sc, c0};
   const dim3 g1(grid_for(32 * (int64_t)h.nseg), nv);
-  { const cudaError_t pe_ = launch_pdl(fine_restrict_cells_kernel, dim3(g1), dim3(kT), 0, s, r, r_ld, h.seg_ptr, h.cnode, h.code, h.nseg, m.L, h.part, cs); if (pe_ != cudaSuccess) return pe_; }
+  { const cudaError_t pe_ = launch_pdl(fine_restrict_cells_kernel, dim3(g1), dim3(kT), 0, s, r, r_ld, h.seg_ptr, h.cnode, h.ccode, h.nseg, m.L, h.part, cs); if (pe_ != cudaSuccess) return pe_; }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const bool sweep = first_sweep && h.nlev > 1;

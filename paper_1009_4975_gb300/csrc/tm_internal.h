@@ -178,6 +178,7 @@ struct CoarseHierarchy {
   int32_t *cseg = nullptr;               // base cells + 1: cell c's segments [cseg[c], cseg[c+1])
   int32_t *ncell = nullptr;              // per mesh node: its base cell
   uint32_t *code = nullptr;              // per mesh node: position in the cell, bit 31 = no unknowns
+  uint32_t *ccode = nullptr;             // the same codes in cnode order (read beside cnode)
   double *Q = nullptr;                   // 27 x 576: moment -> cell-matrix coefficients
   float *part = nullptr;                 // kMaxRhs cases x segments x 24: partial restrictions
   double *Kc64 = nullptr;                // coarsest level's cell matrices in FP64
