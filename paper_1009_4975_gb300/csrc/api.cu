@@ -285,7 +285,29 @@ int ensure_coarse(tm_ctx *ctx) {
   TM_CUDA(ctx, upload(o, B, &h.seg_cell, seg_cell));
   TM_CUDA(ctx, upload(o, B, &h.cseg, cseg));
   h.nseg = (int32_t)seg_cell.size();
-  TM_CUDA(ctx, upload(o, B, &h.Q, Q));
+  {
+    // the symmetric cell matrices by upper-triangle entry, with the moments that contribute
+    std::vector<int32_t> qent(kCellUpper);
+    std::vector<uint8_t> qidx((size_t)kCellUpper * kCellNnz, 0);
+    std::vector<double> qval((size_t)kCellUpper * kCellNnz, 0.0);
+    int u = 0;
+    for (int i = 0; i < 24; ++i)
+      for (int j = i; j < 24; ++j, ++u) {
+        int nnz = 0;
+        for (int q = 0; q < 27; ++q) {
+          const double v = Q[(size_t)q * 576 + 24 * i + j];
+          if (v != 0.0) {
+            qidx[(size_t)u * kCellNnz + nnz] = (uint8_t)q;
+            qval[(size_t)u * kCellNnz + nnz] = v;
+            ++nnz;
+          }
+        }
+        qent[u] = i | (j << 5) | (nnz << 10);
+      }
+    TM_CUDA(ctx, upload(o, B, &h.qent, qent));
+    TM_CUDA(ctx, upload(o, B, &h.qidx, qidx));
+    TM_CUDA(ctx, upload(o, B, &h.qval, qval));
+  }
   const int nlev = (int)shapes.size() / 3;
   for (int l = 0; l < nlev; ++l) {
     CoarseLevel &c = h.lev[l];

@@ -144,18 +144,29 @@ __global__ void moments_up_kernel(const double *mc, int Xc, int Yc, int Zc, int 
   for (int q = 0; q < 27; ++q) mp[27 * (int64_t)p + q] = acc[q];
 }
 
-// K_C = (2/H)^2 sum_q Q_q mom_q, one thread per (cell, entry); FP64 accumulation.
-__global__ void cellmat_kernel(const double *mom, const double *Q, int ncell, double H, float *K32, double *K64) {
+// K_C = (2/H)^2 sum_q Q_q mom_q, one thread per (cell, upper-triangle entry); FP64 accumulation
+// over the moments whose coefficient is nonzero (in ascending q: the same sum as over all 27),
+// stored to the entry and its mirror (the Q_q are symmetric).
+__global__ void cellmat_kernel(const double *mom, const int32_t *qent, const uint8_t *qidx, const double *qval,
+                               int ncell, double H, float *K32, double *K64) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= (int64_t)ncell * 576) return;
-  const int64_t c = t / 576;
-  const int ent = (int)(t % 576);
+  if (t >= (int64_t)ncell * kCellUpper) return;
+  const int64_t c = t / kCellUpper;
+  const int u = (int)(t % kCellUpper);
+  const int e = qent[u], i = e & 31, j = (e >> 5) & 31, nnz = e >> 10;
+  const double *mc = mom + 27 * c;
   double s = 0.0;
-#pragma unroll
-  for (int q = 0; q < 27; ++q) s += Q[q * 576 + ent] * mom[27 * c + q];
+  for (int k = 0; k < nnz; ++k) s += qval[u * kCellNnz + k] * mc[qidx[u * kCellNnz + k]];
   s *= 4.0 / (H * H);
-  if (K32) K32[t] = (float)s;
-  if (K64) K64[t] = s;
+  const int64_t a = 576 * c + 24 * i + j, b = 576 * c + 24 * j + i;
+  if (K32) {
+    K32[a] = (float)s;
+    K32[b] = (float)s;
+  }
+  if (K64) {
+    K64[a] = s;
+    K64[b] = s;
+  }
 }
 
 // Inverse l1 row sums of the assembled level matrix: d_(I,c) = sum over free neighbours J, c'
@@ -584,8 +595,9 @@ cudaError_t coarse_setup_launch(const DeviceMesh &m, CoarseHierarchy &h, const d
   }
   for (int l = 0; l < h.nlev; ++l) {
     const CoarseLevel &c = h.lev[l];
-    const int64_t n = (int64_t)c.X * c.Y * c.Z * 576;
-    cellmat_kernel<<<grid_for(n), kT, 0, s>>>(c.mom, h.Q, c.X * c.Y * c.Z, c.H, c.K, l == h.nlev - 1 ? h.Kc64 : nullptr);
+    const int64_t n = (int64_t)c.X * c.Y * c.Z * kCellUpper;
+    cellmat_kernel<<<grid_for(n), kT, 0, s>>>(c.mom, h.qent, h.qidx, h.qval, c.X * c.Y * c.Z, c.H, c.K,
+                                              l == h.nlev - 1 ? h.Kc64 : nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (l < h.nlev - 1) {
       l1diag_kernel<<<grid_for(c.nodes), kT, 0, s>>>(c.K, c.X, c.Y, c.Z, h.faces, c.dinv);

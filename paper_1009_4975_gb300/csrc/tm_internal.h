@@ -179,7 +179,12 @@ struct CoarseHierarchy {
   int32_t *ncell = nullptr;              // per mesh node: its base cell
   uint32_t *code = nullptr;              // per mesh node: position in the cell, bit 31 = no unknowns
   uint32_t *ccode = nullptr;             // the same codes in cnode order (read beside cnode)
-  double *Q = nullptr;                   // 27 x 576: moment -> cell-matrix coefficients
+  // the moment -> cell-matrix coefficients (27 x 576, coarse_moment_matrices), as the upper
+  // triangle by entry: qent[u] = i | j << 5 | nonzeros << 10, then per entry the
+  // moments with a nonzero coefficient (qidx, ascending) and the coefficients (qval)
+  int32_t *qent = nullptr;
+  uint8_t *qidx = nullptr;
+  double *qval = nullptr;
   float *part = nullptr;                 // kMaxRhs cases x segments x 24: partial restrictions
   double *Kc64 = nullptr;                // coarsest level's cell matrices in FP64
   float *Ainv = nullptr;                 // coarsest level: dense inverse over all its DOFs
@@ -194,6 +199,8 @@ std::string coarse_shapes(const HostMesh &m, std::vector<int> &shapes);
 void coarse_tables(const HostMesh &m, std::vector<int32_t> &cell_elem, std::vector<int32_t> &cptr,
                    std::vector<int32_t> &cnode, std::vector<int32_t> &ncell, std::vector<uint32_t> &code);
 constexpr int kSegNodes = 64;
+constexpr int kCellUpper = 300;   // entries of the upper triangle of a 24 x 24 cell matrix
+constexpr int kCellNnz = 27;      // room per entry for its nonzero moment coefficients
 void coarse_segments(const std::vector<int32_t> &cptr, std::vector<int32_t> &seg_ptr, std::vector<int32_t> &seg_cell,
                      std::vector<int32_t> &cseg);
 void coarse_moment_matrices(double nu, std::vector<double> &Q);
