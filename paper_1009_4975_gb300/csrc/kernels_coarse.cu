@@ -76,6 +76,7 @@ __global__ void moments0_kernel(const int32_t *cell_elem, const int32_t *leaf, c
   if (warp >= ncell) return;
   const int cx = warp % X, cy = (warp / X) % Y, cz = warp / (X * Y);
   const int S = 1 << L;
+  const double invS = 1.0 / S;   // a power of two: dividing by S and multiplying by invS agree exactly
   const int o[3] = {cx * S, cy * S, cz * S};
   double m[27];
 #pragma unroll
@@ -88,17 +89,22 @@ __global__ void moments0_kernel(const int32_t *cell_elem, const int32_t *leaf, c
     double I[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double lo = 2.0 * (double)(l[a] - o[a]) / S - 1.0, hi = 2.0 * (double)(l[a] + s - o[a]) / S - 1.0;
+      const double lo = 2.0 * (double)(l[a] - o[a]) * invS - 1.0, hi = 2.0 * (double)(l[a] + s - o[a]) * invS - 1.0;
       I[a][0] = 0.5 * H * (hi - lo);
-      I[a][1] = 0.5 * H * (hi * hi - lo * lo) / 2.0;
+      I[a][1] = 0.5 * H * (hi * hi - lo * lo) * 0.5;
       I[a][2] = 0.5 * H * (hi * hi * hi - lo * lo * lo) / 3.0;
     }
+    double EI[9];   // ((E I_x) I_y), the leading products of the moment terms below
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) EI[a + 3 * b] = E * I[0][a] * I[1][b];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
       for (int b = 0; b < 3; ++b)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) m[a + 3 * b + 9 * c] += E * I[0][a] * I[1][b] * I[2][c];
+        for (int a = 0; a < 3; ++a) m[a + 3 * b + 9 * c] += EI[a + 3 * b] * I[2][c];
   }
 #pragma unroll
   for (int q = 0; q < 27; ++q) m[q] = warp_sum(m[q]);
