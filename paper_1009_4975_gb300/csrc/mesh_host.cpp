@@ -436,9 +436,18 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     auto morton6 = [](int i, int j, int k) {
       return (i & 1) | ((j & 1) << 1) | ((k & 1) << 2) | ((i & 2) << 2) | ((j & 2) << 3) | ((k & 2) << 4);
     };
-    int32_t lat[125];
-    uint8_t hax[125];
-    for (int64_t e = 0; e + 64 <= Ne;) {
+    // Whether element e starts a brick depends only on the elements and nodes around it (two
+    // aligned cubes of equal-level elements never overlap unless they coincide), so the starts
+    // are found in parallel over element chunks, each chunk's bricks in element order.
+    struct Found {
+      int64_t e;
+      int32_t lat[125];
+      uint8_t hax[125];
+      uint32_t fold[125];
+    };
+    auto check = [&](int64_t e, Found &f) -> bool {
+      int32_t *lat = f.lat;
+      uint8_t *hax = f.hax;
       const int32_t *l0 = &m.leaf[4 * e];
       const int32_t s = 1 << (L - l0[3]);
       bool ok = l0[0] % (4 * s) == 0 && l0[1] % (4 * s) == 0 && l0[2] % (4 * s) == 0;
@@ -448,56 +457,50 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
         const int32_t *lt = &m.leaf[4 * (e + t)];
         ok = lt[3] == l0[3] && lt[0] == l0[0] + s * i && lt[1] == l0[1] + s * j && lt[2] == l0[2] + s * k;
       }
-      if (ok) {
-        for (int c = 0; c < 5; ++c)
-          for (int b = 0; b < 5; ++b)
-            for (int a = 0; a < 5; ++a) {
-              const int ex = a < 4 ? a : 3, ey = b < 4 ? b : 3, ez = c < 4 ? c : 3;
-              const int q = (a - ex) + 2 * (b - ey) + 4 * (c - ez);
-              lat[a + 5 * b + 25 * c] = m.conn[8 * (e + morton6(ex, ey, ez)) + q];
-            }
-        for (int nd = 0; ok && nd < 125; ++nd) {
-          hax[nd] = 0;
-          const int32_t hi = m.hang_index[lat[nd]];
-          if (hi < 0) continue;
-          const int a = nd % 5, b = (nd / 5) % 5, c = nd / 25;
-          int nm = 0, dmask = 0;
-          int d[4][3];
-          for (int q = 0; q < 4; ++q) {
-            const int32_t mm = m.hang_master[4 * hi + q];
-            if (mm < 0) continue;
-            const int32_t *p = &m.node_xyz[3 * mm];
-            const int32_t rel[3] = {p[0] - l0[0] - s * a, p[1] - l0[1] - s * b, p[2] - l0[2] - s * c};
-            for (int ax = 0; ax < 3; ++ax) {
-              if (rel[ax] != 0 && rel[ax] != s && rel[ax] != -s) ok = false;
-              d[nm][ax] = rel[ax] / s;
-              if (rel[ax] != 0) dmask |= 1 << ax;
-            }
-            if (m.hang_index[mm] >= 0) ok = false;
-            ++nm;
+      if (!ok) return false;
+      for (int c = 0; c < 5; ++c)
+        for (int b = 0; b < 5; ++b)
+          for (int a = 0; a < 5; ++a) {
+            const int ex = a < 4 ? a : 3, ey = b < 4 ? b : 3, ez = c < 4 ? c : 3;
+            const int q = (a - ex) + 2 * (b - ey) + 4 * (c - ez);
+            lat[a + 5 * b + 25 * c] = m.conn[8 * (e + morton6(ex, ey, ez)) + q];
           }
-          const int naxes = (dmask & 1) + ((dmask >> 1) & 1) + ((dmask >> 2) & 1);
-          if (!ok || !((nm == 2 && naxes == 1) || (nm == 4 && naxes == 2))) { ok = false; break; }
-          // every master moves by exactly one lattice step along each interpolation axis, and
-          // the masters are distinct
-          for (int q = 0; q < nm && ok; ++q)
-            for (int ax = 0; ax < 3; ++ax)
-              if (((dmask >> ax) & 1) ? (d[q][ax] == 0) : (d[q][ax] != 0)) ok = false;
-          for (int q = 0; q < nm && ok; ++q)
-            for (int r = q + 1; r < nm; ++r)
-              if (d[q][0] == d[r][0] && d[q][1] == d[r][1] && d[q][2] == d[r][2]) ok = false;
-          for (int ax = 0; ax < 3 && ok; ++ax) {
-            const int pos = ax == 0 ? a : (ax == 1 ? b : c);
-            if (((dmask >> ax) & 1) && (pos == 0 || pos == 4)) ok = false;
+      for (int nd = 0; nd < 125; ++nd) {
+        hax[nd] = 0;
+        const int32_t hi = m.hang_index[lat[nd]];
+        if (hi < 0) continue;
+        const int a = nd % 5, b = (nd / 5) % 5, c = nd / 25;
+        int nm = 0, dmask = 0;
+        int d[4][3];
+        for (int q = 0; q < 4; ++q) {
+          const int32_t mm = m.hang_master[4 * hi + q];
+          if (mm < 0) continue;
+          const int32_t *p = &m.node_xyz[3 * mm];
+          const int32_t rel[3] = {p[0] - l0[0] - s * a, p[1] - l0[1] - s * b, p[2] - l0[2] - s * c};
+          for (int ax = 0; ax < 3; ++ax) {
+            if (rel[ax] != 0 && rel[ax] != s && rel[ax] != -s) return false;
+            d[nm][ax] = rel[ax] / s;
+            if (rel[ax] != 0) dmask |= 1 << ax;
           }
-          hax[nd] = (uint8_t)dmask;
+          if (m.hang_index[mm] >= 0) return false;
+          ++nm;
         }
+        const int naxes = (dmask & 1) + ((dmask >> 1) & 1) + ((dmask >> 2) & 1);
+        if (!((nm == 2 && naxes == 1) || (nm == 4 && naxes == 2))) return false;
+        // every master moves by exactly one lattice step along each interpolation axis, and
+        // the masters are distinct
+        for (int q = 0; q < nm; ++q)
+          for (int ax = 0; ax < 3; ++ax)
+            if (((dmask >> ax) & 1) ? (d[q][ax] == 0) : (d[q][ax] != 0)) return false;
+        for (int q = 0; q < nm; ++q)
+          for (int r = q + 1; r < nm; ++r)
+            if (d[q][0] == d[r][0] && d[q][1] == d[r][1] && d[q][2] == d[r][2]) return false;
+        for (int ax = 0; ax < 3; ++ax) {
+          const int pos = ax == 0 ? a : (ax == 1 ? b : c);
+          if (((dmask >> ax) & 1) && (pos == 0 || pos == 4)) return false;
+        }
+        hax[nd] = (uint8_t)dmask;
       }
-      if (!ok) {
-        ++e;
-        continue;
-      }
-      m.brick_e0.push_back((int32_t)e);
       // fold masks: which lattice neighbours of a regular node are hanging nodes it is a master
       // of -- bits 2 ax + (step > 0): the neighbour one step along axis ax, edge-hanging along
       // ax; bits 6 + 4 pl + 2 (step1 > 0) + (step0 > 0): the diagonal neighbour in coordinate
@@ -522,18 +525,34 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
               }
           }
         }
-        m.brick_fold.push_back(fm);
+        f.fold[nd] = fm;
       }
-      for (int nd = 0; nd < 125; ++nd) {
-        uint32_t g = (uint32_t)lat[nd];
-        if (m.nflag[lat[nd]] & 1) g |= 0x80000000u;
-        m.brick_node.push_back((int32_t)g);
-        m.brick_hax.push_back(hax[nd]);
-        if (!hax[nd]) nblocks_of[lat[nd]]++;
+      return true;
+    };
+    const int64_t ncand = Ne >= 64 ? Ne - 63 : 0;
+    const int nt = host_threads(ncand);
+    std::vector<std::vector<Found>> found(nt);
+    chunked(nt, (size_t)ncand, [&](int t, size_t lo, size_t hi) {
+      Found f;
+      for (size_t e = lo; e < hi; ++e)
+        if (check((int64_t)e, f)) {
+          f.e = (int64_t)e;
+          found[t].push_back(f);
+        }
+    });
+    for (const auto &fv : found)
+      for (const Found &f : fv) {
+        m.brick_e0.push_back((int32_t)f.e);
+        m.brick_fold.insert(m.brick_fold.end(), f.fold, f.fold + 125);
+        for (int nd = 0; nd < 125; ++nd) {
+          uint32_t g = (uint32_t)f.lat[nd];
+          if (m.nflag[f.lat[nd]] & 1) g |= 0x80000000u;
+          m.brick_node.push_back((int32_t)g);
+          m.brick_hax.push_back(f.hax[nd]);
+          if (!f.hax[nd]) nblocks_of[f.lat[nd]]++;
+        }
+        std::memset(&in_brick[f.e], 1, 64);
       }
-      std::memset(&in_brick[e], 1, 64);
-      e += 64;
-    }
     m.nbrick = (int32_t)m.brick_e0.size();
   }
   // blocks: consecutive runs of the non-brick elements in Morton order (gen), at most kBlockElems
