@@ -18,7 +18,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
-#include <map>
+#include <unordered_map>
 #include <numeric>
 #include <thread>
 
@@ -223,7 +223,46 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
         ckey[8 * e + k] = morton3(l[0] + s * (k & 1), l[1] + s * ((k >> 1) & 1), l[2] + s * ((k >> 2) & 1));
     }
   });
-  {
+  uint64_t kmax = 0;
+  for (uint64_t k : ckey) kmax = std::max(kmax, k);
+  const uint64_t nword = kmax / 64 + 1;
+  if (nword <= std::max<uint64_t>(1u << 16, (uint64_t)(8 * Ne))) {
+    // a bitmap of the Morton key space: a node's id is the number of distinct corner keys below
+    // its own, the same numbering as sorting and deduplicating the keys
+    std::vector<uint64_t> bm(nword, 0);
+    chunked(host_threads(8 * Ne), (size_t)(8 * Ne), [&](int, size_t lo, size_t hi) {
+      for (size_t i = lo; i < hi; ++i) {
+        uint64_t *w = &bm[ckey[i] >> 6];
+        const uint64_t b = 1ull << (ckey[i] & 63);
+        if (!(__atomic_load_n(w, __ATOMIC_RELAXED) & b)) __atomic_fetch_or(w, b, __ATOMIC_RELAXED);
+      }
+    });
+    std::vector<int64_t> below(nword);   // set bits in the words before w
+    const int nt = host_threads(nword * 8);
+    std::vector<int64_t> part(nt + 1, 0);
+    chunked(nt, nword, [&](int t, size_t lo, size_t hi) {
+      int64_t c = 0;
+      for (size_t w = lo; w < hi; ++w) c += __builtin_popcountll(bm[w]);
+      part[t + 1] = c;
+    });
+    for (int t = 0; t < nt; ++t) part[t + 1] += part[t];
+    m.Nn = part[nt];
+    m.node_key.resize(m.Nn);
+    chunked(nt, nword, [&](int t, size_t lo, size_t hi) {
+      int64_t c = part[t];
+      for (size_t w = lo; w < hi; ++w) {
+        below[w] = c;
+        for (uint64_t v = bm[w]; v; v &= v - 1) m.node_key[c++] = 64 * (uint64_t)w + __builtin_ctzll(v);
+      }
+    });
+    m.conn.resize(8 * Ne);
+    chunked(host_threads(8 * Ne), (size_t)(8 * Ne), [&](int, size_t lo, size_t hi) {
+      for (size_t i = lo; i < hi; ++i) {
+        const uint64_t w = ckey[i] >> 6, low = (1ull << (ckey[i] & 63)) - 1;
+        m.conn[i] = (int32_t)(below[w] + __builtin_popcountll(bm[w] & low));
+      }
+    });
+  } else {
     std::vector<uint64_t> sk;
     const std::vector<int64_t> ord = radix_order(ckey, &sk);
     std::vector<int32_t> nid(8 * Ne);
@@ -294,8 +333,10 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     struct Found { int32_t n; std::array<int32_t, 4> ms; };
     const int nt = host_threads(Ne);
     std::vector<std::vector<Found>> found(nt);
+    // (each thread fills a vector of its own and hands it over at the end: vectors side by side in
+    // one array would share the cache lines of their end pointers)
     chunked(nt, (size_t)Ne, [&](int t, size_t lo, size_t hi) {
-      std::vector<Found> &out = found[t];
+      std::vector<Found> out;
       for (size_t e = lo; e < hi; ++e) {
         const int32_t *l = &m.leaf[4 * e];
         const int32_t s = 1 << (L - l[3]);
@@ -319,6 +360,7 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
         for (auto &ed : edges) probe(ed, 2);
         for (auto &fc : faces) probe(fc, 4);
       }
+      found[t].swap(out);
     });
     for (const auto &fv : found)
       for (const Found &f : fv) {
@@ -533,12 +575,14 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     const int nt = host_threads(ncand);
     std::vector<std::vector<Found>> found(nt);
     chunked(nt, (size_t)ncand, [&](int t, size_t lo, size_t hi) {
+      std::vector<Found> out;
       Found f;
       for (size_t e = lo; e < hi; ++e)
         if (check((int64_t)e, f)) {
           f.e = (int64_t)e;
-          found[t].push_back(f);
+          out.push_back(f);
         }
+      found[t].swap(out);
     });
     for (const auto &fv : found)
       for (const Found &f : fv) {
@@ -811,7 +855,17 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
 
   // ---- 8. Jacobi diagonal coefficients: d_{m,c} = sum_e c_e q_{e,m,c}
   {
-    std::map<std::array<int64_t, 3>, int> tab_index;
+    // coefficient triples by their bit patterns; the maps only number them in order of first
+    // appearance, so their iteration order never matters
+    struct TripleHash {
+      size_t operator()(const std::array<int64_t, 3> &k) const {
+        uint64_t h = 0x9E3779B97F4A7C15ull;
+        for (int c = 0; c < 3; ++c) h = (h ^ (uint64_t)k[c]) * 0xFF51AFD7ED558CCDull;
+        return (size_t)(h ^ (h >> 29));
+      }
+    };
+    using TripleMap = std::unordered_map<std::array<int64_t, 3>, int, TripleHash>;
+    TripleMap tab_index;
     {
       // entry 0: a corner that is its own node in an element without hanging corners
       const double q = m.K0[0];
@@ -828,13 +882,17 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     std::vector<std::vector<int32_t>> cx_node(nt), cx_lq(nt);
     std::vector<std::vector<std::array<double, 3>>> cx_tab(nt);
     std::vector<int32_t> ex_end(Ne, 0);   // per element: end of its entries within its chunk's list
+    std::vector<uint8_t> plain(Ne);       // per element: no hanging corners
     chunked(nt, (size_t)Ne, [&](int t, size_t lo, size_t hi) {
-      std::map<std::array<int64_t, 3>, int> local;
+      TripleMap local;
+      std::vector<int32_t> my_node, my_lq;   // handed over at the end (no shared cache lines)
+      std::vector<std::array<double, 3>> my_tab;
       for (size_t e = lo; e < hi; ++e) {
-        bool plain = true;
-        for (int k = 0; k < 8; ++k) plain &= m.hang_index[m.conn[8 * e + k]] < 0;
-        if (plain) {
-          ex_end[e] = (int32_t)cx_node[t].size();
+        bool pl = true;
+        for (int k = 0; k < 8; ++k) pl &= m.hang_index[m.conn[8 * e + k]] < 0;
+        plain[e] = pl;
+        if (pl) {
+          ex_end[e] = (int32_t)my_node.size();
           continue;
         }
         // corner expansion: (node, weight) pairs
@@ -886,17 +944,20 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
           auto it = local.find(kq);
           int li;
           if (it == local.end()) {
-            li = (int)cx_tab[t].size();
+            li = (int)my_tab.size();
             local[kq] = li;
-            cx_tab[t].push_back(q);
+            my_tab.push_back(q);
           } else {
             li = it->second;
           }
-          cx_node[t].push_back(uniq[u]);
-          cx_lq[t].push_back(li);
+          my_node.push_back(uniq[u]);
+          my_lq.push_back(li);
         }
-        ex_end[e] = (int32_t)cx_node[t].size();
+        ex_end[e] = (int32_t)my_node.size();
       }
+      cx_node[t].swap(my_node);
+      cx_lq[t].swap(my_lq);
+      cx_tab[t].swap(my_tab);
     });
     std::vector<std::vector<uint16_t>> l2g(nt);
     for (int t = 0; t < nt; ++t)
@@ -915,64 +976,53 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
         }
         l2g[t].push_back((uint16_t)qi);
       }
-    // the entries in element order, and the count of every node
-    std::vector<int32_t> ex_node;
-    std::vector<uint16_t> ex_q;
-    std::vector<int64_t> chunk_base(nt + 1, 0);
-    for (int t = 0; t < nt; ++t) {
-      chunk_base[t + 1] = chunk_base[t] + (int64_t)cx_node[t].size();
-      for (size_t i = 0; i < cx_node[t].size(); ++i) {
-        ex_node.push_back(cx_node[t][i]);
-        ex_q.push_back(l2g[t][cx_lq[t][i]]);
-      }
-    }
-    for (int t = 0; t < nt; ++t) {   // ex_end relative to the whole list
-      const size_t lo = (size_t)Ne * t / nt, hi = (size_t)Ne * (t + 1) / nt;
-      for (size_t e = lo; e < hi; ++e) ex_end[e] += (int32_t)chunk_base[t];
-    }
-    std::vector<int32_t> cnt(Nn + 1, 0);
-    {
-      int32_t x0 = 0;
-      for (int64_t e = 0; e < Ne; ++e) {
-        if (ex_end[e] == x0) {
-          bool plain = true;
-          for (int k = 0; k < 8; ++k) plain &= m.hang_index[m.conn[8 * e + k]] < 0;
-          if (plain) {
-            for (int k = 0; k < 8; ++k) cnt[m.conn[8 * e + k] + 1]++;
-            continue;
-          }
-        }
-        for (int32_t i = x0; i < ex_end[e]; ++i) cnt[ex_node[i] + 1]++;
-        x0 = ex_end[e];
-      }
-    }
-    // pass 2: fill the node-major CSR in element order
-    m.dg_ptr.assign(Nn + 1, 0);
-    for (int64_t n = 0; n < Nn; ++n) m.dg_ptr[n + 1] = m.dg_ptr[n] + cnt[n + 1];
-    m.dg_elem.resize(m.dg_ptr[Nn]);
-    m.dg_q.resize(m.dg_ptr[Nn]);
-    std::vector<int32_t> fill(m.dg_ptr.begin(), m.dg_ptr.end() - 1);
-    int32_t x0 = 0;
-    for (int64_t e = 0; e < Ne; ++e) {
-      if (ex_end[e] == x0) {          // no hanging corners: the 8 corners with the plain triple
-        bool plain = true;
-        for (int k = 0; k < 8; ++k) plain &= m.hang_index[m.conn[8 * e + k]] < 0;
-        if (plain) {
-          for (int k = 0; k < 8; ++k) {
-            const int32_t n = m.conn[8 * e + k];
-            m.dg_elem[fill[n]] = (int32_t)e;
-            m.dg_q[fill[n]++] = 0;
-          }
+    // the count of every node per chunk, then each chunk's write position inside every node's
+    // list (after the earlier chunks' entries), so the chunks fill the node-major CSR in
+    // parallel in element order
+    std::vector<int32_t> ccnt((size_t)nt * Nn, 0);
+    auto chunk_entries = [&](int t, size_t lo, size_t hi, auto &&emit) {
+      int32_t x0 = 0;   // ex_end is relative to the chunk's own list
+      for (size_t e = lo; e < hi; ++e) {
+        if (plain[e]) {
+          for (int k = 0; k < 8; ++k) emit(m.conn[8 * e + k], (int32_t)e, (uint16_t)0);
           continue;
         }
+        for (int32_t i = x0; i < ex_end[e]; ++i) emit(cx_node[t][i], (int32_t)e, l2g[t][cx_lq[t][i]]);
+        x0 = ex_end[e];
       }
-      for (int32_t i = x0; i < ex_end[e]; ++i) {
-        const int32_t n = ex_node[i];
-        m.dg_elem[fill[n]] = (int32_t)e;
-        m.dg_q[fill[n]++] = ex_q[i];
+    };
+    chunked(nt, (size_t)Ne, [&](int t, size_t lo, size_t hi) {
+      int32_t *c = &ccnt[(size_t)t * Nn];
+      chunk_entries(t, lo, hi, [&](int32_t n, int32_t, uint16_t) { c[n]++; });
+    });
+    m.dg_ptr.assign(Nn + 1, 0);
+    chunked(host_threads(Nn), (size_t)Nn, [&](int, size_t lo, size_t hi) {
+      for (size_t n = lo; n < hi; ++n) {
+        int32_t s = 0;
+        for (int t = 0; t < nt; ++t) s += ccnt[(size_t)t * Nn + n];
+        m.dg_ptr[n + 1] = s;
       }
-      x0 = ex_end[e];
-    }
+    });
+    for (int64_t n = 0; n < Nn; ++n) m.dg_ptr[n + 1] += m.dg_ptr[n];
+    chunked(host_threads(Nn), (size_t)Nn, [&](int, size_t lo, size_t hi) {
+      for (size_t n = lo; n < hi; ++n) {
+        int32_t s = m.dg_ptr[n];
+        for (int t = 0; t < nt; ++t) {
+          const int32_t v = ccnt[(size_t)t * Nn + n];
+          ccnt[(size_t)t * Nn + n] = s;
+          s += v;
+        }
+      }
+    });
+    m.dg_elem.resize(m.dg_ptr[Nn]);
+    m.dg_q.resize(m.dg_ptr[Nn]);
+    chunked(nt, (size_t)Ne, [&](int t, size_t lo, size_t hi) {
+      int32_t *f = &ccnt[(size_t)t * Nn];
+      chunk_entries(t, lo, hi, [&](int32_t n, int32_t e, uint16_t q) {
+        m.dg_elem[f[n]] = e;
+        m.dg_q[f[n]++] = q;
+      });
+    });
   }
   return "";
 }

@@ -67,6 +67,34 @@ def test_tables_bit_exact_against_oracle(tm, make):
     assert 0 < info["max_local"] <= 1024
 
 
+def _morton(x, y, z):
+    k = 0
+    for b in range(21):
+        k |= ((x >> b) & 1) << (3 * b) | ((y >> b) & 1) << (3 * b + 1) | ((z >> b) & 1) << (3 * b + 2)
+    return k
+
+
+def test_tables_bit_exact_on_a_sparse_key_space(tm):
+    """A long thin domain (1 x 1 x 160 base cells, two levels of refinement with hanging nodes):
+    its corner Morton keys span far more 64-bit words than 8 per element, so the library numbers
+    the nodes by sorting the keys instead of ranking them in a bitmap of the key space.  Both give
+    the sorted distinct keys; the tables still equal the oracle's."""
+    dom = W.Domain(1, 1, 160, 2, 1.0)
+    rng = np.random.default_rng(5)
+    lv = W.uniform_leaves(dom)
+    lv = W.refine(dom, lv, rng.random(len(lv)) < 0.3)
+    lv = W.balance(dom, W.refine(dom, lv, (lv[:, 3] == 1) & (rng.random(len(lv)) < 0.3)))
+    fx, fy, fz = dom.fine_shape
+    assert _morton(fx, fy, fz) // 64 + 1 > max(1 << 16, 8 * len(lv))
+    info, t = tm.tm_tables_build(dom.nx, dom.ny, dom.nz, dom.L, dom.h0, lv)
+    m = M.build_mesh(dom.nx, dom.ny, dom.nz, dom.L, dom.h0, lv)
+    hn = m.hanging_ids()
+    assert info["Nn"] == m.Nn and info["n_hanging"] == hn.size > 0
+    assert np.array_equal(t["node_xyz"], m.nodes)
+    assert np.array_equal(t["conn"], m.conn)
+    assert np.array_equal(t["hang_node"], hn)
+
+
 def test_tables_other_dirichlet_faces(tm):
     w = W.config1()
     d = w.dom
