@@ -1148,92 +1148,146 @@ namespace amr {
 std::string adapt_leaves(const HostMesh &m, const int8_t *mark, const double *rho, std::vector<int32_t> &leaves,
                          std::vector<double> &rho_out) {
   const int L = m.L;
+  const int64_t Ne = m.Ne;
   const int64_t fx = (int64_t)m.nx << L, fy = (int64_t)m.ny << L, fz = (int64_t)m.nz << L;
-  leaves.clear();
-  rho_out.clear();
-  for (int64_t e = 0; e < m.Ne; ++e) {
+  // Every element's check and output depend on it and its family alone, so chunks of elements are
+  // checked and counted in parallel, then write their outputs at the offsets of the earlier
+  // chunks: the element order, and the first error in element order, of a sequential pass.
+  auto check = [&](int64_t e) -> const char * {
     const int32_t *l = &m.leaf[4 * e];
     const int32_t s = 1 << (L - l[3]);
-    if (mark[e] == 1) {
-      if (l[3] >= L) return "refinement mark on a finest-level element";
-      const int32_t h = s / 2;
-      for (int k = 0; k < 8; ++k) {
-        leaves.insert(leaves.end(), {l[0] + h * (k & 1), l[1] + h * ((k >> 1) & 1), l[2] + h * ((k >> 2) & 1), l[3] + 1});
-        rho_out.push_back(rho[e]);
-      }
-    } else if (mark[e] == -1) {
-      if (l[3] == 0) return "derefinement mark on a level-0 element";
-      const int32_t ps = 2 * s;
-      const int k0 = (l[0] % ps ? 1 : 0) + (l[1] % ps ? 2 : 0) + (l[2] % ps ? 4 : 0);
-      if (k0) {   // merged with the family's first sibling, which must carry the same mark
-        const int32_t *f = e >= k0 ? &m.leaf[4 * (e - k0)] : nullptr;
-        if (!f || f[3] != l[3] || f[0] != l[0] - s * (k0 & 1) || f[1] != l[1] - s * ((k0 >> 1) & 1) ||
-            f[2] != l[2] - s * ((k0 >> 2) & 1) || mark[e - k0] != -1)
-          return "family marked for derefinement is not 8 sibling leaves";
-        continue;
-      }
-      if (e + 8 > m.Ne) return "incomplete family marked for derefinement";
-      double sum = 0.0;
-      for (int k = 0; k < 8; ++k) {
-        const int32_t *q = &m.leaf[4 * (e + k)];
-        if (mark[e + k] != -1 || q[3] != l[3] || q[0] != l[0] + s * (k & 1) || q[1] != l[1] + s * ((k >> 1) & 1) ||
-            q[2] != l[2] + s * ((k >> 2) & 1))
-          return "family marked for derefinement is not 8 sibling leaves";
-        sum += rho[e + k];
-      }
-      leaves.insert(leaves.end(), {l[0], l[1], l[2], l[3] - 1});
-      rho_out.push_back(sum / 8.0);
-    } else {
-      leaves.insert(leaves.end(), {l[0], l[1], l[2], l[3]});
-      rho_out.push_back(rho[e]);
+    if (mark[e] == 1) return l[3] >= L ? "refinement mark on a finest-level element" : nullptr;
+    if (mark[e] != -1) return nullptr;
+    if (l[3] == 0) return "derefinement mark on a level-0 element";
+    const int32_t ps = 2 * s;
+    const int k0 = (l[0] % ps ? 1 : 0) + (l[1] % ps ? 2 : 0) + (l[2] % ps ? 4 : 0);
+    if (k0) {   // merged with the family's first sibling, which must carry the same mark
+      const int32_t *f = e >= k0 ? &m.leaf[4 * (e - k0)] : nullptr;
+      if (!f || f[3] != l[3] || f[0] != l[0] - s * (k0 & 1) || f[1] != l[1] - s * ((k0 >> 1) & 1) ||
+          f[2] != l[2] - s * ((k0 >> 2) & 1) || mark[e - k0] != -1)
+        return "family marked for derefinement is not 8 sibling leaves";
+      return nullptr;
     }
-  }
-  // 2:1 balance by refinement
+    if (e + 8 > Ne) return "incomplete family marked for derefinement";
+    for (int k = 0; k < 8; ++k) {
+      const int32_t *q = &m.leaf[4 * (e + k)];
+      if (mark[e + k] != -1 || q[3] != l[3] || q[0] != l[0] + s * (k & 1) || q[1] != l[1] + s * ((k >> 1) & 1) ||
+          q[2] != l[2] + s * ((k >> 2) & 1))
+        return "family marked for derefinement is not 8 sibling leaves";
+    }
+    return nullptr;
+  };
+  auto count = [&](int64_t e) -> int64_t {
+    if (mark[e] == 1) return 8;
+    if (mark[e] == -1) {
+      const int32_t *l = &m.leaf[4 * e];
+      const int32_t ps = 2 << (L - l[3]);
+      return l[0] % ps || l[1] % ps || l[2] % ps ? 0 : 1;
+    }
+    return 1;
+  };
+  const int nt = host_threads(Ne);
+  std::vector<int64_t> off(nt + 1, 0);
+  std::vector<const char *> err(nt, nullptr);
+  chunked(nt, (size_t)Ne, [&](int t, size_t lo, size_t hi) {
+    int64_t c = 0;
+    for (size_t e = lo; e < hi; ++e) {
+      if ((err[t] = check((int64_t)e))) return;
+      c += count((int64_t)e);
+    }
+    off[t + 1] = c;
+  });
+  for (int t = 0; t < nt; ++t)
+    if (err[t]) return err[t];
+  for (int t = 0; t < nt; ++t) off[t + 1] += off[t];
+  leaves.assign(4 * (size_t)off[nt], 0);
+  rho_out.assign((size_t)off[nt], 0.0);
+  chunked(nt, (size_t)Ne, [&](int t, size_t lo, size_t hi) {
+    int64_t o = off[t];
+    for (size_t e = lo; e < hi; ++e) {
+      const int32_t *l = &m.leaf[4 * e];
+      const int32_t s = 1 << (L - l[3]);
+      if (mark[e] == 1) {
+        const int32_t h = s / 2;
+        for (int k = 0; k < 8; ++k, ++o) {
+          int32_t *q = &leaves[4 * o];
+          q[0] = l[0] + h * (k & 1); q[1] = l[1] + h * ((k >> 1) & 1); q[2] = l[2] + h * ((k >> 2) & 1); q[3] = l[3] + 1;
+          rho_out[o] = rho[e];
+        }
+      } else if (mark[e] == -1) {
+        if (!count((int64_t)e)) continue;
+        double sum = 0.0;
+        for (int k = 0; k < 8; ++k) sum += rho[e + k];
+        int32_t *q = &leaves[4 * o];
+        q[0] = l[0]; q[1] = l[1]; q[2] = l[2]; q[3] = l[3] - 1;
+        rho_out[o++] = sum / 8.0;
+      } else {
+        std::memcpy(&leaves[4 * o], l, 16);
+        rho_out[o++] = rho[e];
+      }
+    }
+  });
+  // 2:1 balance by refinement: paint every leaf's level into the finest cells (leaves are
+  // disjoint, so the threads write disjoint cells), then split every leaf that touches -- across
+  // a face, an edge or a corner -- a leaf more than one level finer
   std::vector<uint8_t> lv((size_t)(fx * fy * fz));
   for (int pass = 0; pass < 64; ++pass) {
     const int64_t n = (int64_t)rho_out.size();
-    for (int64_t i = 0; i < n; ++i) {
-      const int32_t *l = &leaves[4 * i];
-      const int32_t s = 1 << (L - l[3]);
-      for (int z = 0; z < s; ++z)
-        for (int y = 0; y < s; ++y)
-          std::memset(&lv[((size_t)(l[2] + z) * fy + (l[1] + y)) * fx + l[0]], l[3], s);
-    }
-    std::vector<char> need(n, 0);
-    bool any = false;
-    for (int64_t i = 0; i < n; ++i) {
-      const int32_t *l = &leaves[4 * i];
-      const int32_t s = 1 << (L - l[3]);
-      int mx = 0;
-      for (int64_t z = std::max<int64_t>(l[2] - 1, 0); z < std::min<int64_t>(l[2] + s + 1, fz); ++z)
-        for (int64_t y = std::max<int64_t>(l[1] - 1, 0); y < std::min<int64_t>(l[1] + s + 1, fy); ++y)
-          for (int64_t x = std::max<int64_t>(l[0] - 1, 0); x < std::min<int64_t>(l[0] + s + 1, fx); ++x) {
-            const bool inside = x >= l[0] && x < l[0] + s && y >= l[1] && y < l[1] + s && z >= l[2] && z < l[2] + s;
-            if (!inside) mx = std::max<int>(mx, lv[((size_t)z * fy + y) * fx + x]);
+    const int nb = host_threads(n);
+    chunked(nb, (size_t)n, [&](int, size_t lo, size_t hi) {
+      for (size_t i = lo; i < hi; ++i) {
+        const int32_t *l = &leaves[4 * i];
+        const int32_t s = 1 << (L - l[3]);
+        for (int z = 0; z < s; ++z)
+          for (int y = 0; y < s; ++y)
+            std::memset(&lv[((size_t)(l[2] + z) * fy + (l[1] + y)) * fx + l[0]], l[3], s);
+      }
+    });
+    std::vector<uint8_t> need(n, 0);
+    std::vector<int64_t> noff(nb + 1, 0);
+    chunked(nb, (size_t)n, [&](int t, size_t lo, size_t hi) {
+      int64_t c = 0;
+      for (size_t i = lo; i < hi; ++i) {
+        const int32_t *l = &leaves[4 * i];
+        const int64_t s = (int64_t)1 << (L - l[3]);
+        const int64_t x0 = std::max<int64_t>(l[0] - 1, 0), x1 = std::min<int64_t>(l[0] + s + 1, fx);
+        int mx = 0;
+        for (int64_t z = std::max<int64_t>(l[2] - 1, 0); z < std::min<int64_t>(l[2] + s + 1, fz); ++z)
+          for (int64_t y = std::max<int64_t>(l[1] - 1, 0); y < std::min<int64_t>(l[1] + s + 1, fy); ++y) {
+            const uint8_t *row = &lv[((size_t)z * fy + y) * fx];
+            if (z >= l[2] && z < l[2] + s && y >= l[1] && y < l[1] + s) {   // the leaf's own rows: both ends
+              if (l[0] - 1 >= 0) mx = std::max<int>(mx, row[l[0] - 1]);
+              if (l[0] + s < fx) mx = std::max<int>(mx, row[l[0] + s]);
+            } else {
+              for (int64_t x = x0; x < x1; ++x) mx = std::max<int>(mx, row[x]);
+            }
           }
-      if (mx > l[3] + 1) {
-        need[i] = 1;
-        any = true;
+        need[i] = mx > l[3] + 1;
+        c += need[i] ? 8 : 1;
       }
-    }
-    if (!any) return "";
-    std::vector<int32_t> nl;
-    std::vector<double> nr;
-    nl.reserve(leaves.size());
-    nr.reserve(rho_out.size());
-    for (int64_t i = 0; i < n; ++i) {
-      const int32_t *l = &leaves[4 * i];
-      if (!need[i]) {
-        nl.insert(nl.end(), l, l + 4);
-        nr.push_back(rho_out[i]);
-        continue;
+      noff[t + 1] = c;
+    });
+    for (int t = 0; t < nb; ++t) noff[t + 1] += noff[t];
+    if (noff[nb] == n) return "";
+    std::vector<int32_t> nl(4 * (size_t)noff[nb]);
+    std::vector<double> nr((size_t)noff[nb]);
+    chunked(nb, (size_t)n, [&](int t, size_t lo, size_t hi) {
+      int64_t o = noff[t];
+      for (size_t i = lo; i < hi; ++i) {
+        const int32_t *l = &leaves[4 * i];
+        if (!need[i]) {
+          std::memcpy(&nl[4 * o], l, 16);
+          nr[o++] = rho_out[i];
+          continue;
+        }
+        const int32_t h = (1 << (L - l[3])) / 2;
+        for (int k = 0; k < 8; ++k, ++o) {
+          int32_t *q = &nl[4 * o];
+          q[0] = l[0] + h * (k & 1); q[1] = l[1] + h * ((k >> 1) & 1); q[2] = l[2] + h * ((k >> 2) & 1); q[3] = l[3] + 1;
+          nr[o] = rho_out[i];
+        }
       }
-      const int32_t h = (1 << (L - l[3])) / 2;
-      for (int k = 0; k < 8; ++k) {
-        nl.insert(nl.end(), {l[0] + h * (k & 1), l[1] + h * ((k >> 1) & 1), l[2] + h * ((k >> 2) & 1), l[3] + 1});
-        nr.push_back(rho_out[i]);
-      }
-    }
+    });
     leaves.swap(nl);
     rho_out.swap(nr);
   }

@@ -86,3 +86,28 @@ def test_transfer_matches_the_oracle(tm):
     np.testing.assert_allclose(got, want, rtol=1e-14, atol=1e-14 * np.abs(uf).max())
     with pytest.raises(tm.TmError):
         tm.tm_tables_transfer(d.nx, d.ny, d.nz, d.L, d.h0, m.leaves, uf, [[-1, 0, 0]])
+
+
+def test_adapt_on_several_host_threads(tm):
+    """A mesh of over 65,536 leaves, which the library splits into element chunks on several host
+    threads: refinement, derefinement and the 2:1 balancing still equal the oracle bit for bit,
+    and a malformed mark in the last chunk alone is still rejected."""
+    w = W.small_truss(seed=2, base=(24, 12, 12), L=2)
+    d = w.dom
+    m = M.build_mesh(d.nx, d.ny, d.nz, d.L, d.h0, w.leaves)
+    assert m.Ne > 65536
+    phi = W.truss_sdf(m.centres, 9, r0=0.09)
+    rho = np.clip(0.5 - phi / (2.0 * d.h_min), 1e-3, 1.0)
+    marks = A.final_marks(m, rho, 0.5, 1.6 * d.h_min)
+    rng = np.random.default_rng(3)
+    marks = np.where((marks == 0) & (m.leaves[:, 3] < d.L) & (rng.random(m.Ne) < 0.02), 1, marks).astype(np.int8)
+    assert (marks == 1).sum() > 100 and (marks == -1).sum() > 1000
+    want_l, want_r = A.adapt(m, marks, rho)
+    got_l, got_r = tm.tm_tables_adapt(d.nx, d.ny, d.nz, d.L, d.h0, m.leaves, marks, rho)
+    np.testing.assert_array_equal(got_l, want_l)
+    assert got_r.tobytes() == want_r.tobytes()
+    bad = marks.copy()
+    e = np.nonzero(m.leaves[:, 3] == d.L)[0][-1]         # refine past the finest level, near the end
+    bad[e] = 1
+    with pytest.raises(tm.TmError):
+        tm.tm_tables_adapt(d.nx, d.ny, d.nz, d.L, d.h0, m.leaves, bad, rho)
