@@ -293,31 +293,43 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     }
   });
 
-  // ---- 3. balance via a dense owner map of the finest cells
+  // ---- 3. balance via a dense owner map of the finest cells (the leaves are disjoint, so the
+  // threads paint disjoint cells)
   {
     std::vector<int32_t> &owner = m.cellmap;
     owner.assign((size_t)(fx * fy * fz), 0);
-    for (int64_t e = 0; e < Ne; ++e) {
-      const int32_t *l = &m.leaf[4 * e];
-      const int32_t s = 1 << (L - l[3]);
-      for (int z = 0; z < s; ++z)
-        for (int y = 0; y < s; ++y) {
-          int32_t *row = &owner[((size_t)(l[2] + z) * fy + (l[1] + y)) * fx + l[0]];
-          for (int x = 0; x < s; ++x) row[x] = (int32_t)e;
-        }
-    }
-    for (int64_t n = 0; n < Nn; ++n) {
-      const int32_t px = m.node_xyz[3 * n], py = m.node_xyz[3 * n + 1], pz = m.node_xyz[3 * n + 2];
-      int lo = 1 << 30, hi = -1;
-      for (int c = 0; c < 8; ++c) {
-        const int64_t cx = px - 1 + (c & 1), cy = py - 1 + ((c >> 1) & 1), cz = pz - 1 + ((c >> 2) & 1);
-        if (cx < 0 || cy < 0 || cz < 0 || cx >= fx || cy >= fy || cz >= fz) continue;
-        const int lv = m.leaf[4 * owner[((size_t)cz * fy + cy) * fx + cx] + 3];
-        lo = std::min(lo, lv);
-        hi = std::max(hi, lv);
+    chunked(host_threads(Ne), (size_t)Ne, [&](int, size_t lo, size_t hi) {
+      for (size_t e = lo; e < hi; ++e) {
+        const int32_t *l = &m.leaf[4 * e];
+        const int32_t s = 1 << (L - l[3]);
+        for (int z = 0; z < s; ++z)
+          for (int y = 0; y < s; ++y) {
+            int32_t *row = &owner[((size_t)(l[2] + z) * fy + (l[1] + y)) * fx + l[0]];
+            for (int x = 0; x < s; ++x) row[x] = (int32_t)e;
+          }
       }
-      if (hi - lo > 1) return "mesh is not 2:1 balanced";
-    }
+    });
+    const int nt = host_threads(Nn);
+    std::vector<uint8_t> unbalanced(nt, 0);
+    chunked(nt, (size_t)Nn, [&](int t, size_t lo, size_t hi) {
+      for (size_t n = lo; n < hi; ++n) {
+        const int32_t px = m.node_xyz[3 * n], py = m.node_xyz[3 * n + 1], pz = m.node_xyz[3 * n + 2];
+        int lv_lo = 1 << 30, lv_hi = -1;
+        for (int c = 0; c < 8; ++c) {
+          const int64_t cx = px - 1 + (c & 1), cy = py - 1 + ((c >> 1) & 1), cz = pz - 1 + ((c >> 2) & 1);
+          if (cx < 0 || cy < 0 || cz < 0 || cx >= fx || cy >= fy || cz >= fz) continue;
+          const int lv = m.leaf[4 * owner[((size_t)cz * fy + cy) * fx + cx] + 3];
+          lv_lo = std::min(lv_lo, lv);
+          lv_hi = std::max(lv_hi, lv);
+        }
+        if (lv_hi - lv_lo > 1) {
+          unbalanced[t] = 1;
+          return;
+        }
+      }
+    });
+    for (uint8_t u : unbalanced)
+      if (u) return "mesh is not 2:1 balanced";
   }
 
   // ---- 4. hanging nodes: edge midpoints and face centres that are nodes
@@ -638,30 +650,30 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
   }
   const int32_t nblk = (int32_t)blks.size();
   m.nblk = nblk;
+  // Every block's lists depend on its own elements and on nblocks_of alone, so contiguous ranges of
+  // blocks are built on host threads, each with a node -> local id map of its own (capped so the
+  // maps stay within 512 MB), and concatenated in block order with the running offsets of a
+  // sequential pass.
+  const int nbt = std::max(1, std::min(host_threads((size_t)nblk * 4096), (int)((int64_t(1) << 27) / std::max<int64_t>(Nn, 1))));
   std::vector<std::vector<int32_t>> bl(nblk);   // regular nodes per block, ascending
-  {
-    std::vector<int32_t> seen(Nn, -1);          // block that last listed the node
-    for (int32_t b = 0; b < nblk; ++b) {
-      std::vector<int32_t> &v = bl[b];
-      auto add = [&](int32_t n) {
-        if (seen[n] != b) {
-          seen[n] = b;
-          v.push_back(n);
-        }
-      };
+  chunked(nbt, (size_t)nblk, [&](int, size_t lo, size_t hi) {
+    for (size_t b = lo; b < hi; ++b) {
+      std::vector<int32_t> v;
       for (int64_t u = blks[b].e0; u < blks[b].e1; ++u)
         for (int k = 0; k < 8; ++k) {
           const int32_t n = m.conn[8 * (int64_t)gen[u] + k];
           const int32_t h = m.hang_index[n];
-          if (h < 0) add(n);
+          if (h < 0) v.push_back(n);
           else
             for (int j = 0; j < 4; ++j)
-              if (m.hang_master[4 * h + j] >= 0) add(m.hang_master[4 * h + j]);
+              if (m.hang_master[4 * h + j] >= 0) v.push_back(m.hang_master[4 * h + j]);
         }
       std::sort(v.begin(), v.end());
-      for (int32_t n : v) nblocks_of[n]++;
+      v.erase(std::unique(v.begin(), v.end()), v.end());
+      for (int32_t n : v) __atomic_fetch_add(&nblocks_of[n], 1, __ATOMIC_RELAXED);
+      bl[b].swap(v);
     }
-  }
+  });
   m.blk_elem.assign(2 * (size_t)nblk, 0);
   m.blk_node.assign(nblk + 1, 0);
   m.blk_shared.assign(nblk, 0);
@@ -670,78 +682,106 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
   m.blk_iptr.assign(nblk + 1, 0);
   m.blk_inv.assign(nblk, 0);
   m.lcorner.assign(8 * (size_t)Ne, 0);
-  std::vector<int32_t> local_of(Nn, -1);
-  std::vector<int32_t> lcount, lfill;          // per-block CSR scratch of the inverse lists
+  // per block: nreg, nshared, nhang, ninv (its lists' lengths); per thread: the lists
+  std::vector<std::array<int32_t, 4>> bsz(nblk);
+  struct BlkLists { std::vector<int32_t> lnode; std::vector<uint16_t> hent, iptr, inv; };
+  std::vector<BlkLists> bls(nbt);
+  std::vector<const char *> berr(nbt, nullptr);
+  std::vector<int32_t> bmax(nbt, 0);
+  chunked(nbt, (size_t)nblk, [&](int t, size_t lo, size_t hi) {
+    BlkLists out;
+    std::vector<int32_t> local_of(Nn, -1);
+    std::vector<int32_t> lcount, lfill;          // per-block CSR scratch of the inverse lists
+    int32_t max_local = 0;
+    for (size_t b = lo; b < hi; ++b) {
+      const std::vector<int32_t> &v = bl[b];
+      std::vector<int32_t> order;
+      order.reserve(v.size());
+      for (int32_t n : v) if (nblocks_of[n] > 1) order.push_back(n);
+      const int32_t nshared = (int32_t)order.size();
+      for (int32_t n : v) if (nblocks_of[n] == 1) order.push_back(n);
+      const int32_t nreg = (int32_t)order.size();
+      for (int32_t i = 0; i < nreg; ++i) local_of[order[i]] = i;
+      out.lnode.insert(out.lnode.end(), order.begin(), order.end());
+      // hanging nodes used by this block: local ids nreg, nreg+1, ... in first-use order
+      std::vector<int32_t> used_h;
+      const int64_t e0 = blks[b].e0, e1 = blks[b].e1;   // range of gen
+      for (int64_t u = e0; u < e1; ++u)
+        for (int k = 0; k < 8; ++k) {
+          const int32_t n = m.conn[8 * (int64_t)gen[u] + k];
+          if (m.hang_index[n] >= 0 && local_of[n] < 0) {
+            local_of[n] = nreg + (int32_t)used_h.size();
+            used_h.push_back(m.hang_index[n]);
+          }
+        }
+      const int32_t nloc = nreg + (int32_t)used_h.size();
+      if (nloc > kMaxLocal) { berr[t] = "block local-node limit exceeded"; break; }
+      max_local = std::max(max_local, nloc);
+      for (int64_t u = e0; u < e1; ++u)
+        for (int k = 0; k < 8; ++k) {
+          const int64_t e = gen[u];
+          m.lcorner[8 * e + k] = (uint16_t)local_of[m.conn[8 * e + k]];
+        }
+      // inverse lists, built as one block-local CSR: per local node its slots (element order),
+      // then its fold entries (hanging order)
+      if (used_h.size() >= (size_t)kQuarterBit) { berr[t] = "too many hanging nodes in a block"; break; }
+      lcount.assign(nloc + 1, 0);
+      for (int64_t u = e0; u < e1; ++u)
+        for (int k = 0; k < 8; ++k) lcount[local_of[m.conn[8 * (int64_t)gen[u] + k]] + 1]++;
+      for (size_t j = 0; j < used_h.size(); ++j)
+        for (int q = 0; q < 4; ++q) {
+          const int32_t mm = m.hang_master[4 * used_h[j] + q];
+          if (mm >= 0) lcount[local_of[mm] + 1]++;
+        }
+      for (int32_t i = 0; i < nloc; ++i) lcount[i + 1] += lcount[i];
+      if (lcount[nloc] > 0xFFFF) { berr[t] = "inverse list of a block too long"; break; }
+      const size_t inv0 = out.inv.size();
+      out.inv.resize(inv0 + lcount[nloc]);
+      lfill.assign(lcount.begin(), lcount.end() - 1);
+      for (int64_t u = e0; u < e1; ++u)
+        for (int k = 0; k < 8; ++k)   // the slot's offset in the block's per-element result buffer
+          out.inv[inv0 + lfill[local_of[m.conn[8 * (int64_t)gen[u] + k]]]++] = (uint16_t)((u - e0) * kSlotRow + 3 * k);
+      for (size_t j = 0; j < used_h.size(); ++j) {
+        const int32_t h = used_h[j];
+        const bool quarter = m.hang_master[4 * h + 2] >= 0;
+        for (int q = 0; q < 4; ++q) {
+          const int32_t mm = m.hang_master[4 * h + q];
+          out.hent.push_back(mm >= 0 ? (uint16_t)local_of[mm] : (uint16_t)0xFFFF);
+          if (mm >= 0)
+            out.inv[inv0 + lfill[local_of[mm]]++] = (uint16_t)(kFoldBit | (quarter ? kQuarterBit : 0) | j);
+        }
+      }
+      for (int32_t i = 0; i <= nloc; ++i) out.iptr.push_back((uint16_t)lcount[i]);
+      bsz[b] = {nreg, nshared, (int32_t)used_h.size(), lcount[nloc]};
+      m.blk_elem[2 * b] = (int32_t)e0;
+      m.blk_elem[2 * b + 1] = (int32_t)e1;
+      for (int32_t n : order) local_of[n] = -1;
+      for (int32_t h : used_h) local_of[m.hang_node[h]] = -1;
+    }
+    bmax[t] = max_local;
+    bls[t] = std::move(out);
+  });
+  for (int t = 0; t < nbt; ++t)
+    if (berr[t]) return berr[t];
   int32_t max_local = 0;
+  for (int t = 0; t < nbt; ++t) max_local = std::max(max_local, bmax[t]);
+  int64_t ninv_all = 0;
   for (int32_t b = 0; b < nblk; ++b) {
-    const std::vector<int32_t> &v = bl[b];
-    std::vector<int32_t> order;
-    order.reserve(v.size());
-    for (int32_t n : v) if (nblocks_of[n] > 1) order.push_back(n);
-    const int32_t nshared = (int32_t)order.size();
-    for (int32_t n : v) if (nblocks_of[n] == 1) order.push_back(n);
-    const int32_t nreg = (int32_t)order.size();
-    for (int32_t i = 0; i < nreg; ++i) local_of[order[i]] = i;
+    const int32_t nreg = bsz[b][0], nshared = bsz[b][1], nhang = bsz[b][2], nloc = nreg + nhang;
     m.blk_node[b + 1] = m.blk_node[b] + nreg;
     m.blk_shared[b] = nshared;
     m.blk_slot[b + 1] = m.blk_slot[b] + nshared;
-    m.lnode.insert(m.lnode.end(), order.begin(), order.end());
-    // hanging nodes used by this block: local ids nreg, nreg+1, ... in first-use order
-    std::vector<int32_t> used_h;
-    const int64_t e0 = blks[b].e0, e1 = blks[b].e1;   // range of gen
-    for (int64_t u = e0; u < e1; ++u)
-      for (int k = 0; k < 8; ++k) {
-        const int32_t n = m.conn[8 * (int64_t)gen[u] + k];
-        if (m.hang_index[n] >= 0 && local_of[n] < 0) {
-          local_of[n] = nreg + (int32_t)used_h.size();
-          used_h.push_back(m.hang_index[n]);
-        }
-      }
-    const int32_t nloc = nreg + (int32_t)used_h.size();
-    if (nloc > kMaxLocal) return "block local-node limit exceeded";
-    max_local = std::max(max_local, nloc);
-    m.blk_hang[b + 1] = m.blk_hang[b] + (int32_t)used_h.size();
-    for (int64_t u = e0; u < e1; ++u)
-      for (int k = 0; k < 8; ++k) {
-        const int64_t e = gen[u];
-        m.lcorner[8 * e + k] = (uint16_t)local_of[m.conn[8 * e + k]];
-      }
-    // inverse lists, built as one block-local CSR: per local node its slots (element order),
-    // then its fold entries (hanging order)
-    if (used_h.size() >= (size_t)kQuarterBit) return "too many hanging nodes in a block";
-    lcount.assign(nloc + 1, 0);
-    for (int64_t u = e0; u < e1; ++u)
-      for (int k = 0; k < 8; ++k) lcount[local_of[m.conn[8 * (int64_t)gen[u] + k]] + 1]++;
-    for (size_t j = 0; j < used_h.size(); ++j)
-      for (int q = 0; q < 4; ++q) {
-        const int32_t mm = m.hang_master[4 * used_h[j] + q];
-        if (mm >= 0) lcount[local_of[mm] + 1]++;
-      }
-    for (int32_t i = 0; i < nloc; ++i) lcount[i + 1] += lcount[i];
-    if (lcount[nloc] > 0xFFFF) return "inverse list of a block too long";
-    m.blk_inv[b] = (int32_t)m.inv.size();
+    m.blk_hang[b + 1] = m.blk_hang[b] + nhang;
+    m.blk_inv[b] = (int32_t)ninv_all;
     m.blk_iptr[b + 1] = m.blk_iptr[b] + nloc + 1;
-    const size_t inv0 = m.inv.size();
-    m.inv.resize(inv0 + lcount[nloc]);
-    lfill.assign(lcount.begin(), lcount.end() - 1);
-    for (int64_t u = e0; u < e1; ++u)
-      for (int k = 0; k < 8; ++k)   // the slot's offset in the block's per-element result buffer
-        m.inv[inv0 + lfill[local_of[m.conn[8 * (int64_t)gen[u] + k]]]++] = (uint16_t)((u - e0) * kSlotRow + 3 * k);
-    for (size_t j = 0; j < used_h.size(); ++j) {
-      const int32_t h = used_h[j];
-      const bool quarter = m.hang_master[4 * h + 2] >= 0;
-      for (int q = 0; q < 4; ++q) {
-        const int32_t mm = m.hang_master[4 * h + q];
-        m.hent.push_back(mm >= 0 ? (uint16_t)local_of[mm] : (uint16_t)0xFFFF);
-        if (mm >= 0)
-          m.inv[inv0 + lfill[local_of[mm]]++] = (uint16_t)(kFoldBit | (quarter ? kQuarterBit : 0) | j);
-      }
-    }
-    for (int32_t i = 0; i <= nloc; ++i) m.iptr.push_back((uint16_t)lcount[i]);
-    m.blk_elem[2 * b] = (int32_t)e0;
-    m.blk_elem[2 * b + 1] = (int32_t)e1;
-    for (int32_t n : order) local_of[n] = -1;
-    for (int32_t h : used_h) local_of[m.hang_node[h]] = -1;
+    ninv_all += bsz[b][3];
+  }
+  for (int t = 0; t < nbt; ++t) {
+    m.lnode.insert(m.lnode.end(), bls[t].lnode.begin(), bls[t].lnode.end());
+    m.hent.insert(m.hent.end(), bls[t].hent.begin(), bls[t].hent.end());
+    m.iptr.insert(m.iptr.end(), bls[t].iptr.begin(), bls[t].iptr.end());
+    m.inv.insert(m.inv.end(), bls[t].inv.begin(), bls[t].inv.end());
+    bls[t] = BlkLists();
   }
   m.max_local = max_local;
 
