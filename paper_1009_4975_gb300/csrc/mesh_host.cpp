@@ -185,59 +185,78 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
   const int64_t Ne = d.n_leaves;
   m.Ne = Ne;
 
-  // ---- 1. validate, sort, disjoint + cover
+  // ---- 1. validate, sort, disjoint + cover (on host threads: the first failing leaf of the first
+  // failing chunk is the first failing leaf in order)
   std::vector<uint64_t> key(Ne);
-  for (int64_t e = 0; e < Ne; ++e) {
-    const int32_t *l = d.leaves + 4 * e;
-    if (l[3] < 0 || l[3] > L) return "leaf level out of range";
-    const int64_t s = (int64_t)1 << (L - l[3]);
-    for (int a = 0; a < 3; ++a) {
-      const int64_t ext = a == 0 ? fx : (a == 1 ? fy : fz);
-      if (l[a] < 0 || l[a] + s > ext) return "leaf outside the domain";
-      if (l[a] % s) return "leaf anchor not aligned to its size";
-    }
-    key[e] = morton3(l[0], l[1], l[2]);
+  {
+    const int nt = host_threads(Ne);
+    std::vector<const char *> err(nt, nullptr);
+    chunked(nt, (size_t)Ne, [&](int t, size_t lo, size_t hi) {
+      for (size_t e = lo; e < hi; ++e) {
+        const int32_t *l = d.leaves + 4 * e;
+        if (l[3] < 0 || l[3] > L) { err[t] = "leaf level out of range"; return; }
+        const int64_t s = (int64_t)1 << (L - l[3]);
+        for (int a = 0; a < 3; ++a) {
+          const int64_t ext = a == 0 ? fx : (a == 1 ? fy : fz);
+          if (l[a] < 0 || l[a] + s > ext) { err[t] = "leaf outside the domain"; return; }
+          if (l[a] % s) { err[t] = "leaf anchor not aligned to its size"; return; }
+        }
+        key[e] = morton3(l[0], l[1], l[2]);
+      }
+    });
+    for (const char *e : err)
+      if (e) return e;
   }
   m.perm = radix_order(key);
   m.leaf.resize(4 * Ne);
-  int64_t covered = 0;
-  for (int64_t i = 0; i < Ne; ++i) {
-    const int32_t *l = d.leaves + 4 * m.perm[i];
-    std::memcpy(&m.leaf[4 * i], l, 16);
-    const int64_t s = (int64_t)1 << (L - l[3]);
-    covered += s * s * s;
-    if (i + 1 < Ne) {
-      const uint64_t end = key[m.perm[i]] + (uint64_t)(s * s * s);
-      if (end > key[m.perm[i + 1]]) return "leaves overlap";
-    }
-  }
-  if (covered != fx * fy * fz) return "leaves do not cover the domain";
-
-  // ---- 2. nodes: the distinct corner keys in Morton order; conn and coordinates from them
-  std::vector<uint64_t> ckey(8 * Ne);
-  chunked(host_threads(Ne), (size_t)Ne, [&](int, size_t lo, size_t hi) {
-    for (size_t e = lo; e < hi; ++e) {
-      const int32_t *l = &m.leaf[4 * e];
-      const int32_t s = 1 << (L - l[3]);
-      for (int k = 0; k < 8; ++k)
-        ckey[8 * e + k] = morton3(l[0] + s * (k & 1), l[1] + s * ((k >> 1) & 1), l[2] + s * ((k >> 2) & 1));
-    }
-  });
-  uint64_t kmax = 0;
-  for (uint64_t k : ckey) kmax = std::max(kmax, k);
-  const uint64_t nword = kmax / 64 + 1;
-  if (nword <= std::max<uint64_t>(1u << 16, (uint64_t)(8 * Ne))) {
-    // a bitmap of the Morton key space: a node's id is the number of distinct corner keys below
-    // its own, the same numbering as sorting and deduplicating the keys
-    std::vector<uint64_t> bm(nword, 0);
-    chunked(host_threads(8 * Ne), (size_t)(8 * Ne), [&](int, size_t lo, size_t hi) {
+  {
+    // sorted leaves that each end at or before the next one's key neither overlap nor, when their
+    // volumes add up to the domain's, leave a gap
+    const int nt = host_threads(Ne);
+    std::vector<int64_t> covered(nt, 0);
+    std::vector<uint8_t> overlap(nt, 0);
+    chunked(nt, (size_t)Ne, [&](int t, size_t lo, size_t hi) {
       for (size_t i = lo; i < hi; ++i) {
-        uint64_t *w = &bm[ckey[i] >> 6];
-        const uint64_t b = 1ull << (ckey[i] & 63);
-        if (!(__atomic_load_n(w, __ATOMIC_RELAXED) & b)) __atomic_fetch_or(w, b, __ATOMIC_RELAXED);
+        const int32_t *l = d.leaves + 4 * m.perm[i];
+        std::memcpy(&m.leaf[4 * i], l, 16);
+        const int64_t s = (int64_t)1 << (L - l[3]);
+        covered[t] += s * s * s;
+        if ((int64_t)i + 1 < Ne && key[m.perm[i]] + (uint64_t)(s * s * s) > key[m.perm[i + 1]]) overlap[t] = 1;
       }
     });
-    std::vector<int64_t> below(nword);   // set bits in the words before w
+    int64_t total = 0;
+    for (int t = 0; t < nt; ++t) {
+      if (overlap[t]) return "leaves overlap";
+      total += covered[t];
+    }
+    if (total != fx * fy * fz) return "leaves do not cover the domain";
+  }
+
+  // ---- 2. nodes: the distinct corner keys in Morton order; conn and coordinates from them
+  auto corner_key = [&](size_t e, int k) {
+    const int32_t *l = &m.leaf[4 * e];
+    const int32_t s = 1 << (L - l[3]);
+    return morton3(l[0] + s * (k & 1), l[1] + s * ((k >> 1) & 1), l[2] + s * ((k >> 2) & 1));
+  };
+  // the key grows with each coordinate, so the domain's far corner (always a node) has the
+  // largest key
+  const uint64_t nword = morton3((uint32_t)fx, (uint32_t)fy, (uint32_t)fz) / 64 + 1;
+  // a bitmap of the Morton key space (when it is small enough): a node's id is the number of
+  // distinct corner keys below its own, the same numbering as sorting and deduplicating the keys
+  std::vector<uint64_t> bm;
+  std::vector<int64_t> below;   // set bits in the words before w
+  if (nword <= std::max<uint64_t>(1u << 16, (uint64_t)(8 * Ne))) {
+    bm.assign(nword, 0);
+    chunked(host_threads(8 * Ne), (size_t)Ne, [&](int, size_t lo, size_t hi) {
+      for (size_t e = lo; e < hi; ++e)
+        for (int k = 0; k < 8; ++k) {
+          const uint64_t key = corner_key(e, k);
+          uint64_t *w = &bm[key >> 6];
+          const uint64_t b = 1ull << (key & 63);
+          if (!(__atomic_load_n(w, __ATOMIC_RELAXED) & b)) __atomic_fetch_or(w, b, __ATOMIC_RELAXED);
+        }
+    });
+    below.resize(nword);
     const int nt = host_threads(nword * 8);
     std::vector<int64_t> part(nt + 1, 0);
     chunked(nt, nword, [&](int t, size_t lo, size_t hi) {
@@ -256,13 +275,20 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
       }
     });
     m.conn.resize(8 * Ne);
-    chunked(host_threads(8 * Ne), (size_t)(8 * Ne), [&](int, size_t lo, size_t hi) {
-      for (size_t i = lo; i < hi; ++i) {
-        const uint64_t w = ckey[i] >> 6, low = (1ull << (ckey[i] & 63)) - 1;
-        m.conn[i] = (int32_t)(below[w] + __builtin_popcountll(bm[w] & low));
-      }
+    chunked(host_threads(8 * Ne), (size_t)Ne, [&](int, size_t lo, size_t hi) {
+      for (size_t e = lo; e < hi; ++e)
+        for (int k = 0; k < 8; ++k) {
+          const uint64_t key = corner_key(e, k);
+          const uint64_t w = key >> 6, low = (1ull << (key & 63)) - 1;
+          m.conn[8 * e + k] = (int32_t)(below[w] + __builtin_popcountll(bm[w] & low));
+        }
     });
   } else {
+    std::vector<uint64_t> ckey(8 * Ne);
+    chunked(host_threads(Ne), (size_t)Ne, [&](int, size_t lo, size_t hi) {
+      for (size_t e = lo; e < hi; ++e)
+        for (int k = 0; k < 8; ++k) ckey[8 * e + k] = corner_key(e, k);
+    });
     std::vector<uint64_t> sk;
     const std::vector<int64_t> ord = radix_order(ckey, &sk);
     std::vector<int32_t> nid(8 * Ne);
@@ -362,7 +388,14 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
             z += m.node_xyz[3 * cn[cs[i]] + 2];
           }
           x /= nc; y /= nc; z /= nc;
-          const int64_t n = find_key(m.node_key, morton3((uint32_t)x, (uint32_t)y, (uint32_t)z));
+          const uint64_t key = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+          int64_t n;
+          if (bm.empty()) {
+            n = find_key(m.node_key, key);
+          } else {
+            const uint64_t w = key >> 6, bit = 1ull << (key & 63);
+            n = w < bm.size() && (bm[w] & bit) ? below[w] + __builtin_popcountll(bm[w] & (bit - 1)) : -1;
+          }
           if (n < 0) return;
           Found f{(int32_t)n, {-1, -1, -1, -1}};
           for (int i = 0; i < nc; ++i) f.ms[i] = cn[cs[i]];
@@ -402,6 +435,9 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
         if (mm >= 0 && m.hang_index[mm] >= 0) return "constraint chain (master is hanging)";
       }
   }
+
+  std::vector<uint64_t>().swap(bm);
+  std::vector<int64_t>().swap(below);
 
   // ---- 5. flags
   m.nflag.assign(Nn, 0);
@@ -817,16 +853,18 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     // the brick pass's packed table: per brick 3 x 128 int32 -- node ids (125, then e0 at 125),
     // output targets (125), fold mask | axes << 24 (125)
     m.brick_tab.assign((size_t)384 * m.nbrick, 0);
-    for (int32_t bk = 0; bk < m.nbrick; ++bk) {
-      int32_t *t = &m.brick_tab[(size_t)384 * bk];
-      for (int nd = 0; nd < 125; ++nd) {
-        const size_t i = (size_t)125 * bk + nd;
-        t[nd] = m.brick_node[i];
-        t[128 + nd] = m.brick_out[i];
-        t[256 + nd] = (int32_t)(m.brick_fold[i] | ((uint32_t)m.brick_hax[i] << 24));
+    chunked(host_threads((size_t)m.nbrick * 128), (size_t)m.nbrick, [&](int, size_t lo, size_t hi) {
+      for (size_t bk = lo; bk < hi; ++bk) {
+        int32_t *t = &m.brick_tab[(size_t)384 * bk];
+        for (int nd = 0; nd < 125; ++nd) {
+          const size_t i = (size_t)125 * bk + nd;
+          t[nd] = m.brick_node[i];
+          t[128 + nd] = m.brick_out[i];
+          t[256 + nd] = (int32_t)(m.brick_fold[i] | ((uint32_t)m.brick_hax[i] << 24));
+        }
+        t[125] = m.brick_e0[bk];
       }
-      t[125] = m.brick_e0[bk];
-    }
+    });
     m.sh_ptr.push_back(0);
     m.sh_of_node.assign(Nn, -1);
     for (int64_t n = 0; n < Nn; ++n)
@@ -850,47 +888,59 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     m.max_rec_bytes = 0;
     m.max_rec_stage = 0;
     auto align = [](size_t v, size_t a) { return (v + a - 1) / a * a; };
-    for (int32_t b = 0; b < nblk; ++b) {
-      const int32_t nreg = m.blk_node[b + 1] - m.blk_node[b];
-      const int32_t nshared = m.blk_shared[b];
-      const int32_t nhang = m.blk_hang[b + 1] - m.blk_hang[b];
-      const int32_t nloc = nreg + nhang;
-      const int32_t ninv = m.iptr[m.blk_iptr[b] + nloc];
-      const int32_t ne = m.blk_elem[2 * b + 1] - m.blk_elem[2 * b];
+    struct Layout { int32_t nreg, nshared, nhang, nloc, ninv, ne; size_t o_lcorner, o_elist, o_lnode, o_lslot, o_hent, o_iptr, o_inv, bytes; };
+    auto layout = [&](int32_t b) {
+      Layout y;
+      y.nreg = m.blk_node[b + 1] - m.blk_node[b];
+      y.nshared = m.blk_shared[b];
+      y.nhang = m.blk_hang[b + 1] - m.blk_hang[b];
+      y.nloc = y.nreg + y.nhang;
+      y.ninv = m.iptr[m.blk_iptr[b] + y.nloc];
+      y.ne = m.blk_elem[2 * b + 1] - m.blk_elem[2 * b];
       size_t off = 64;
-      const size_t o_lcorner = off; off += 16 * (size_t)ne;
-      const size_t o_elist = off; off += 4 * (size_t)ne;
+      y.o_lcorner = off; off += 16 * (size_t)y.ne;
+      y.o_elist = off; off += 4 * (size_t)y.ne;
       off = align(off, 16);   // the sections from lnode on are staged into shared memory
-      const size_t o_lnode = off; off += 4 * (size_t)nreg;
-      const size_t o_lslot = off; off += 4 * (size_t)nshared;
+      y.o_lnode = off; off += 4 * (size_t)y.nreg;
+      y.o_lslot = off; off += 4 * (size_t)y.nshared;
       off = align(off, 8);
-      const size_t o_hent = off; off += 8 * (size_t)nhang;
-      const size_t o_iptr = off; off += 2 * (size_t)(nloc + 1);
-      const size_t o_inv = off; off += 2 * (size_t)ninv;
-      const size_t bytes = align(off, 16);
-      std::vector<uint8_t> rec(bytes, 0);
-      const int32_t *el = &gen[m.blk_elem[2 * b]];
-      int32_t hdr[16] = {el[0], ne, nreg, nshared, nhang, ninv, (int32_t)o_lslot, (int32_t)o_hent,
-                         (int32_t)o_iptr, (int32_t)o_inv, (int32_t)o_lcorner, (int32_t)o_lnode, (int32_t)o_elist,
-                         0, 0, 0};
-      std::memcpy(rec.data(), hdr, sizeof(hdr));
-      for (int32_t t = 0; t < ne; ++t) std::memcpy(&rec[o_lcorner + 16 * (size_t)t], &m.lcorner[8 * (size_t)el[t]], 16);
-      std::memcpy(&rec[o_elist], el, 4 * (size_t)ne);
-      for (int32_t i = 0; i < nreg; ++i) {
-        uint32_t g = (uint32_t)m.lnode[m.blk_node[b] + i];
-        if (m.nflag[g] & 1) g |= 0x80000000u;
-        std::memcpy(&rec[o_lnode + 4 * i], &g, 4);
-      }
-      if (nshared) std::memcpy(&rec[o_lslot], &m.lslot[m.blk_slot[b]], 4 * (size_t)nshared);
-      if (nhang) std::memcpy(&rec[o_hent], &m.hent[4 * (size_t)m.blk_hang[b]], 8 * (size_t)nhang);
-      std::memcpy(&rec[o_iptr], &m.iptr[m.blk_iptr[b]], 2 * (size_t)(nloc + 1));
-      if (ninv) std::memcpy(&rec[o_inv], &m.inv[m.blk_inv[b]], 2 * (size_t)ninv);
-      m.brec.insert(m.brec.end(), rec.begin(), rec.end());
-      m.rec_off[b + 1] = (int32_t)(m.brec.size() / 16);
-      m.max_rec_bytes = std::max<int32_t>(m.max_rec_bytes, (int32_t)bytes);
-      m.rec_skip[b] = (int32_t)((o_lnode - 64) / 16);
-      m.max_rec_stage = std::max<int32_t>(m.max_rec_stage, (int32_t)(bytes - (o_lnode - 64)));
+      y.o_hent = off; off += 8 * (size_t)y.nhang;
+      y.o_iptr = off; off += 2 * (size_t)(y.nloc + 1);
+      y.o_inv = off; off += 2 * (size_t)y.ninv;
+      y.bytes = align(off, 16);
+      return y;
+    };
+    // the offsets in block order, then the records written in parallel
+    for (int32_t b = 0; b < nblk; ++b) {
+      const Layout y = layout(b);
+      m.rec_off[b + 1] = m.rec_off[b] + (int32_t)(y.bytes / 16);
+      m.max_rec_bytes = std::max<int32_t>(m.max_rec_bytes, (int32_t)y.bytes);
+      m.rec_skip[b] = (int32_t)((y.o_lnode - 64) / 16);
+      m.max_rec_stage = std::max<int32_t>(m.max_rec_stage, (int32_t)(y.bytes - (y.o_lnode - 64)));
     }
+    m.brec.assign(16 * (size_t)m.rec_off[nblk], 0);
+    chunked(host_threads((size_t)nblk * 4096), (size_t)nblk, [&](int, size_t lo, size_t hi) {
+      for (size_t b = lo; b < hi; ++b) {
+        const Layout y = layout((int32_t)b);
+        uint8_t *rec = &m.brec[16 * (size_t)m.rec_off[b]];
+        const int32_t *el = &gen[m.blk_elem[2 * b]];
+        int32_t hdr[16] = {el[0], y.ne, y.nreg, y.nshared, y.nhang, y.ninv, (int32_t)y.o_lslot, (int32_t)y.o_hent,
+                           (int32_t)y.o_iptr, (int32_t)y.o_inv, (int32_t)y.o_lcorner, (int32_t)y.o_lnode,
+                           (int32_t)y.o_elist, 0, 0, 0};
+        std::memcpy(rec, hdr, sizeof(hdr));
+        for (int32_t t = 0; t < y.ne; ++t) std::memcpy(&rec[y.o_lcorner + 16 * (size_t)t], &m.lcorner[8 * (size_t)el[t]], 16);
+        std::memcpy(&rec[y.o_elist], el, 4 * (size_t)y.ne);
+        for (int32_t i = 0; i < y.nreg; ++i) {
+          uint32_t g = (uint32_t)m.lnode[m.blk_node[b] + i];
+          if (m.nflag[g] & 1) g |= 0x80000000u;
+          std::memcpy(&rec[y.o_lnode + 4 * i], &g, 4);
+        }
+        if (y.nshared) std::memcpy(&rec[y.o_lslot], &m.lslot[m.blk_slot[b]], 4 * (size_t)y.nshared);
+        if (y.nhang) std::memcpy(&rec[y.o_hent], &m.hent[4 * (size_t)m.blk_hang[b]], 8 * (size_t)y.nhang);
+        std::memcpy(&rec[y.o_iptr], &m.iptr[m.blk_iptr[b]], 2 * (size_t)(y.nloc + 1));
+        if (y.ninv) std::memcpy(&rec[y.o_inv], &m.inv[m.blk_inv[b]], 2 * (size_t)y.ninv);
+      }
+    });
   }
 
   // ---- 8. Jacobi diagonal coefficients: d_{m,c} = sum_e c_e q_{e,m,c}
