@@ -161,7 +161,12 @@ int tm_mesh_tables(tm_ctx *ctx, int64_t *perm, int32_t *node_xyz, int32_t *conn,
 /* Host-only construction of the same integer tables (no device, no context):
  * the tables tm_mesh_upload builds, for inspection and testing on machines
  * without a GPU.  On failure returns TM_EINVAL and writes a message into err
- * (err_len bytes, may be 0).  info->device_bytes is 0. */
+ * (err_len bytes, may be 0).  info->device_bytes is 0.
+ * Host threads: tm_mesh_upload, tm_tables_build and the adaptation's new leaf set
+ * (tm_amr_adapt, tm_tables_adapt) run on up to 16 host threads, one per 65,536
+ * items at most; the environment variable TM_HOST_THREADS (a positive integer,
+ * read at every call) lowers the limit.  Every table and error is the same for
+ * any number of threads. */
 typedef struct tm_tables tm_tables;
 int tm_tables_build(const tm_mesh_desc *d, tm_tables **out, tm_mesh_info *info, char *err, int err_len);
 /* Same layout as tm_mesh_tables. */

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <unordered_map>
 #include <numeric>
@@ -54,9 +55,16 @@ static inline uint32_t compact3(uint64_t x) {
 // LSD radix sort of keys, returning the permutation (stable).
 static_assert(kBlockElems * kSlotRow < kQuarterBit, "inverse-list slot offsets must stay below the fold bits");
 
-// Host threads for the table builds: up to 16, at most one per 64k items.
+// Host threads for the table builds: up to 16, at most one per 64k items, and at most the
+// positive integer in the environment variable TM_HOST_THREADS when it holds one (read at every
+// call).  The tables do not depend on the number.
 static int host_threads(size_t n) {
-  const int hw = (int)std::thread::hardware_concurrency();
+  int hw = (int)std::thread::hardware_concurrency();
+  if (const char *env = std::getenv("TM_HOST_THREADS")) {
+    char *end = nullptr;
+    const long v = std::strtol(env, &end, 10);
+    if (end != env && *end == 0 && v > 0) hw = (int)std::min<long>(v, 16);
+  }
   return (int)std::max<size_t>(1, std::min<size_t>({(size_t)16, (size_t)(hw > 0 ? hw : 1), n / 65536 + 1}));
 }
 
@@ -968,7 +976,8 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     // (node, coefficient triple) entries in element order; every chunk numbers the distinct
     // triples it meets in order of first appearance, and the chunks' numberings are merged in
     // chunk order, so the table is the one an element-order pass would build
-    const int nt = host_threads(Ne);
+    // (the threads' node counts below take nt x Nn int32: capped at 512 MB)
+    const int nt = std::max(1, std::min(host_threads(Ne), (int)((int64_t(1) << 27) / std::max<int64_t>(Nn, 1))));
     std::vector<std::vector<int32_t>> cx_node(nt), cx_lq(nt);
     std::vector<std::vector<std::array<double, 3>>> cx_tab(nt);
     std::vector<int32_t> ex_end(Ne, 0);   // per element: end of its entries within its chunk's list

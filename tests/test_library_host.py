@@ -131,3 +131,40 @@ def test_python_binding_fails_loudly_without_gpu(tm):
         pytest.skip("a GPU is present")
     with pytest.raises(tm.TmError):
         tm.tm_create(0, stream=0)
+
+
+def test_tables_do_not_depend_on_the_number_of_host_threads(tm, monkeypatch):
+    """The table build and the adaptation's new leaf set split their passes over host threads
+    (at most one per 65,536 items, limited by TM_HOST_THREADS) and merge the chunks in order.  On a
+    202k-leaf truss mesh (bricks, blocks, hanging nodes) every exported table and the adapted leaf
+    set are the same bytes with 1, 3 and the default number of threads."""
+    w = W.small_truss(seed=3, base=(32, 16, 16), L=2)
+    d = w.dom
+    rng = np.random.default_rng(8)
+    mark = ((w.leaves[:, 3] < d.L) & (rng.random(len(w.leaves)) < 0.05)).astype(np.int8)
+    rho = rng.uniform(1e-3, 1.0, len(w.leaves))
+
+    def everything(nthreads):
+        if nthreads is None:
+            monkeypatch.delenv("TM_HOST_THREADS", raising=False)
+        else:
+            monkeypatch.setenv("TM_HOST_THREADS", str(nthreads))
+        info, t = tm.tm_tables_build(d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, dirichlet_faces=w.dirichlet_faces)
+        ops = tm.tm_tables_operator(d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, w.dirichlet_faces)
+        # the adaptation takes the leaves in canonical (Morton) order
+        leaves = np.asarray(w.leaves)[t["perm"]]
+        al, ar = tm.tm_tables_adapt(d.nx, d.ny, d.nz, d.L, d.h0, leaves, mark[t["perm"]], rho[t["perm"]])
+        arrays = dict(t)
+        arrays.update({k: v for k, v in ops.items() if isinstance(v, np.ndarray)})
+        arrays.update(adapt_leaves=np.asarray(al), adapt_rho=np.asarray(ar))
+        return info, ops["info"], arrays
+
+    ref_info, ref_ops_info, ref = everything(1)
+    assert ref_info["Ne"] > 3 * 65536 and ref_info["n_blocks"] > 100 and ref_info["n_bricks"] > 1000
+    assert ref_info["n_hanging"] > 0
+    for n in (3, None):
+        info, ops_info, got = everything(n)
+        assert info == ref_info and ops_info == ref_ops_info
+        assert got.keys() == ref.keys()
+        for k in ref:
+            assert got[k].dtype == ref[k].dtype and got[k].tobytes() == ref[k].tobytes(), (n, k)
