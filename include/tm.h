@@ -198,6 +198,17 @@ int tm_tables_operator(const tm_tables *t, int32_t *rec_off, uint8_t *brec, doub
  * neighbour one step along axis a, hanging along a; bit 6 + 4 p + 2 (step1 > 0) + (step0 > 0) the
  * diagonal neighbour in coordinate plane p = (x, y), (x, z), (y, z), hanging in that plane). */
 int tm_tables_bricks(const tm_tables *t, int32_t *e0, int32_t *node, uint8_t *hax, int32_t *out, uint32_t *fold);
+/* Host-only export of the Jacobi-diagonal tables of tm_jacobi_diag (Sec. 5), node-major:
+ * the diagonal of C^T K(rho) C at a free node n, component c, is the sum over
+ * j in [ptr[n], ptr[n + 1]) of c_e tab[3 q[j] + c] with e = elem[j] (ascending within a node)
+ * and c_e = (Emin + rho_e^penal (E0 - Emin)) h_e, h_e the element's edge length; tab holds the
+ * distinct triples v^T K0_cc v of the unit cube's matrix K0 (E = 1), v the node's weights on
+ * the element's corners (1 at its own corner; 1/2 or 1/4 at the corners it is a master of),
+ * tab[0..2] the triple of a corner that is its own node.  Sizes: ptr[Nn + 1],
+ * elem[*n_entries], q[*n_entries], tab[3 *n_triples].  Any pointer may be NULL; call with
+ * them NULL to learn the sizes first. */
+int tm_tables_diag(const tm_tables *t, int32_t *ptr, int32_t *elem, uint16_t *q, double *tab, int64_t *n_entries,
+                   int64_t *n_triples);
 
 /* Host-only evaluation of a finite-element field of the tables' mesh at integer points
  * (the warm start after remeshing: the old displacement at the new mesh's nodes, see

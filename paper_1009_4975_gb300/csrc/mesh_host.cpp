@@ -1203,6 +1203,19 @@ int tm_tables_bricks(const tm_tables *t, int32_t *e0, int32_t *node, uint8_t *ha
   return TM_OK;
 }
 
+int tm_tables_diag(const tm_tables *t, int32_t *ptr, int32_t *elem, uint16_t *q, double *tab, int64_t *n_entries,
+                   int64_t *n_triples) {
+  if (!t) return TM_EINVAL;
+  const amr::HostMesh &h = t->m;
+  if (n_entries) *n_entries = (int64_t)h.dg_elem.size();
+  if (n_triples) *n_triples = (int64_t)(h.dg_tab.size() / 3);
+  if (ptr) std::memcpy(ptr, h.dg_ptr.data(), h.dg_ptr.size() * sizeof(int32_t));
+  if (elem) std::memcpy(elem, h.dg_elem.data(), h.dg_elem.size() * sizeof(int32_t));
+  if (q) std::memcpy(q, h.dg_q.data(), h.dg_q.size() * sizeof(uint16_t));
+  if (tab) std::memcpy(tab, h.dg_tab.data(), h.dg_tab.size() * sizeof(double));
+  return TM_OK;
+}
+
 int tm_tables_transfer(const tm_tables *t, const double *u_full, int64_t n_points, const int32_t *points,
                        double *out) {
   if (!t || !u_full || (n_points > 0 && (!points || !out)) || n_points < 0) return TM_EINVAL;

@@ -67,7 +67,7 @@ class tm_profile_data(C.Structure):
 EXPORTS = ["tm_create", "tm_destroy", "tm_set_stream", "tm_last_error", "tm_mesh_upload", "tm_mesh_tables",
            "tm_tables_build", "tm_tables_copy", "tm_tables_free", "tm_build_rhs", "tm_apply_K", "tm_apply_K_f32", "tm_apply_K_f32_static", "tm_apply_K_f32_multi", "tm_jacobi_diag", "tm_pcg_solve", "tm_pcg_solve_batch", "tm_pcg_solve_multi", "tm_expand",
            "tm_sensitivity", "tm_filter", "tm_oc_update", "tm_amr_mark", "tm_amr_adapt", "tm_design_difference",
-           "tm_tables_adapt", "tm_tables_operator", "tm_tables_bricks", "tm_tables_transfer", "tm_unet_param_count", "tm_unet_workspace_floats",
+           "tm_tables_adapt", "tm_tables_operator", "tm_tables_bricks", "tm_tables_diag", "tm_tables_transfer", "tm_unet_param_count", "tm_unet_workspace_floats",
            "tm_unet_forward", "tm_unet_backward", "tm_profile", "tm_profile_read", "tm_coarse_setup",
            "tm_coarse_cells", "tm_coarse_apply", "tm_coarse_restrict", "tm_coarse_prolong", "tm_coarse_vcycle", "tm_transfer_displacement", "tm_learn_input",
            "tm_learn_guess", "tm_learn_output_grad", "tm_adam_step"]
@@ -109,6 +109,7 @@ def load_library(path: str = LIB_PATH):
         "tm_tables_adapt": [vp, vp, vp, i64, vp, vp, C.POINTER(i64)],
         "tm_tables_operator": [vp, vp, vp, vp, vp, vp, C.POINTER(i64)],
         "tm_tables_bricks": [vp, vp, vp, vp, vp, vp],
+        "tm_tables_diag": [vp, vp, vp, vp, vp, C.POINTER(i64), C.POINTER(i64)],
         "tm_tables_transfer": [vp, vp, i64, vp, vp],
         "tm_unet_forward": [vp, C.POINTER(tm_unet_desc), vp, vp, vp, vp],
         "tm_unet_backward": [vp, C.POINTER(tm_unet_desc), vp, vp, vp, vp, vp, vp],
@@ -541,6 +542,34 @@ def tm_unet_backward(ctx: Ctx, desc: tm_unet_desc, params, x, dy, dparams, dx, w
                                               _ptr(dparams, torch.float32, None, "dparams"),
                                               None if dx is None else _ptr(dx, torch.float32, None, "dx"),
                                               _ptr(ws, torch.float32, None, "ws")))
+
+
+def tm_tables_diag(nx, ny, nz, max_level, h0, leaves, dirichlet_faces=1, nu=0.3):
+    """Host-only export of the Jacobi-diagonal tables (tm_tables_diag): dict with info, ptr, elem,
+    q (uint16), tab (triples x 3)."""
+    lib = load_library()
+    lv = np.ascontiguousarray(np.asarray(leaves, np.int32).reshape(-1, 4))
+    d = tm_mesh_desc(nx, ny, nz, max_level, h0, lv.shape[0], lv.ctypes.data_as(C.POINTER(C.c_int32)),
+                     dirichlet_faces, 1.0, 1e-9, nu, 3.0)
+    info = tm_mesh_info()
+    h = C.c_void_p()
+    err = C.create_string_buffer(512)
+    rc = lib.tm_tables_build(C.byref(d), C.byref(h), C.byref(info), err, 512)
+    if rc != TM_OK:
+        raise TmError(rc, err.value.decode())
+    try:
+        ne, nt = C.c_int64(0), C.c_int64(0)
+        lib.tm_tables_diag(h, None, None, None, None, C.byref(ne), C.byref(nt))
+        out = {"info": {k: getattr(info, k) for k, _ in tm_mesh_info._fields_},
+               "ptr": np.zeros(info.Nn + 1, np.int32), "elem": np.zeros(ne.value, np.int32),
+               "q": np.zeros(ne.value, np.uint16), "tab": np.zeros((nt.value, 3))}
+        rc = lib.tm_tables_diag(h, *[C.c_void_p(out[k].ctypes.data) for k in ("ptr", "elem", "q", "tab")],
+                                C.byref(ne), C.byref(nt))
+        if rc != TM_OK:
+            raise TmError(rc, "tm_tables_diag failed")
+        return out
+    finally:
+        lib.tm_tables_free(h)
 
 
 def tm_tables_transfer(nx, ny, nz, max_level, h0, leaves, u_full, points, dirichlet_faces=1):

@@ -168,3 +168,31 @@ def test_tables_do_not_depend_on_the_number_of_host_threads(tm, monkeypatch):
         assert got.keys() == ref.keys()
         for k in ref:
             assert got[k].dtype == ref[k].dtype and got[k].tobytes() == ref[k].tobytes(), (n, k)
+
+
+@pytest.mark.parametrize("make", [W.config1b, W.small_truss])
+def test_jacobi_diagonal_tables_against_the_assembled_matrix(tm, make):
+    """The Jacobi diagonal the library's tables give (sum over a node's entries of c_e times a
+    tabulated triple v^T K0 v, Sec. 5) equals the diagonal of the oracle's assembled C^T K C at
+    every free DOF, for random densities, on meshes with edge- and face-hanging nodes."""
+    from oracle import fem as F
+    w = make()
+    d = w.dom
+    m = M.build_mesh(d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, dirichlet_faces=w.dirichlet_faces)
+    rng = np.random.default_rng(11)
+    rho = rng.uniform(1e-3, 1.0, m.Ne)
+    A, _, _ = F.reduced_system(m, rho, w.load_nodes, w.load_comp, w.load_val, w.E0, w.Emin, w.nu, w.penal)
+    g = tm.tm_tables_diag(d.nx, d.ny, d.nz, d.L, d.h0, w.leaves, w.dirichlet_faces, nu=w.nu)
+    assert g["info"]["n_hanging"] > 0
+    ptr, elem, q, tab = g["ptr"], g["elem"], g["q"], g["tab"]
+    assert ptr[0] == 0 and np.all(np.diff(ptr) >= 0) and ptr[-1] == elem.size == q.size
+    assert int(q.max()) < tab.shape[0]
+    ce = (w.Emin + rho ** w.penal * (w.E0 - w.Emin)) * (d.h0 / 2.0 ** m.leaves[:, 3])
+    node = np.repeat(np.arange(m.Nn), np.diff(ptr))
+    dfull = np.zeros((m.Nn, 3))
+    np.add.at(dfull, node, ce[elem][:, None] * tab[q])
+    got = F.from_full_layout(m, dfull.ravel())
+    np.testing.assert_allclose(got, A.diagonal(), rtol=1e-13, atol=0)
+    # ascending elements within every node, and every element-node incidence listed once
+    same = node[1:] == node[:-1]
+    assert np.all(elem[1:][same] > elem[:-1][same])
