@@ -15,7 +15,9 @@
  * ---------------------------------------
  * - Status: every function returns TM_OK (0) or a TM_E* code; the message of
  *   the last failure is available from tm_last_error().  Nothing falls back to
- *   the host: a missing or failing GPU is an error.
+ *   the host: a missing or failing GPU is an error.  No C++ exception leaves the
+ *   library: a failed host allocation inside a call returns TM_ENOMEM, and a host
+ *   thread that cannot be started leaves its share of the work to the calling one.
  * - Memory: pointers named *_dev are caller-owned device memory on the
  *   context's device; all other pointers are caller-owned host memory that is
  *   only read (or written, for outputs) during the call.  The library copies
@@ -52,7 +54,7 @@ extern "C" {
 #define TM_ENOTCONVERGED 3   /* solver hit max_iter before rtol                   */
 #define TM_ENONFINITE 4      /* NaN/Inf met in a reduction                        */
 #define TM_ETIMEOUT 5        /* a bounded device-side wait gave up                */
-#define TM_ENOMEM 6          /* device allocation failed                          */
+#define TM_ENOMEM 6          /* device or host allocation failed                  */
 #define TM_ESTATE 7          /* call out of order (e.g. no mesh uploaded)         */
 
 #define TM_PREC_FP64 0       /* every step in FP64                                */

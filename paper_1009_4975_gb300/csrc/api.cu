@@ -405,7 +405,7 @@ int enqueue_twolevel(tm_ctx *ctx, int mode, const float *r, float *p, const floa
 
 extern "C" {
 
-int tm_create(tm_ctx **out, int device, void *cuda_stream) {
+int tm_create(tm_ctx **out, int device, void *cuda_stream) try {
   if (!out) return TM_EINVAL;
   *out = nullptr;
   int n = 0;
@@ -425,9 +425,11 @@ int tm_create(tm_ctx **out, int device, void *cuda_stream) {
   }
   *out = c;
   return TM_OK;
+} catch (...) {
+  return exception_status(nullptr);
 }
 
-int tm_destroy(tm_ctx *ctx) {
+int tm_destroy(tm_ctx *ctx) try {
   if (!ctx) return TM_OK;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
@@ -450,17 +452,21 @@ int tm_destroy(tm_ctx *ctx) {
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   delete ctx;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_set_stream(tm_ctx *ctx, void *cuda_stream) {
+int tm_set_stream(tm_ctx *ctx, void *cuda_stream) try {
   if (!ctx) return TM_EINVAL;
   ctx->stream = (cudaStream_t)cuda_stream;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 const char *tm_last_error(tm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
-int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
+int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) try {
   TM_CHECK_CTX(ctx);
   if (!d) return fail(ctx, TM_EINVAL, "null mesh descriptor");
   TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -571,10 +577,12 @@ int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info) {
     info->n_bricks = m.nbrick;
   }
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 int tm_mesh_tables(tm_ctx *ctx, int64_t *perm, int32_t *node_xyz, int32_t *conn, int32_t *hang_node,
-                   int32_t *hang_master, uint8_t *node_flags) {
+                   int32_t *hang_master, uint8_t *node_flags) try {
   if (!ctx) return TM_EINVAL;
   TM_CHECK_MESH(ctx);
   const HostMesh &h = ctx->host;
@@ -585,10 +593,12 @@ int tm_mesh_tables(tm_ctx *ctx, int64_t *perm, int32_t *node_xyz, int32_t *conn,
   if (hang_master) std::memcpy(hang_master, h.hang_master.data(), h.hang_master.size() * sizeof(int32_t));
   if (node_flags) std::memcpy(node_flags, h.nflag.data(), h.nflag.size());
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 int tm_build_rhs(tm_ctx *ctx, int64_t n_loads, const int32_t *node_xyz, const int32_t *comp, const double *val,
-                 double *f_dev) {
+                 double *f_dev) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (n_loads < 0 || (n_loads > 0 && (!node_xyz || !comp || !val)) || !f_dev)
@@ -623,9 +633,11 @@ int tm_build_rhs(tm_ctx *ctx, int64_t n_loads, const int32_t *node_xyz, const in
     TM_CUDA(ctx, e);
   }
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_apply_K(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double *y_dev) {
+int tm_apply_K(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double *y_dev) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!rho_dev || !x_dev || !y_dev) return fail(ctx, TM_EINVAL, "null pointer");
@@ -634,9 +646,11 @@ int tm_apply_K(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double *
   int rc = timed_apply<double>(ctx, ctx->w.ce64, x_dev, y_dev, ctx->w.part64, nullptr, nullptr, true, nullptr);
   if (rc) return rc;
   return drain_profile(ctx, false);
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_apply_K_f32(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float *y_dev) {
+int tm_apply_K_f32(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float *y_dev) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!rho_dev || !x_dev || !y_dev) return fail(ctx, TM_EINVAL, "null pointer");
@@ -645,9 +659,11 @@ int tm_apply_K_f32(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float
   int rc = timed_apply<float>(ctx, ctx->w.ce32, x_dev, y_dev, ctx->w.part32, nullptr, nullptr, true, nullptr);
   if (rc) return rc;
   return drain_profile(ctx, false);
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_apply_K_f32_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const float *x_dev, float *y_dev) {
+int tm_apply_K_f32_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const float *x_dev, float *y_dev) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!rho_dev || !x_dev || !y_dev) return fail(ctx, TM_EINVAL, "null pointer");
@@ -659,9 +675,11 @@ int tm_apply_K_f32_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const flo
                                   ctx->stream));
   ctx->launches += 3;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_apply_K_f32_static(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float *y_dev) {
+int tm_apply_K_f32_static(tm_ctx *ctx, const double *rho_dev, const float *x_dev, float *y_dev) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!rho_dev || !x_dev || !y_dev) return fail(ctx, TM_EINVAL, "null pointer");
@@ -677,9 +695,11 @@ int tm_apply_K_f32_static(tm_ctx *ctx, const double *rho_dev, const float *x_dev
   TM_CUDA(ctx, launch_apply<float>(m, ce, x_dev, y_dev, part, nullptr, nullptr, nullptr, true, nullptr, ctx->stream));
   ctx->launches += 3;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_jacobi_diag(tm_ctx *ctx, const double *rho_dev, double *d_dev) {
+int tm_jacobi_diag(tm_ctx *ctx, const double *rho_dev, double *d_dev) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!rho_dev || !d_dev) return fail(ctx, TM_EINVAL, "null pointer");
@@ -687,10 +707,12 @@ int tm_jacobi_diag(tm_ctx *ctx, const double *rho_dev, double *d_dev) {
   TM_CUDA(ctx, launch_diag(ctx->dm, ctx->w.ce64, d_dev, nullptr, nullptr, ctx->stream));
   ctx->launches += 2;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 int tm_pcg_solve_batch(int n, tm_ctx *const *ctxs, const double *const *rho_dev, const double *const *f_dev,
-                       double *const *u_dev, const tm_solve_opts *opts, tm_solve_stats *stats, int *status) {
+                       double *const *u_dev, const tm_solve_opts *opts, tm_solve_stats *stats, int *status) try {
   if (n < 1 || !ctxs || !rho_dev || !f_dev || !u_dev || !opts) return TM_EINVAL;
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i]) return TM_EINVAL;
@@ -699,13 +721,20 @@ int tm_pcg_solve_batch(int n, tm_ctx *const *ctxs, const double *const *rho_dev,
   }
   // one host thread per context: each drives its own solve on its own streams, so the
   // solves' kernels, graph replays and convergence checks interleave on the GPU
+  // (a solve whose thread cannot be started runs on the calling thread)
   std::vector<int> rc(n, TM_OK);
   std::vector<std::thread> th;
   th.reserve(n);
-  for (int i = 0; i < n; ++i)
-    th.emplace_back([&, i] {
+  for (int i = 0; i < n; ++i) {
+    auto solve = [&, i] {
       rc[i] = tm_pcg_solve(ctxs[i], rho_dev[i], f_dev[i], u_dev[i], opts, stats ? &stats[i] : nullptr);
-    });
+    };
+    try {
+      th.emplace_back(solve);
+    } catch (...) {
+      solve();
+    }
+  }
   for (auto &t : th) t.join();
   int first = TM_OK;
   for (int i = 0; i < n; ++i) {
@@ -713,18 +742,22 @@ int tm_pcg_solve_batch(int n, tm_ctx *const *ctxs, const double *const *rho_dev,
     if (first == TM_OK && rc[i] != TM_OK) first = rc[i];
   }
   return first;
+} catch (...) {
+  return exception_status(nullptr);
 }
 
-int tm_expand(tm_ctx *ctx, const double *u_dev, double *u_full_dev) {
+int tm_expand(tm_ctx *ctx, const double *u_dev, double *u_full_dev) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!u_dev || !u_full_dev) return fail(ctx, TM_EINVAL, "null pointer");
   TM_CUDA(ctx, launch_expand(ctx->dm, u_dev, u_full_dev, ctx->stream));
   ctx->launches += ctx->dm.nh > 0 ? 2 : 1;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_amr_mark(tm_ctx *ctx, const double *rho_dev, double rho_solid, double r_amr, int8_t *mark_dev) {
+int tm_amr_mark(tm_ctx *ctx, const double *rho_dev, double rho_solid, double r_amr, int8_t *mark_dev) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!rho_dev || !mark_dev) return fail(ctx, TM_EINVAL, "null pointer");
@@ -732,10 +765,12 @@ int tm_amr_mark(tm_ctx *ctx, const double *rho_dev, double rho_solid, double r_a
   TM_CUDA(ctx, launch_amr_mark(ctx->dm, rho_dev, rho_solid, r_amr, ctx->w.mark_tmp, mark_dev, ctx->stream));
   ctx->launches += 3;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 int tm_amr_adapt(tm_ctx *ctx, const int8_t *mark_dev, const double *rho_dev, int64_t capacity, int32_t *leaves_out,
-                 double *rho_out, int64_t *n_out) {
+                 double *rho_out, int64_t *n_out) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!mark_dev || !rho_dev || !n_out) return fail(ctx, TM_EINVAL, "null pointer");
@@ -755,10 +790,12 @@ int tm_amr_adapt(tm_ctx *ctx, const int8_t *mark_dev, const double *rho_dev, int
   std::memcpy(leaves_out, lv.data(), lv.size() * sizeof(int32_t));
   std::memcpy(rho_out, rn.data(), rn.size() * sizeof(double));
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 int tm_design_difference(tm_ctx *ctx, const double *rho_dev, int64_t n_other, const int32_t *leaves_other,
-                         const double *rho_other, double *d_out) {
+                         const double *rho_other, double *d_out) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!rho_dev || !leaves_other || !rho_other || !d_out || n_other < 1) return fail(ctx, TM_EINVAL, "bad arguments");
@@ -808,10 +845,12 @@ int tm_design_difference(tm_ctx *ctx, const double *rho_dev, int64_t n_other, co
   ctx->launches += 2;
   *d_out = out[0] / out[1];
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 int tm_transfer_displacement(tm_ctx *ctx, const double *u_full_dev, int64_t n_points, const int32_t *points_dev,
-                             double *out_dev) {
+                             double *out_dev) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (n_points < 0 || !u_full_dev || (n_points > 0 && (!points_dev || !out_dev)))
@@ -826,9 +865,11 @@ int tm_transfer_displacement(tm_ctx *ctx, const double *u_full_dev, int64_t n_po
   TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (nbad) return fail(ctx, TM_EINVAL, std::to_string(nbad) + " transfer points outside the mesh's box");
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_learn_input(tm_ctx *ctx, const double *rho_dev, const double *f_dev, int g, float *x_dev, double *s_out) {
+int tm_learn_input(tm_ctx *ctx, const double *rho_dev, const double *f_dev, int g, float *x_dev, double *s_out) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!rho_dev || !f_dev || !x_dev) return fail(ctx, TM_EINVAL, "null pointer");
@@ -844,9 +885,11 @@ int tm_learn_input(tm_ctx *ctx, const double *rho_dev, const double *f_dev, int 
   if (!(s > 0) || !std::isfinite(s)) return fail(ctx, TM_EINVAL, "the load restricts to zero on the voxel grid");
   if (s_out) *s_out = s;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_learn_guess(tm_ctx *ctx, const float *out_dev, double s, int g, double *u0_dev) {
+int tm_learn_guess(tm_ctx *ctx, const float *out_dev, double s, int g, double *u0_dev) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!out_dev || !u0_dev) return fail(ctx, TM_EINVAL, "null pointer");
@@ -855,9 +898,11 @@ int tm_learn_guess(tm_ctx *ctx, const float *out_dev, double s, int g, double *u
   TM_CUDA(ctx, learn_guess_launch(ctx->dm, ctx->learn, out_dev, s, u0_dev, ctx->stream));
   ctx->launches += 1;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_learn_output_grad(tm_ctx *ctx, const double *au0_dev, const double *f_dev, double s, int g, float *dout_dev) {
+int tm_learn_output_grad(tm_ctx *ctx, const double *au0_dev, const double *f_dev, double s, int g, float *dout_dev) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!au0_dev || !f_dev || !dout_dev) return fail(ctx, TM_EINVAL, "null pointer");
@@ -866,10 +911,12 @@ int tm_learn_output_grad(tm_ctx *ctx, const double *au0_dev, const double *f_dev
   TM_CUDA(ctx, learn_grad_launch(ctx->dm, ctx->learn, au0_dev, f_dev, s, ctx->learn.pf, dout_dev, ctx->stream));
   ctx->launches += 2;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 int tm_adam_step(tm_ctx *ctx, int64_t n, float *params_dev, const float *grads_dev, float *m_dev, float *v_dev,
-                 int step, float lr, float beta1, float beta2, float eps) {
+                 int step, float lr, float beta1, float beta2, float eps) try {
   TM_CHECK_CTX(ctx);
   if (n < 0 || (n > 0 && (!params_dev || !grads_dev || !m_dev || !v_dev)) || step < 1 || !(lr > 0) ||
       !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
@@ -879,9 +926,11 @@ int tm_adam_step(tm_ctx *ctx, int64_t n, float *params_dev, const float *grads_d
   TM_CUDA(ctx, adam_launch(params_dev, grads_dev, m_dev, v_dev, n, lr, beta1, beta2, eps, c1, c2, ctx->stream));
   ctx->launches += 1;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_profile(tm_ctx *ctx, int enable) {
+int tm_profile(tm_ctx *ctx, int enable) try {
   TM_CHECK_CTX(ctx);
   TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   int rc = drain_profile(ctx, true);
@@ -890,9 +939,11 @@ int tm_profile(tm_ctx *ctx, int enable) {
   ctx->launches = 0;
   ctx->prof = tm_profile_data();
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_profile_read(tm_ctx *ctx, tm_profile_data *out) {
+int tm_profile_read(tm_ctx *ctx, tm_profile_data *out) try {
   TM_CHECK_CTX(ctx);
   if (!out) return fail(ctx, TM_EINVAL, "null pointer");
   TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -901,6 +952,8 @@ int tm_profile_read(tm_ctx *ctx, tm_profile_data *out) {
   *out = ctx->prof;
   out->launches = ctx->launches;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 }  // extern "C"
@@ -1076,7 +1129,7 @@ int run_cg(tm_ctx *ctx, int check_every, bool graphs, int *iters_out, int *nonfi
 extern "C" {
 
 int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double *u_dev, const tm_solve_opts *opts,
-                 tm_solve_stats *stats) {
+                 tm_solve_stats *stats) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!rho_dev || !f_dev || !u_dev || !opts) return fail(ctx, TM_EINVAL, "null pointer");
@@ -1231,10 +1284,12 @@ int tm_pcg_solve(tm_ctx *ctx, const double *rho_dev, const double *f_dev, double
   if (stats) *stats = out;
   if (status == TM_ENOTCONVERGED) return fail(ctx, status, "max_iter reached before rtol");
   return status;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 int tm_pcg_solve_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const double *f_dev, double *u_dev,
-                       const tm_solve_opts *opts, tm_solve_stats *stats) {
+                       const tm_solve_opts *opts, tm_solve_stats *stats) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!rho_dev || !f_dev || !u_dev || !opts) return fail(ctx, TM_EINVAL, "null pointer");
@@ -1469,10 +1524,12 @@ int tm_pcg_solve_multi(tm_ctx *ctx, int nrhs, const double *rho_dev, const doubl
   if (stats) std::memcpy(stats, out.data(), nrhs * sizeof(tm_solve_stats));
   if (status == TM_ENOTCONVERGED) return fail(ctx, status, "max_iter reached before rtol");
   return status;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 int tm_sensitivity(tm_ctx *ctx, const double *rho_dev, const double *u_full_dev, double *dc_dev,
-                   double *compliance_out) {
+                   double *compliance_out) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!rho_dev || !u_full_dev || !dc_dev) return fail(ctx, TM_EINVAL, "null pointer");
@@ -1482,9 +1539,11 @@ int tm_sensitivity(tm_ctx *ctx, const double *rho_dev, const double *u_full_dev,
   ctx->launches += 1;
   if (compliance_out) return read_scalar(ctx, cdev, compliance_out);
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_filter(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double rmin, int mode, double *out_dev) {
+int tm_filter(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double rmin, int mode, double *out_dev) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!rho_dev || !x_dev || !out_dev) return fail(ctx, TM_EINVAL, "null pointer");
@@ -1493,10 +1552,12 @@ int tm_filter(tm_ctx *ctx, const double *rho_dev, const double *x_dev, double rm
   TM_CUDA(ctx, launch_filter(ctx->dm, rho_dev, x_dev, rmin, mode, out_dev, ctx->stream));
   ctx->launches += 1;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 int tm_oc_update(tm_ctx *ctx, const double *rho_dev, const double *dc_dev, double volfrac, double move, double eta,
-                 double rho_min, double *rho_new_dev, double *change_out) {
+                 double rho_min, double *rho_new_dev, double *change_out) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!rho_dev || !dc_dev || !rho_new_dev) return fail(ctx, TM_EINVAL, "null pointer");
@@ -1529,10 +1590,12 @@ int tm_oc_update(tm_ctx *ctx, const double *rho_dev, const double *dc_dev, doubl
   if (change_out) return read_scalar(ctx, &oc_state(ctx)->change, change_out);
   TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 // ---------------------------------------------------------------- two-level preconditioner
-int tm_coarse_setup(tm_ctx *ctx, const double *rho_dev, int32_t *levels_out, int32_t *shapes_out) {
+int tm_coarse_setup(tm_ctx *ctx, const double *rho_dev, int32_t *levels_out, int32_t *shapes_out) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   if (!rho_dev) return fail(ctx, TM_EINVAL, "null pointer");
@@ -1547,6 +1610,8 @@ int tm_coarse_setup(tm_ctx *ctx, const double *rho_dev, int32_t *levels_out, int
       shapes_out[3 * l + 2] = h.lev[l].Z;
     }
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 #define TM_CHECK_COARSE(ctx)                                                                 \
@@ -1554,7 +1619,7 @@ int tm_coarse_setup(tm_ctx *ctx, const double *rho_dev, int32_t *levels_out, int
     if (!(ctx)->coarse_ready) return fail(ctx, TM_ESTATE, "no two-level set-up for this mesh"); \
   } while (0)
 
-int tm_coarse_cells(tm_ctx *ctx, int level, float *K_dev) {
+int tm_coarse_cells(tm_ctx *ctx, int level, float *K_dev) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   TM_CHECK_COARSE(ctx);
@@ -1564,9 +1629,11 @@ int tm_coarse_cells(tm_ctx *ctx, int level, float *K_dev) {
   TM_CUDA(ctx, cudaMemcpyAsync(K_dev, c.K, 576 * (size_t)c.X * c.Y * c.Z * sizeof(float), cudaMemcpyDeviceToDevice,
                                ctx->stream));
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_coarse_apply(tm_ctx *ctx, int level, const float *x_dev, float *y_dev) {
+int tm_coarse_apply(tm_ctx *ctx, int level, const float *x_dev, float *y_dev) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   TM_CHECK_COARSE(ctx);
@@ -1575,9 +1642,11 @@ int tm_coarse_apply(tm_ctx *ctx, int level, const float *x_dev, float *y_dev) {
   TM_CUDA(ctx, coarse_level_apply_launch(h, level, x_dev, y_dev, ctx->stream));
   ctx->launches += 1;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_coarse_restrict(tm_ctx *ctx, const float *r_dev, float *b0_dev) {
+int tm_coarse_restrict(tm_ctx *ctx, const float *r_dev, float *b0_dev) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   TM_CHECK_COARSE(ctx);
@@ -1588,9 +1657,11 @@ int tm_coarse_restrict(tm_ctx *ctx, const float *r_dev, float *b0_dev) {
                                cudaMemcpyDeviceToDevice, ctx->stream));
   ctx->launches += 2;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_coarse_prolong(tm_ctx *ctx, const float *v0_dev, float *y_dev) {
+int tm_coarse_prolong(tm_ctx *ctx, const float *v0_dev, float *y_dev) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   TM_CHECK_COARSE(ctx);
@@ -1598,9 +1669,11 @@ int tm_coarse_prolong(tm_ctx *ctx, const float *v0_dev, float *y_dev) {
   TM_CUDA(ctx, coarse_prolong_launch(ctx->dm, ctx->coarse, v0_dev, y_dev, ctx->stream));
   ctx->launches += 1;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
-int tm_coarse_vcycle(tm_ctx *ctx, const float *b0_dev, float *x0_dev, int nu) {
+int tm_coarse_vcycle(tm_ctx *ctx, const float *b0_dev, float *x0_dev, int nu) try {
   TM_CHECK_CTX(ctx);
   TM_CHECK_MESH(ctx);
   TM_CHECK_COARSE(ctx);
@@ -1614,6 +1687,8 @@ int tm_coarse_vcycle(tm_ctx *ctx, const float *b0_dev, float *x0_dev, int nu) {
   TM_CUDA(ctx, cudaMemcpyAsync(x0_dev, h.lev[0].x, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
   ctx->launches += 1 + nl;
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 }  // extern "C"

@@ -3,6 +3,7 @@
 // and the dense inverse of the coarsest level.  Integer work and small dense algebra only.
 #include <algorithm>
 #include <cmath>
+#include <exception>
 #include <thread>
 #include <string>
 #include <vector>
@@ -178,18 +179,37 @@ static double dot4(const double *a, const double *b, int n) {
   return (s0 + s1) + (s2 + s3);
 }
 
-// f(i) for i in [0, n) on up to 8 host threads, rows dealt out round robin (row costs fall with i)
+// f(i) for i in [0, n) on up to 8 host threads, rows dealt out round robin (row costs fall with i).
+// A stripe whose thread cannot be started runs on the calling thread; an exception is caught on
+// its thread and rethrown here once every thread has joined.
 template <typename F>
 static void parallel_rows(int n, F f) {
   const int hw = (int)std::thread::hardware_concurrency();
   const int nt = std::max(1, std::min({8, hw > 0 ? hw : 1, n / 32}));
-  std::vector<std::thread> pool;
-  for (int t = 1; t < nt; ++t)
-    pool.emplace_back([&, t] {
+  std::vector<std::exception_ptr> ex(nt);
+  auto stripe = [&](int t) {
+    try {
       for (int i = t; i < n; i += nt) f(i);
-    });
-  for (int i = 0; i < n; i += nt) f(i);
+    } catch (...) {
+      ex[t] = std::current_exception();
+    }
+  };
+  std::vector<std::thread> pool;
+  std::vector<int> here;
+  pool.reserve(nt);
+  here.reserve(nt);
+  for (int t = 1; t < nt; ++t) {
+    try {
+      pool.emplace_back(stripe, t);
+    } catch (...) {
+      here.push_back(t);
+    }
+  }
+  stripe(0);
+  for (int t : here) stripe(t);
   for (auto &th : pool) th.join();
+  for (const std::exception_ptr &e : ex)
+    if (e) std::rethrow_exception(e);
 }
 
 std::string coarse_dense_inverse(const std::vector<double> &Kc, int X, int Y, int Z, unsigned faces,

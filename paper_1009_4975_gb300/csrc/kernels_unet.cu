@@ -334,7 +334,7 @@ int64_t tm_unet_workspace_floats(const tm_unet_desc *d) {
   return amr::make_plan(d, p) ? 2 * p.n_act : -1;
 }
 
-int tm_unet_forward(tm_ctx *ctx, const tm_unet_desc *d, const float *params, const float *x, float *y, float *ws) {
+int tm_unet_forward(tm_ctx *ctx, const tm_unet_desc *d, const float *params, const float *x, float *y, float *ws) try {
   using namespace amr;
   if (!ctx) return TM_EINVAL;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return unet_fail(ctx, TM_ECUDA, "cudaSetDevice");
@@ -371,10 +371,12 @@ int tm_unet_forward(tm_ctx *ctx, const tm_unet_desc *d, const float *params, con
   UNET_CUDA(ctx, unet_conv_fwd(ws + level_out(p, 0), params + p.out_w, params + p.out_b, y, p.N, p.C[0], p.co, p.X[0],
                                p.Y[0], p.Z[0], 1, false, s));
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 int tm_unet_backward(tm_ctx *ctx, const tm_unet_desc *d, const float *params, const float *x, const float *dy,
-                     float *dparams, float *dx, float *ws) {
+                     float *dparams, float *dx, float *ws) try {
   using namespace amr;
   if (!ctx) return TM_EINVAL;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return unet_fail(ctx, TM_ECUDA, "cudaSetDevice");
@@ -419,6 +421,8 @@ int tm_unet_backward(tm_ctx *ctx, const tm_unet_desc *d, const float *params, co
                                  p.Z[i - 1], true, true, s));
   }
   return TM_OK;
+} catch (...) {
+  return exception_status(ctx);
 }
 
 }  // extern "C"

@@ -19,7 +19,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <exception>
 #include <unordered_map>
+#include <memory>
 #include <numeric>
 #include <thread>
 
@@ -69,12 +71,35 @@ static int host_threads(size_t n) {
 }
 
 // f(t, lo, hi) over nt contiguous chunks of [0, n), one host thread each.
+// A chunk whose thread cannot be started runs on the calling thread (the chunks share nothing but
+// their index t, so where they run does not change the result), and an exception a chunk throws
+// is caught on its thread and rethrown here once every thread has joined.
 template <typename F>
 static void chunked(int nt, size_t n, F f) {
+  std::vector<std::exception_ptr> ex(nt);
+  auto run = [&](int t) {
+    try {
+      f(t, n * t / nt, n * (t + 1) / nt);
+    } catch (...) {
+      ex[t] = std::current_exception();
+    }
+  };
   std::vector<std::thread> pool;
-  for (int t = 1; t < nt; ++t) pool.emplace_back([&, t] { f(t, n * t / nt, n * (t + 1) / nt); });
-  f(0, 0, n / nt);
+  std::vector<int> here;
+  pool.reserve(nt);
+  here.reserve(nt);
+  for (int t = 1; t < nt; ++t) {
+    try {
+      pool.emplace_back(run, t);
+    } catch (...) {
+      here.push_back(t);
+    }
+  }
+  run(0);
+  for (int t : here) run(t);
   for (auto &th : pool) th.join();
+  for (const std::exception_ptr &e : ex)
+    if (e) std::rethrow_exception(e);
 }
 
 // Each pass: per-chunk digit counts, then every chunk scatters its items in order to the positions
@@ -1133,19 +1158,42 @@ struct tm_tables {
   amr::HostMesh m;
 };
 
+// The handler of the host-only entry points' function-try-blocks (inside a catch only): the status
+// of the exception that would otherwise cross the C boundary, its message into err (err_len bytes).
+static int table_exception(char *err, int err_len) noexcept {
+  int code = TM_EINVAL;
+  const char *what = "unexpected C++ exception";
+  try {
+    throw;
+  } catch (const std::bad_alloc &) {
+    code = TM_ENOMEM;
+    what = "host memory allocation failed";
+  } catch (const std::length_error &) {
+    code = TM_ENOMEM;
+    what = "host array size out of range";
+  } catch (const std::exception &e) {
+    what = e.what();
+  } catch (...) {
+  }
+  if (err && err_len > 0) {
+    std::strncpy(err, what, (size_t)err_len - 1);
+    err[err_len - 1] = 0;
+  }
+  return code;
+}
+
 extern "C" {
 
-int tm_tables_build(const tm_mesh_desc *d, tm_tables **out, tm_mesh_info *info, char *err, int err_len) {
+int tm_tables_build(const tm_mesh_desc *d, tm_tables **out, tm_mesh_info *info, char *err, int err_len) try {
   if (!d || !out) return TM_EINVAL;
   *out = nullptr;
-  tm_tables *t = new tm_tables();
+  std::unique_ptr<tm_tables> t(new tm_tables());
   std::string msg = amr::build_host_mesh(*d, t->m);
   if (!msg.empty()) {
     if (err && err_len > 0) {
       std::strncpy(err, msg.c_str(), (size_t)err_len - 1);
       err[err_len - 1] = 0;
     }
-    delete t;
     return TM_EINVAL;
   }
   const amr::HostMesh &m = t->m;
@@ -1162,12 +1210,14 @@ int tm_tables_build(const tm_mesh_desc *d, tm_tables **out, tm_mesh_info *info, 
     info->max_block_bytes = m.max_rec_bytes;
     info->n_bricks = m.nbrick;
   }
-  *out = t;
+  *out = t.release();
   return TM_OK;
+} catch (...) {
+  return table_exception(err, err_len);
 }
 
 int tm_tables_copy(const tm_tables *t, int64_t *perm, int32_t *node_xyz, int32_t *conn, int32_t *hang_node,
-                   int32_t *hang_master, uint8_t *node_flags) {
+                   int32_t *hang_master, uint8_t *node_flags) try {
   if (!t) return TM_EINVAL;
   const amr::HostMesh &h = t->m;
   if (perm) std::memcpy(perm, h.perm.data(), h.perm.size() * sizeof(int64_t));
@@ -1177,10 +1227,12 @@ int tm_tables_copy(const tm_tables *t, int64_t *perm, int32_t *node_xyz, int32_t
   if (hang_master) std::memcpy(hang_master, h.hang_master.data(), h.hang_master.size() * sizeof(int32_t));
   if (node_flags) std::memcpy(node_flags, h.nflag.data(), h.nflag.size());
   return TM_OK;
+} catch (...) {
+  return table_exception(nullptr, 0);
 }
 
 int tm_tables_operator(const tm_tables *t, int32_t *rec_off, uint8_t *brec, double *modal, int32_t *sh_node,
-                       int32_t *sh_ptr, int64_t *rec_bytes) {
+                       int32_t *sh_ptr, int64_t *rec_bytes) try {
   if (!t) return TM_EINVAL;
   const amr::HostMesh &h = t->m;
   if (rec_bytes) *rec_bytes = (int64_t)h.brec.size();
@@ -1190,9 +1242,11 @@ int tm_tables_operator(const tm_tables *t, int32_t *rec_off, uint8_t *brec, doub
   if (sh_node) std::memcpy(sh_node, h.sh_node.data(), h.sh_node.size() * sizeof(int32_t));
   if (sh_ptr) std::memcpy(sh_ptr, h.sh_ptr.data(), h.sh_ptr.size() * sizeof(int32_t));
   return TM_OK;
+} catch (...) {
+  return table_exception(nullptr, 0);
 }
 
-int tm_tables_bricks(const tm_tables *t, int32_t *e0, int32_t *node, uint8_t *hax, int32_t *out, uint32_t *fold) {
+int tm_tables_bricks(const tm_tables *t, int32_t *e0, int32_t *node, uint8_t *hax, int32_t *out, uint32_t *fold) try {
   if (!t) return TM_EINVAL;
   const amr::HostMesh &h = t->m;
   if (e0) std::memcpy(e0, h.brick_e0.data(), h.brick_e0.size() * sizeof(int32_t));
@@ -1201,10 +1255,12 @@ int tm_tables_bricks(const tm_tables *t, int32_t *e0, int32_t *node, uint8_t *ha
   if (out) std::memcpy(out, h.brick_out.data(), h.brick_out.size() * sizeof(int32_t));
   if (fold) std::memcpy(fold, h.brick_fold.data(), h.brick_fold.size() * sizeof(uint32_t));
   return TM_OK;
+} catch (...) {
+  return table_exception(nullptr, 0);
 }
 
 int tm_tables_diag(const tm_tables *t, int32_t *ptr, int32_t *elem, uint16_t *q, double *tab, int64_t *n_entries,
-                   int64_t *n_triples) {
+                   int64_t *n_triples) try {
   if (!t) return TM_EINVAL;
   const amr::HostMesh &h = t->m;
   if (n_entries) *n_entries = (int64_t)h.dg_elem.size();
@@ -1214,10 +1270,12 @@ int tm_tables_diag(const tm_tables *t, int32_t *ptr, int32_t *elem, uint16_t *q,
   if (q) std::memcpy(q, h.dg_q.data(), h.dg_q.size() * sizeof(uint16_t));
   if (tab) std::memcpy(tab, h.dg_tab.data(), h.dg_tab.size() * sizeof(double));
   return TM_OK;
+} catch (...) {
+  return table_exception(nullptr, 0);
 }
 
 int tm_tables_transfer(const tm_tables *t, const double *u_full, int64_t n_points, const int32_t *points,
-                       double *out) {
+                       double *out) try {
   if (!t || !u_full || (n_points > 0 && (!points || !out)) || n_points < 0) return TM_EINVAL;
   const amr::HostMesh &h = t->m;
   const int64_t fx = (int64_t)h.nx << h.L, fy = (int64_t)h.ny << h.L, fz = (int64_t)h.nz << h.L;
@@ -1243,6 +1301,8 @@ int tm_tables_transfer(const tm_tables *t, const double *u_full, int64_t n_point
     out[3 * i + 2] = v[2];
   }
   return TM_OK;
+} catch (...) {
+  return table_exception(nullptr, 0);
 }
 
 void tm_tables_free(tm_tables *t) { delete t; }
@@ -1411,7 +1471,7 @@ std::string adapt_leaves(const HostMesh &m, const int8_t *mark, const double *rh
 extern "C" {
 
 int tm_tables_adapt(const tm_tables *t, const int8_t *mark, const double *rho, int64_t capacity,
-                    int32_t *leaves_out, double *rho_out, int64_t *n_out) {
+                    int32_t *leaves_out, double *rho_out, int64_t *n_out) try {
   if (!t || !mark || !rho || !n_out) return TM_EINVAL;
   std::vector<int32_t> lv;
   std::vector<double> r;
@@ -1421,6 +1481,8 @@ int tm_tables_adapt(const tm_tables *t, const int8_t *mark, const double *rho, i
   std::memcpy(leaves_out, lv.data(), lv.size() * sizeof(int32_t));
   std::memcpy(rho_out, r.data(), r.size() * sizeof(double));
   return TM_OK;
+} catch (...) {
+  return table_exception(nullptr, 0);
 }
 
 }  // extern "C"

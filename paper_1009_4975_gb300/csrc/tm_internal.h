@@ -5,6 +5,9 @@
 #include <stdint.h>
 
 #include <deque>
+#include <exception>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -312,6 +315,34 @@ struct tm_ctx {
   cudaEvent_t ev_coarse = nullptr;   // the coarsest level's cell matrices reached the host
   bool capturing = false;
 };
+
+// The handler of the C-ABI entry points' function-try-blocks (call it only inside a catch): a C++
+// exception must not cross the C boundary, so it becomes a status -- TM_ENOMEM for a failed host
+// allocation (std::bad_alloc, std::length_error), TM_EINVAL for anything else -- and the context,
+// when there is one, keeps its message.
+inline int exception_status(tm_ctx *ctx) noexcept {
+  int code = TM_EINVAL;
+  const char *what = "unexpected C++ exception";
+  try {
+    throw;
+  } catch (const std::bad_alloc &) {
+    code = TM_ENOMEM;
+    what = "host memory allocation failed";
+  } catch (const std::length_error &) {
+    code = TM_ENOMEM;
+    what = "host array size out of range";
+  } catch (const std::exception &e) {
+    what = e.what();
+  } catch (...) {
+  }
+  if (ctx) {
+    try {
+      ctx->err = what;
+    } catch (...) {
+    }
+  }
+  return code;
+}
 
 namespace amr {
 // device-side launchers of the operator file; each returns the launch's cudaError_t

@@ -196,3 +196,42 @@ def test_jacobi_diagonal_tables_against_the_assembled_matrix(tm, make):
     # ascending elements within every node, and every element-node incidence listed once
     same = node[1:] == node[:-1]
     assert np.all(elem[1:][same] > elem[:-1][same])
+
+
+_NOMEM_CHILD = r"""
+import resource, sys
+import numpy as np
+import paper_1009_4975_gb300 as P
+P.load_library()
+nx, ny, nz = 128, 128, 64
+g = np.stack(np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij"), -1).reshape(-1, 3)
+leaves = np.ascontiguousarray(np.concatenate([g, np.zeros((len(g), 1), np.int64)], 1).astype(np.int32))
+vm = [int(l.split()[1]) * 1024 for l in open("/proc/self/status") if l.startswith("VmSize")][0]
+cap = vm + (int(sys.argv[1]) << 20)
+resource.setrlimit(resource.RLIMIT_AS, (cap, cap))
+try:
+    info, _ = P.tm_tables_build(nx, ny, nz, 0, 1.0, leaves)
+    print("built", info["Ne"])
+except P.TmError as e:
+    print("status", e.code, str(e))
+"""
+
+
+@pytest.mark.parametrize("headroom_mb", [16, 200, 500, 4000])
+def test_host_allocation_failure_is_a_status_not_an_abort(headroom_mb):
+    """A C++ exception must not cross the C ABI.  A child process whose address space is capped a
+    little above its size at the call builds the tables of a 1M-leaf mesh: where the cap cuts the
+    build off (in the calling thread, in a worker thread or at a thread's start), tm_tables_build
+    returns TM_ENOMEM with a message and the process lives on; with room enough it builds."""
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "-c", _NOMEM_CHILD, str(headroom_mb)], cwd=ROOT, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = r.stdout.split()
+    if headroom_mb >= 4000:
+        assert out[:2] == ["built", str(128 * 128 * 64)]
+    else:
+        import paper_1009_4975_gb300 as P
+        assert out[:2] == ["status", str(P.TM_ENOMEM)], r.stdout
+        assert "host memory allocation failed" in r.stdout
