@@ -145,9 +145,11 @@ const char *tm_last_error(tm_ctx *ctx);
 /* Build the mesh tables of Sec. 6 from a leaf set and upload them (paper
  * Sec. 4 marks/refines, Sec. 6 Fig. 3 limits incompatibility to one level).
  * Rejects with TM_EINVAL: leaves out of range or misaligned, overlapping or
- * non-covering leaf sets, and sets that are not 2:1 balanced (any two leaves
- * whose closures meet differ by at most one level).  Replaces any previous
- * mesh.  `info` (may be NULL) receives the sizes. */
+ * non-covering leaf sets, sets that are not 2:1 balanced (any two leaves
+ * whose closures meet differ by at most one level), 2^29 leaves or more, and
+ * meshes whose tables would need a 32-bit offset above 2^31 - 1 (3 Nn, the
+ * Jacobi-diagonal entries, the shared-node partials or the block records).
+ * Replaces any previous mesh.  `info` (may be NULL) receives the sizes. */
 int tm_mesh_upload(tm_ctx *ctx, const tm_mesh_desc *d, tm_mesh_info *info);
 
 /* Copy the integer tables to host arrays (any may be NULL):

@@ -57,6 +57,11 @@ static inline uint32_t compact3(uint64_t x) {
 // LSD radix sort of keys, returning the permutation (stable).
 static_assert(kBlockElems * kSlotRow < kQuarterBit, "inverse-list slot offsets must stay below the fold bits");
 
+// The tables keep node ids and their list, slot and record offsets in 32-bit integers; a mesh
+// whose tables would need more is rejected.
+constexpr int64_t kMaxOffset = ((int64_t)1 << 31) - 1;
+constexpr const char *kTooLarge = "mesh too large: a table offset would exceed 2^31 - 1";
+
 // Host threads for the table builds: up to 16, at most one per 64k items, and at most the
 // positive integer in the environment variable TM_HOST_THREADS when it holds one (read at every
 // call).  The tables do not depend on the number.
@@ -341,6 +346,7 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
       for (size_t i = lo; i < hi; ++i) m.conn[ord[i]] = nid[i];
     });
   }
+  if (3 * m.Nn > kMaxOffset) return kTooLarge;   // 3 DOFs per node
   const int64_t Nn = m.Nn;
   m.node_xyz.resize(3 * Nn);
   chunked(host_threads(Nn), (size_t)Nn, [&](int, size_t lo, size_t hi) {
@@ -834,16 +840,24 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     if (berr[t]) return berr[t];
   int32_t max_local = 0;
   for (int t = 0; t < nbt; ++t) max_local = std::max(max_local, bmax[t]);
-  int64_t ninv_all = 0;
-  for (int32_t b = 0; b < nblk; ++b) {
-    const int32_t nreg = bsz[b][0], nshared = bsz[b][1], nhang = bsz[b][2], nloc = nreg + nhang;
-    m.blk_node[b + 1] = m.blk_node[b] + nreg;
-    m.blk_shared[b] = nshared;
-    m.blk_slot[b + 1] = m.blk_slot[b] + nshared;
-    m.blk_hang[b + 1] = m.blk_hang[b] + nhang;
-    m.blk_inv[b] = (int32_t)ninv_all;
-    m.blk_iptr[b + 1] = m.blk_iptr[b] + nloc + 1;
-    ninv_all += bsz[b][3];
+  {
+    // running offsets in 64 bits: the tables keep them in 32
+    int64_t node = 0, slot = 0, hang = 0, iptr = 0, inv = 0;
+    for (int32_t b = 0; b < nblk; ++b) {
+      const int32_t nreg = bsz[b][0], nshared = bsz[b][1], nhang = bsz[b][2], nloc = nreg + nhang;
+      m.blk_shared[b] = nshared;
+      m.blk_inv[b] = (int32_t)inv;
+      node += nreg;
+      slot += nshared;
+      hang += nhang;
+      iptr += nloc + 1;
+      inv += bsz[b][3];
+      if (std::max({node, slot, 4 * hang, iptr, inv}) > kMaxOffset) return kTooLarge;
+      m.blk_node[b + 1] = (int32_t)node;
+      m.blk_slot[b + 1] = (int32_t)slot;
+      m.blk_hang[b + 1] = (int32_t)hang;
+      m.blk_iptr[b + 1] = (int32_t)iptr;
+    }
   }
   for (int t = 0; t < nbt; ++t) {
     m.lnode.insert(m.lnode.end(), bls[t].lnode.begin(), bls[t].lnode.end());
@@ -868,7 +882,14 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
       if (!m.brick_hax[i] && nblocks_of[n] > 1) cnt[n + 1]++;
     }
     std::vector<int32_t> start(Nn + 1, 0);
-    for (int64_t n = 0; n < Nn; ++n) start[n + 1] = start[n] + cnt[n + 1];
+    {
+      int64_t run = 0;
+      for (int64_t n = 0; n < Nn; ++n) {
+        run += cnt[n + 1];
+        if (3 * run > kMaxOffset) return kTooLarge;   // 3 partials per shared slot
+        start[n + 1] = (int32_t)run;
+      }
+    }
     std::vector<int32_t> fill(start.begin(), start.end() - 1);
     m.lslot.assign(m.blk_slot[nblk], 0);
     for (int32_t b = 0; b < nblk; ++b)
@@ -944,9 +965,12 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
       return y;
     };
     // the offsets in block order, then the records written in parallel
+    int64_t rec_units = 0;
     for (int32_t b = 0; b < nblk; ++b) {
       const Layout y = layout(b);
-      m.rec_off[b + 1] = m.rec_off[b] + (int32_t)(y.bytes / 16);
+      rec_units += (int64_t)(y.bytes / 16);
+      if (rec_units > kMaxOffset) return kTooLarge;
+      m.rec_off[b + 1] = (int32_t)rec_units;
       m.max_rec_bytes = std::max<int32_t>(m.max_rec_bytes, (int32_t)y.bytes);
       m.rec_skip[b] = (int32_t)((y.o_lnode - 64) / 16);
       m.max_rec_stage = std::max<int32_t>(m.max_rec_stage, (int32_t)(y.bytes - (y.o_lnode - 64)));
@@ -1083,6 +1107,8 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
       cx_lq[t].swap(my_lq);
       cx_tab[t].swap(my_tab);
     });
+    for (int t = 0; t < nt; ++t)   // ex_end holds positions in a chunk's list as int32
+      if ((int64_t)cx_node[t].size() > kMaxOffset) return kTooLarge;
     std::vector<std::vector<uint16_t>> l2g(nt);
     for (int t = 0; t < nt; ++t)
       for (const auto &q : cx_tab[t]) {
@@ -1127,7 +1153,14 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
         m.dg_ptr[n + 1] = s;
       }
     });
-    for (int64_t n = 0; n < Nn; ++n) m.dg_ptr[n + 1] += m.dg_ptr[n];
+    {
+      int64_t run = 0;
+      for (int64_t n = 0; n < Nn; ++n) {
+        run += m.dg_ptr[n + 1];
+        if (run > kMaxOffset) return kTooLarge;
+        m.dg_ptr[n + 1] = (int32_t)run;
+      }
+    }
     chunked(host_threads(Nn), (size_t)Nn, [&](int, size_t lo, size_t hi) {
       for (size_t n = lo; n < hi; ++n) {
         int32_t s = m.dg_ptr[n];
