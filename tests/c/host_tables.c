@@ -1,6 +1,7 @@
 /* Uses the C ABI from plain C (host-only entry points, no GPU): builds the tables of a
  * 2 x 1 x 1 box with one refined base cell, prints the counts, adapts it with all
- * refinable elements marked for refinement and prints the new leaf count. */
+ * refinable elements marked for refinement and prints the new leaf count, then reads the
+ * Jacobi-diagonal tables. */
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -45,7 +46,24 @@ int main(void) {
   mark[0] = 1;               /* level 1 == L: cannot refine */
   rc = tm_tables_adapt(t, mark, rho, 64, out_leaves, out_rho, &n_out);
   printf("bad mark rc %d\n", rc);
+  /* the Jacobi-diagonal tables: sizes first, then the arrays; the diagonal's component-0 sum at
+   * rho = 1 (c_e = h_e: level-1 elements 0..7 have h = 1/2, the level-0 element h = 1) */
+  int64_t n_entries = 0, n_triples = 0;
+  rc = tm_tables_diag(t, NULL, NULL, NULL, NULL, &n_entries, &n_triples);
+  int32_t *ptr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(info.Nn + 1));
+  int32_t *elem = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_entries);
+  uint16_t *q = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n_entries);
+  double *tab = (double *)malloc(sizeof(double) * 3 * (size_t)n_triples);
+  if (rc == TM_OK) rc = tm_tables_diag(t, ptr, elem, q, tab, &n_entries, &n_triples);
+  double dsum = 0.0;
+  for (int64_t nd = 0; nd < info.Nn; ++nd)
+    for (int32_t j = ptr[nd]; j < ptr[nd + 1]; ++j) dsum += (elem[j] == info.Ne - 1 ? 1.0 : 0.5) * tab[3 * q[j]];
+  printf("diag rc %d entries %lld triples %lld sum0 %.17g\n", rc, (long long)n_entries, (long long)n_triples, dsum);
   tm_tables_free(t);
+  free(ptr);
+  free(elem);
+  free(q);
+  free(tab);
   free(mark);
   free(rho);
   return 0;

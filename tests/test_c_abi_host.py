@@ -36,3 +36,11 @@ def test_c_program_uses_the_host_entry_points(lib, tmp_path):
                         f"blocks {info['n_blocks']}")
     assert lines[1] == "adapt rc 0 leaves 16"      # 8 children of the refined base cell + 8 unchanged
     assert lines[2] == "bad mark rc 1"              # TM_EINVAL
+    g = P.tm_tables_diag(2, 1, 1, 1, 1.0, leaves)
+    h = np.where(np.arange(info["Ne"]) == info["Ne"] - 1, 1.0, 0.5)
+    want = 0.0
+    for nd in range(info["Nn"]):   # the same summation order as the C program
+        for j in range(g["ptr"][nd], g["ptr"][nd + 1]):
+            want += h[g["elem"][j]] * g["tab"][g["q"][j], 0]
+    assert lines[3] == (f"diag rc 0 entries {g['elem'].size} triples {g['tab'].shape[0]} "
+                        f"sum0 {want:.17g}")
