@@ -166,8 +166,10 @@ int tm_mesh_tables(tm_ctx *ctx, int64_t *perm, int32_t *node_xyz, int32_t *conn,
  * the tables tm_mesh_upload builds, for inspection and testing on machines
  * without a GPU.  On failure returns TM_EINVAL and writes a message into err
  * (err_len bytes, may be 0).  info->device_bytes is 0.
- * Host threads: tm_mesh_upload, tm_tables_build and the adaptation's new leaf set
- * (tm_amr_adapt, tm_tables_adapt) run on up to 16 host threads, one per 65,536
+ * Host threads: tm_mesh_upload, tm_tables_build, the adaptation's new leaf set
+ * (tm_amr_adapt, tm_tables_adapt) and the two-level preconditioner's host part
+ * (its per-mesh tables and the coarsest level's dense inverse, in the first solve
+ * on a mesh and in tm_coarse_setup) run on up to 16 host threads, one per 65,536
  * items at most; the environment variable TM_HOST_THREADS (a positive integer,
  * read at every call) lowers the limit.  Every table and error is the same for
  * any number of threads. */

@@ -12,6 +12,45 @@
 
 namespace amr {
 
+// f(t, lo, hi) over nt contiguous chunks of [0, n) on host threads (host_thread_limit(), one per
+// 64k items, and so that the threads' per_thread_ints int32 each stay within 256 MB).  A chunk
+// whose thread cannot be started runs on the calling thread; an exception is rethrown after the
+// join.
+static int parallel_chunks_threads(int64_t n, int64_t per_thread_ints = 0) {
+  int64_t nt = std::min<int64_t>(host_thread_limit(), n / 65536 + 1);
+  if (per_thread_ints > 0) nt = std::min<int64_t>(nt, std::max<int64_t>(1, ((int64_t)1 << 26) / per_thread_ints));
+  return (int)std::max<int64_t>(1, nt);
+}
+
+template <typename F>
+static void parallel_chunks(int64_t n, F f, int nt = 0) {
+  if (nt <= 0) nt = parallel_chunks_threads(n);
+  std::vector<std::exception_ptr> ex(nt);
+  auto run = [&](int t) {
+    try {
+      f(t, n * t / nt, n * (t + 1) / nt);
+    } catch (...) {
+      ex[t] = std::current_exception();
+    }
+  };
+  std::vector<std::thread> pool;
+  std::vector<int> here;
+  pool.reserve(nt);
+  here.reserve(nt);
+  for (int t = 1; t < nt; ++t) {
+    try {
+      pool.emplace_back(run, t);
+    } catch (...) {
+      here.push_back(t);
+    }
+  }
+  run(0);
+  for (int t : here) run(t);
+  for (auto &th : pool) th.join();
+  for (const std::exception_ptr &e : ex)
+    if (e) std::rethrow_exception(e);
+}
+
 // Level 0 is the base grid; level l+1 has ceil(n / 2) cells per axis for the n of level l (a
 // coarse cell may overhang the box: the coarse functions restricted to the box stay nested),
 // added while level l has more than 64 cells.  An axis whose upper face is clamped is halved
@@ -49,38 +88,54 @@ void coarse_tables(const HostMesh &m, std::vector<int32_t> &cell_elem, std::vect
                    std::vector<int32_t> &cnode, std::vector<int32_t> &ncell, std::vector<uint32_t> &code) {
   const int X = m.nx, Y = m.ny, Z = m.nz, S = 1 << m.L;
   const int64_t ncells = (int64_t)X * Y * Z;
-  cell_elem.assign(2 * ncells, 0);
-  for (int64_t e = 0; e < m.Ne;) {
+  // a base cell's leaves are one run of the Morton order: each run's ends are found where the
+  // neighbouring leaf lies in another cell, independently per leaf
+  auto cell_of = [&](int64_t e) {
     const int32_t *l = &m.leaf[4 * e];
-    const int64_t c = (l[0] / S) + X * ((l[1] / S) + (int64_t)Y * (l[2] / S));
-    int64_t e1 = e + 1;
-    while (e1 < m.Ne) {
-      const int32_t *q = &m.leaf[4 * e1];
-      if ((q[0] / S) + X * ((q[1] / S) + (int64_t)Y * (q[2] / S)) != c) break;
-      ++e1;
+    return (l[0] / S) + X * ((l[1] / S) + (int64_t)Y * (l[2] / S));
+  };
+  cell_elem.assign(2 * ncells, 0);
+  parallel_chunks(m.Ne, [&](int, int64_t lo, int64_t hi) {
+    for (int64_t e = lo; e < hi; ++e) {
+      const int64_t c = cell_of(e);
+      if (e == 0 || cell_of(e - 1) != c) cell_elem[2 * c] = (int32_t)e;
+      if (e + 1 == m.Ne || cell_of(e + 1) != c) cell_elem[2 * c + 1] = (int32_t)(e + 1);
     }
-    cell_elem[2 * c] = (int32_t)e;
-    cell_elem[2 * c + 1] = (int32_t)e1;
-    e = e1;
-  }
+  });
+  // nodes by owning cell, ascending within a cell: per chunk of nodes its cell counts, then each
+  // chunk fills its nodes after the earlier chunks' nodes of the same cell
   ncell.assign(m.Nn, 0);
   code.assign(m.Nn, 0);
-  std::vector<int32_t> cnt(ncells + 1, 0);
-  for (int64_t n = 0; n < m.Nn; ++n) {
-    const int32_t *p = &m.node_xyz[3 * n];
-    const int cx = std::min(p[0] / S, X - 1), cy = std::min(p[1] / S, Y - 1), cz = std::min(p[2] / S, Z - 1);
-    const int64_t c = cx + X * (cy + (int64_t)Y * cz);
-    ncell[n] = (int32_t)c;
-    uint32_t cd = (uint32_t)(p[0] - cx * S) | ((uint32_t)(p[1] - cy * S) << 10) | ((uint32_t)(p[2] - cz * S) << 20);
-    if (m.nflag[n]) cd |= 0x80000000u;
-    code[n] = cd;
-    cnt[c + 1]++;
-  }
+  const int nt = parallel_chunks_threads(m.Nn, ncells);
+  std::vector<int32_t> cnt((size_t)nt * ncells, 0);
+  parallel_chunks(m.Nn, [&](int t, int64_t lo, int64_t hi) {
+    int32_t *ct = &cnt[(size_t)t * ncells];
+    for (int64_t n = lo; n < hi; ++n) {
+      const int32_t *p = &m.node_xyz[3 * n];
+      const int cx = std::min(p[0] / S, X - 1), cy = std::min(p[1] / S, Y - 1), cz = std::min(p[2] / S, Z - 1);
+      const int64_t c = cx + X * (cy + (int64_t)Y * cz);
+      ncell[n] = (int32_t)c;
+      uint32_t cd = (uint32_t)(p[0] - cx * S) | ((uint32_t)(p[1] - cy * S) << 10) | ((uint32_t)(p[2] - cz * S) << 20);
+      if (m.nflag[n]) cd |= 0x80000000u;
+      code[n] = cd;
+      ct[c]++;
+    }
+  }, nt);
   cptr.assign(ncells + 1, 0);
-  for (int64_t c = 0; c < ncells; ++c) cptr[c + 1] = cptr[c] + cnt[c + 1];
+  for (int64_t c = 0; c < ncells; ++c) {
+    int32_t run = cptr[c];
+    for (int t = 0; t < nt; ++t) {
+      const int32_t v = cnt[(size_t)t * ncells + c];
+      cnt[(size_t)t * ncells + c] = run;
+      run += v;
+    }
+    cptr[c + 1] = run;
+  }
   cnode.assign(m.Nn, 0);
-  std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
-  for (int64_t n = 0; n < m.Nn; ++n) cnode[fill[ncell[n]]++] = (int32_t)n;
+  parallel_chunks(m.Nn, [&](int t, int64_t lo, int64_t hi) {
+    int32_t *fill = &cnt[(size_t)t * ncells];
+    for (int64_t n = lo; n < hi; ++n) cnode[fill[ncell[n]]++] = (int32_t)n;
+  }, nt);
 }
 
 // Segments of the restriction: each cell's node run cut into pieces of at most kSegNodes, so
@@ -184,8 +239,7 @@ static double dot4(const double *a, const double *b, int n) {
 // its thread and rethrown here once every thread has joined.
 template <typename F>
 static void parallel_rows(int n, F f) {
-  const int hw = (int)std::thread::hardware_concurrency();
-  const int nt = std::max(1, std::min({8, hw > 0 ? hw : 1, n / 32}));
+  const int nt = std::max(1, std::min({8, host_thread_limit(), n / 32}));
   std::vector<std::exception_ptr> ex(nt);
   auto stripe = [&](int t) {
     try {

@@ -62,20 +62,12 @@ static_assert(kBlockElems * kSlotRow < kQuarterBit, "inverse-list slot offsets m
 constexpr int64_t kMaxOffset = ((int64_t)1 << 31) - 1;
 constexpr const char *kTooLarge = "mesh too large: a table offset would exceed 2^31 - 1";
 
-// Host threads for the table builds: up to 16, at most one per 64k items, and at most the
-// positive integer in the environment variable TM_HOST_THREADS when it holds one (read at every
-// call).  The tables do not depend on the number.
+// Host threads for the table builds: host_thread_limit(), at most one per 64k items.  The tables
+// do not depend on the number.
 static int host_threads(size_t n) {
-  int hw = (int)std::thread::hardware_concurrency();
-  if (const char *env = std::getenv("TM_HOST_THREADS")) {
-    char *end = nullptr;
-    const long v = std::strtol(env, &end, 10);
-    if (end != env && *end == 0 && v > 0) hw = (int)std::min<long>(v, 16);
-  }
-  return (int)std::max<size_t>(1, std::min<size_t>({(size_t)16, (size_t)(hw > 0 ? hw : 1), n / 65536 + 1}));
+  return (int)std::max<size_t>(1, std::min<size_t>((size_t)host_thread_limit(), n / 65536 + 1));
 }
 
-// f(t, lo, hi) over nt contiguous chunks of [0, n), one host thread each.
 // A chunk whose thread cannot be started runs on the calling thread (the chunks share nothing but
 // their index t, so where they run does not change the result), and an exception a chunk throws
 // is caught on its thread and rethrown here once every thread has joined.

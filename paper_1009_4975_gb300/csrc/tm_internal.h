@@ -4,11 +4,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <cstdlib>
 #include <deque>
 #include <exception>
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/tm.h"
@@ -315,6 +318,19 @@ struct tm_ctx {
   cudaEvent_t ev_coarse = nullptr;   // the coarsest level's cell matrices reached the host
   bool capturing = false;
 };
+
+// Host threads the library may use at once: the hardware's, at most 16, and at most the positive
+// integer in the environment variable TM_HOST_THREADS when it holds one (read at every call).
+inline int host_thread_limit() {
+  int hw = (int)std::thread::hardware_concurrency();
+  if (hw <= 0) hw = 1;
+  if (const char *env = std::getenv("TM_HOST_THREADS")) {
+    char *end = nullptr;
+    const long v = std::strtol(env, &end, 10);
+    if (end != env && *end == 0 && v > 0) hw = (int)std::min<long>(v, hw);
+  }
+  return std::min(hw, 16);
+}
 
 // The handler of the C-ABI entry points' function-try-blocks (call it only inside a catch): a C++
 // exception must not cross the C boundary, so it becomes a status -- TM_ENOMEM for a failed host
