@@ -1070,9 +1070,12 @@ int batch_graph(tm_ctx *ctx, int count, const T *ce, T *part, TX *x, T *r, T *p,
   ctx->ev_pending.resize(base);
   g.launches = (int)(ctx->launches - launches0);
   ctx->launches = launches0;    // counted at replay
-  if (e != cudaSuccess) return fail(ctx, TM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  if (rc) return rc;
-  if (e2 != cudaSuccess) return fail(ctx, TM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e2));
+  if (e != cudaSuccess || rc || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, TM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    if (rc) return rc;
+    return fail(ctx, TM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e2));
+  }
   e = cudaGraphInstantiate(&g.exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(ctx, TM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
