@@ -97,6 +97,7 @@ class Clocks:
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            os.unlink(self.path)
 
     def stop(self):
         if self.proc is None:
