@@ -280,9 +280,9 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     chunked(host_threads(8 * Ne), (size_t)Ne, [&](int, size_t lo, size_t hi) {
       for (size_t e = lo; e < hi; ++e)
         for (int k = 0; k < 8; ++k) {
-          const uint64_t key = corner_key(e, k);
-          uint64_t *w = &bm[key >> 6];
-          const uint64_t b = 1ull << (key & 63);
+          const uint64_t ck = corner_key(e, k);
+          uint64_t *w = &bm[ck >> 6];
+          const uint64_t b = 1ull << (ck & 63);
           if (!(__atomic_load_n(w, __ATOMIC_RELAXED) & b)) __atomic_fetch_or(w, b, __ATOMIC_RELAXED);
         }
     });
@@ -308,8 +308,8 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     chunked(host_threads(8 * Ne), (size_t)Ne, [&](int, size_t lo, size_t hi) {
       for (size_t e = lo; e < hi; ++e)
         for (int k = 0; k < 8; ++k) {
-          const uint64_t key = corner_key(e, k);
-          const uint64_t w = key >> 6, low = (1ull << (key & 63)) - 1;
+          const uint64_t ck = corner_key(e, k);
+          const uint64_t w = ck >> 6, low = (1ull << (ck & 63)) - 1;
           m.conn[8 * e + k] = (int32_t)(below[w] + __builtin_popcountll(bm[w] & low));
         }
     });
@@ -419,12 +419,12 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
             z += m.node_xyz[3 * cn[cs[i]] + 2];
           }
           x /= nc; y /= nc; z /= nc;
-          const uint64_t key = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+          const uint64_t ck = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
           int64_t n;
           if (bm.empty()) {
-            n = find_key(m.node_key, key);
+            n = find_key(m.node_key, ck);
           } else {
-            const uint64_t w = key >> 6, bit = 1ull << (key & 63);
+            const uint64_t w = ck >> 6, bit = 1ull << (ck & 63);
             n = w < bm.size() && (bm[w] & bit) ? below[w] + __builtin_popcountll(bm[w] & (bit - 1)) : -1;
           }
           if (n < 0) return;
@@ -592,7 +592,7 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
         if (hi < 0) continue;
         const int a = nd % 5, b = (nd / 5) % 5, c = nd / 25;
         int nm = 0, dmask = 0;
-        int d[4][3];
+        int step[4][3];
         for (int q = 0; q < 4; ++q) {
           const int32_t mm = m.hang_master[4 * hi + q];
           if (mm < 0) continue;
@@ -600,7 +600,7 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
           const int32_t rel[3] = {p[0] - l0[0] - s * a, p[1] - l0[1] - s * b, p[2] - l0[2] - s * c};
           for (int ax = 0; ax < 3; ++ax) {
             if (rel[ax] != 0 && rel[ax] != s && rel[ax] != -s) return false;
-            d[nm][ax] = rel[ax] / s;
+            step[nm][ax] = rel[ax] / s;
             if (rel[ax] != 0) dmask |= 1 << ax;
           }
           if (m.hang_index[mm] >= 0) return false;
@@ -612,10 +612,10 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
         // the masters are distinct
         for (int q = 0; q < nm; ++q)
           for (int ax = 0; ax < 3; ++ax)
-            if (((dmask >> ax) & 1) ? (d[q][ax] == 0) : (d[q][ax] != 0)) return false;
+            if (((dmask >> ax) & 1) ? (step[q][ax] == 0) : (step[q][ax] != 0)) return false;
         for (int q = 0; q < nm; ++q)
           for (int r = q + 1; r < nm; ++r)
-            if (d[q][0] == d[r][0] && d[q][1] == d[r][1] && d[q][2] == d[r][2]) return false;
+            if (step[q][0] == step[r][0] && step[q][1] == step[r][1] && step[q][2] == step[r][2]) return false;
         for (int ax = 0; ax < 3; ++ax) {
           const int pos = ax == 0 ? a : (ax == 1 ? b : c);
           if (((dmask >> ax) & 1) && (pos == 0 || pos == 4)) return false;
