@@ -865,36 +865,68 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
   // second pass streams them; each block writes its shared nodes' partials to
   // their CSR positions (lslot).
   {
-    // blocks first (ascending), then bricks (ascending): the order of a node's partials
-    std::vector<int32_t> cnt(Nn + 1, 0);
-    for (int32_t b = 0; b < nblk; ++b)
-      for (int32_t i = 0; i < m.blk_shared[b]; ++i) cnt[m.lnode[m.blk_node[b] + i] + 1]++;
-    for (size_t i = 0; i < m.brick_node.size(); ++i) {
-      const int32_t n = m.brick_node[i] & 0x7FFFFFFF;
-      if (!m.brick_hax[i] && nblocks_of[n] > 1) cnt[n + 1]++;
-    }
+    // blocks first (ascending), then bricks (ascending): the order of a node's partials.  The
+    // units (blocks, then bricks) are split into chunks; each chunk counts its partials per node,
+    // then writes them after the earlier chunks' partials of the same node, which is the order
+    // of one pass over the units (the threads' counts take nt x Nn int32: capped at 512 MB).
+    const int64_t nunit = (int64_t)nblk + m.nbrick;
+    const int nt = std::max(1, std::min(host_threads((size_t)nunit * 512),
+                                        (int)(((int64_t)1 << 27) / std::max<int64_t>(Nn, 1))));
+    auto unit_partials = [&](size_t lo, size_t hi, auto &&emit) {
+      for (size_t u = lo; u < hi; ++u) {
+        if ((int64_t)u < nblk) {
+          const int32_t b = (int32_t)u;
+          for (int32_t i = 0; i < m.blk_shared[b]; ++i) emit(m.lnode[m.blk_node[b] + i], &m.lslot[m.blk_slot[b] + i]);
+        } else {
+          const size_t i0 = (size_t)125 * (u - nblk);
+          for (size_t i = i0; i < i0 + 125; ++i) {
+            const int32_t n = m.brick_node[i] & 0x7FFFFFFF;
+            if (m.brick_hax[i]) m.brick_out[i] = -2;
+            else if (nblocks_of[n] > 1) emit(n, &m.brick_out[i]);
+          }
+        }
+      }
+    };
+    m.lslot.assign(m.blk_slot[nblk], 0);
+    m.brick_out.assign(m.brick_node.size(), -1);
+    std::vector<int32_t> ccnt((size_t)nt * Nn, 0);
+    chunked(nt, (size_t)nunit, [&](int t, size_t lo, size_t hi) {
+      int32_t *c = &ccnt[(size_t)t * Nn];
+      unit_partials(lo, hi, [&](int32_t n, int32_t *) { c[n]++; });
+    });
     std::vector<int32_t> start(Nn + 1, 0);
+    chunked(host_threads(Nn), (size_t)Nn, [&](int, size_t lo, size_t hi) {
+      for (size_t n = lo; n < hi; ++n) {
+        int32_t v = 0;
+        for (int t = 0; t < nt; ++t) v += ccnt[(size_t)t * Nn + n];
+        start[n + 1] = v;
+      }
+    });
+    // shared nodes: those with partials, ascending
+    std::vector<uint8_t> has(Nn);
+    for (int64_t n = 0; n < Nn; ++n) has[n] = start[n + 1] > 0;
     {
       int64_t run = 0;
       for (int64_t n = 0; n < Nn; ++n) {
-        run += cnt[n + 1];
+        run += start[n + 1];
         if (3 * run > kMaxOffset) return kTooLarge;   // 3 partials per shared slot
         start[n + 1] = (int32_t)run;
       }
     }
-    std::vector<int32_t> fill(start.begin(), start.end() - 1);
-    m.lslot.assign(m.blk_slot[nblk], 0);
-    for (int32_t b = 0; b < nblk; ++b)
-      for (int32_t i = 0; i < m.blk_shared[b]; ++i) {
-        const int32_t n = m.lnode[m.blk_node[b] + i];
-        m.lslot[m.blk_slot[b] + i] = fill[n]++;
+    chunked(host_threads(Nn), (size_t)Nn, [&](int, size_t lo, size_t hi) {
+      for (size_t n = lo; n < hi; ++n) {
+        int32_t s0 = start[n];
+        for (int t = 0; t < nt; ++t) {
+          const int32_t v = ccnt[(size_t)t * Nn + n];
+          ccnt[(size_t)t * Nn + n] = s0;
+          s0 += v;
+        }
       }
-    m.brick_out.assign(m.brick_node.size(), -1);
-    for (size_t i = 0; i < m.brick_node.size(); ++i) {
-      const int32_t n = m.brick_node[i] & 0x7FFFFFFF;
-      if (m.brick_hax[i]) m.brick_out[i] = -2;
-      else if (nblocks_of[n] > 1) m.brick_out[i] = fill[n]++;
-    }
+    });
+    chunked(nt, (size_t)nunit, [&](int t, size_t lo, size_t hi) {
+      int32_t *f = &ccnt[(size_t)t * Nn];
+      unit_partials(lo, hi, [&](int32_t n, int32_t *slot) { *slot = f[n]++; });
+    });
     m.nslot = start[Nn];
     // the brick pass's packed table: per brick 3 x 128 int32 -- node ids (125, then e0 at 125),
     // output targets (125), fold mask | axes << 24 (125)
@@ -914,7 +946,7 @@ std::string build_host_mesh(const tm_mesh_desc &d, HostMesh &m) {
     m.sh_ptr.push_back(0);
     m.sh_of_node.assign(Nn, -1);
     for (int64_t n = 0; n < Nn; ++n)
-      if (cnt[n + 1] > 0) {
+      if (has[n]) {
         m.sh_of_node[n] = (int32_t)m.sh_node.size();
         m.sh_node.push_back((int32_t)n);
         m.sh_ptr.push_back(start[n + 1]);
